@@ -1,0 +1,220 @@
+/*
+ * tbsma.h -- C ABI of the B300 (sm_103a) TB-SMA nanowire MD hot path.
+ *
+ * The library advances many independent fcc Au nanowires ("wires") at once:
+ * a per-wire cell-list / Verlet neighbour-list build, the two-pass TB-SMA
+ * force (density pass, then force pass), an FP64 velocity-Verlet step with a
+ * Langevin thermostat and a rigid-grip pull, and per-wire FP64 observables.
+ *
+ * Method (French, Pervaje, Santos, Iacovella, Cummings, arXiv:1311.3890):
+ *   Eq. 1   E_B^i = -sqrt(rho_i),  rho_i = sum_j xi^2 exp(-2q (r_ij/r0 - 1))
+ *   Eq. 2   E_R^i = sum_j A exp(-p (r_ij/r0 - 1))
+ *   Eq. 3   E_C   = sum_i (E_B^i + E_R^i), pairs with r_ij <= r_cut only
+ *   Methods "TB-SMA potential": the force needs rho_i and rho_j, so it is
+ *           computed in two passes over each atom's neighbours.
+ *   Methods "Simulation details": velocity Verlet, dt = 2 fs, two rigid
+ *           gripping layers per end pulled apart along [100].
+ *   Eq. 4   strain = (L - L0)/L0;  Eq. 5  virial stress sigma_xx.
+ *   Results "TB-SMA benchmarks": Verlet list with a buffer (skin) radius.
+ *
+ * Units: Angstrom, eV, amu, fs.  Strain rate in 1/s, temperature in K,
+ * Langevin friction gamma in 1/fs.
+ *
+ * Layout conventions:
+ *   - Positions x and velocities v are caller-owned DEVICE arrays of
+ *     3*N doubles in SoA order: x[0..N) = x-coordinates, x[N..2N) = y,
+ *     x[2N..3N) = z, N = total atoms of all wires.
+ *   - Wire w owns atoms [atom_offset, atom_offset + n_atoms); wires are
+ *     packed back to back in wire order (offset[0] = 0, offset[w+1] =
+ *     offset[w] + n[w]).  The library never reorders atoms.
+ *   - kind[i] (device uint8): 0 mobile, 1 left grip, 2 right grip.
+ *
+ * Ownership: the caller owns x, v, kind and the CUDA stream; the library
+ * keeps the pointers and never frees them, so they must outlive the
+ * context.  The library owns all other device memory (neighbour lists,
+ * cell lists, packed positions, forces), allocated in tbsma_init and freed
+ * in tbsma_destroy.
+ *
+ * Errors: every call returns a tbsma_status; nothing aborts, traps or
+ * prints.  tbsma_last_error() returns a text for the last failure.  Calls
+ * are enqueued on the context's stream and are asynchronous unless stated
+ * otherwise.  Per-wire faults (non-finite coordinates, list or cell
+ * overflow, fixed-point range) are recorded in a per-wire status word; the
+ * calls that synchronise (tbsma_step_nvt_pull, tbsma_build_neighbors with a
+ * counter, tbsma_reduce_observables, tbsma_force_check) return TBSMA_EWIRE
+ * or TBSMA_EOVERFLOW when any wire is flagged.
+ */
+#ifndef TBSMA_H
+#define TBSMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tbsma_ctx tbsma_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  TBSMA_OK = 0,
+  TBSMA_EINVAL = 1,    /* bad argument (null pointer, size, layout) */
+  TBSMA_ENOMEM = 2,    /* device allocation failed */
+  TBSMA_ECUDA = 3,     /* a CUDA runtime call failed */
+  TBSMA_EOVERFLOW = 4, /* neighbour-list or cell capacity exceeded */
+  TBSMA_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+  TBSMA_EWIRE = 6,     /* at least one wire has a non-zero status word */
+  TBSMA_ESTATE = 7     /* call not valid in the context's current state */
+} tbsma_status;
+
+/* Arithmetic of the pair kernels.  FP64: every pair term in double.  MIXED:
+ * pair geometry, exponentials, density and force accumulation in FP32 on
+ * exact fixed-point coordinate differences; positions, velocities,
+ * integration and all reductions stay FP64. */
+typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
+
+/* Per-wire status bits. */
+#define TBSMA_WIRE_NONFINITE 1u     /* NaN/Inf position or velocity */
+#define TBSMA_WIRE_NBR_OVERFLOW 2u  /* an atom has more neighbours than the list holds */
+#define TBSMA_WIRE_CELL_OVERFLOW 4u /* a cell holds more atoms than its capacity */
+#define TBSMA_WIRE_RANGE 8u         /* an atom left the fixed-point range (+-1024 A of the wire centre) */
+
+/* TB-SMA parameters (Table 1; r_cut after Eq. 3), list skin and mass.
+ * Au: A = 0.2061 eV, xi = 1.790 eV, p = 10.229, q = 4.036, r0 = 2.884 A
+ * (the nearest-neighbour distance; Table 1 prints the lattice constant
+ * 4.079 A in that column), r_cut = 5.8 A, r_skin = 0.29 A, mass = 196.966569. */
+typedef struct {
+  double A, xi, p, q, r0, r_cut, r_skin, mass;
+} tbsma_params;
+
+/* One wire of the batch (host array passed to tbsma_init). */
+typedef struct {
+  int64_t atom_offset; /* first atom */
+  int32_t n_atoms;     /* atoms in the wire (>= 1) */
+  int32_t reserved;    /* must be 0 */
+  double L0;           /* initial length, A (Eq. 4) */
+  double strain_rate;  /* 1/s; each grip moves strain_rate*L0*dt/2 per step */
+  double temperature;  /* K, Langevin target */
+  double gamma;        /* 1/fs Langevin friction; 0 = NVE velocity Verlet */
+  uint64_t seed;       /* Philox key of the wire's thermostat */
+} tbsma_wire;
+
+/* Per-wire observables (Eq. 3-5), FP64 reductions. */
+typedef struct {
+  int64_t step;       /* steps done since init */
+  double strain;      /* Eq. 4 */
+  double e_pot;       /* E_C of the wire, eV (Eq. 3) */
+  double e_kin;       /* 1/2 m sum_mobile |v|^2, eV */
+  double temp;        /* 2 E_kin / (3 N_mobile k_B), K */
+  double sigma_xx;    /* Eq. 5, eV/A^3 (x 160.2177 for GPa) */
+  double virial_xx;   /* sum_i 1/2 sum_j r_x,ij F_x,ij, eV */
+  int32_t n_rebuilds; /* neighbour-list rebuilds of this wire during steps */
+  int32_t status;     /* TBSMA_WIRE_* bits */
+} tbsma_obs;
+
+/* Mixed-precision vs FP64 force comparison of one wire (same positions, same list). */
+typedef struct {
+  double max_err_scaled; /* max_i |F_i^mixed - F_i^fp64| / S_i, S_i = sum_j |f_ij| */
+  double max_err_raw;    /* max_i |F_i^mixed - F_i^fp64| / |F_i^fp64| */
+  double norm_err;       /* ||F^mixed - F^fp64||_2 / ||F^fp64||_2 over the wire */
+  double max_abs_err;    /* max_i |F_i^mixed - F_i^fp64|, eV/A */
+} tbsma_fcheck;
+
+/* Create a context for n_wires wires packed in x, v, kind (device, see
+ * layout above) and enqueue on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  Allocates every device buffer, sizes a fixed
+ * cell grid per wire from its initial bounding box (margins for strain up to
+ * 1.0 along x; atoms outside are clamped into edge cells), builds all
+ * neighbour lists and computes the initial forces.  Synchronises.
+ * Errors: EINVAL (null pointers, n_wires < 1, wires not packed back to back,
+ * bad parameters), ENOMEM, ECUDA.  On error *out is NULL. */
+tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, int32_t n_wires,
+                        const tbsma_wire* wires, double* x, double* v, const uint8_t* kind,
+                        void* cuda_stream, tbsma_ctx** out);
+
+/* Draw initial velocities (Methods: random Gaussian velocities per
+ * trajectory): mobile atoms get Philox4x32-10 Gaussians at the wire's
+ * temperature (key = seed, counter = (atom index in wire, 0, 0, 1)), the
+ * mobile centre-of-mass velocity is removed and the velocities are scaled
+ * to the exact target temperature; grip atoms get 0.  Writes v. */
+tbsma_status tbsma_init_velocities(tbsma_ctx* ctx);
+
+/* Re-read x (after the caller changed positions), then rebuild the lists of
+ * the wires whose atoms moved more than r_skin/2 since their last build, or
+ * of all wires if force_all != 0.  If n_rebuilt is non-NULL it receives the
+ * number of wires rebuilt and the call synchronises. */
+tbsma_status tbsma_build_neighbors(tbsma_ctx* ctx, int32_t force_all, int32_t* n_rebuilt);
+
+/* Forces at the current positions (rebuilding lists first if needed), in
+ * SoA 3*N device arrays.  f32_out (nullable) receives the MIXED-precision
+ * forces, f64_out (nullable) the FP64 forces, both on the same list; either
+ * precision can be asked of any context.  The context's own force buffer
+ * (used by the next step) is refreshed in the context's precision. */
+tbsma_status tbsma_compute_forces(tbsma_ctx* ctx, float* f32_out, double* f64_out);
+
+/* Per-atom energies E_B^i + E_R^i (Eq. 1-2) and axial pair virials
+ * 1/2 sum_j r_x,ij F_x,ij at the current positions, context precision,
+ * into device arrays of N doubles (either nullable). */
+tbsma_status tbsma_atom_energies(tbsma_ctx* ctx, double* e_out, double* w_out);
+
+/* Advance every wire by n_steps steps of dt_fs: B A O A (mobile atoms; grips
+ * shifted rigidly), displacement check, list rebuild of flagged wires,
+ * density pass, force pass, B.  Replays a captured CUDA graph; the first
+ * call with a new dt captures it.  Synchronises at the end to read the
+ * wires' status words.  Errors: EINVAL (n_steps < 0, dt_fs <= 0), EWIRE,
+ * EOVERFLOW, ECUDA. */
+tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
+
+/* Per-wire observables at the current state into out[n_wires] (host).
+ * Synchronises.  Returns EWIRE if any wire's status is non-zero (out is
+ * still filled). */
+tbsma_status tbsma_reduce_observables(tbsma_ctx* ctx, tbsma_obs* out);
+
+/* Compare MIXED and FP64 forces at the current positions on the same list,
+ * per wire, into out[n_wires] (host).  Synchronises. */
+tbsma_status tbsma_force_check(tbsma_ctx* ctx, tbsma_fcheck* out);
+
+/* Copy the state from / to host buffers of 3*N doubles (SoA, as x and v).
+ * Either pointer may be NULL to skip it.  Upload re-packs positions,
+ * rebuilds the lists of wires that moved past the skin and recomputes the
+ * forces; download synchronises.  Pinned host memory makes the copies
+ * asynchronous DMA. */
+tbsma_status tbsma_upload_state(tbsma_ctx* ctx, const double* x_host, const double* v_host);
+tbsma_status tbsma_download_state(tbsma_ctx* ctx, double* x_host, double* v_host);
+
+/* Per-wire status words (TBSMA_WIRE_* bits) into status_host[n_wires].
+ * Synchronises. */
+tbsma_status tbsma_get_wire_status(tbsma_ctx* ctx, int32_t* status_host);
+
+/* Neighbour lists (device): n_nbr[N] and nbr[N * cap] (row i holds atom i's
+ * neighbours within r_cut + r_skin, in the library's deterministic order;
+ * unused entries undefined).  cap must equal tbsma_nbr_capacity(ctx). */
+int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
+tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, int32_t cap);
+
+/* Launch shape of the pair kernels: lanes cooperating on one atom
+ * (4, 8, 16 or 32) and threads per block (64..256, multiple of 32).
+ * Invalidates captured graphs. */
+tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t lanes_per_atom, int32_t block_threads);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device, as the thermostat
+ * uses it: out[4i..4i+4) = philox(ctr[4i..4i+4), key[2i..2i+2)).  Device
+ * arrays; enqueued on cuda_stream. */
+tbsma_status tbsma_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n,
+                                 uint32_t* out, void* cuda_stream);
+
+/* The thermostat's Gaussian triples on the device: for each atoms[i],
+ * out[3i..3i+3) = Box-Muller normals of philox(counter = (atoms[i], step lo,
+ * step hi, tag), key = (seed lo, seed hi)); precision selects the
+ * FP64 or FP32 Box-Muller used by that path. */
+tbsma_status tbsma_normals(uint64_t seed, const uint32_t* atoms, int64_t n, int64_t step,
+                           uint32_t tag, tbsma_precision precision, double* out,
+                           void* cuda_stream);
+
+const char* tbsma_last_error(const tbsma_ctx* ctx);
+void tbsma_destroy(tbsma_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBSMA_H */

@@ -1,0 +1,114 @@
+// Device-side building blocks of the TB-SMA wire MD path: layouts shared by
+// the kernels, the counter-based generator and its Gaussian transform.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tbsma {
+
+// ---------------------------------------------------------------- constants
+// CODATA 2018.  1 amu*A^2/fs^2 in eV = amu[kg] * 1e10 / e[J].
+constexpr double kBoltzmann = 8.617333262e-5;  // eV/K
+constexpr double kAmuKg = 1.66053906660e-27;
+constexpr double kElectronVoltJ = 1.602176634e-19;
+constexpr double kMvv2e = kAmuKg * 1.0e10 / kElectronVoltJ;
+
+// Fixed-point positions: 2^21 units per Angstrom relative to the wire centre.
+// A neighbour difference below 8 A (2^24 units) converts to float exactly.
+constexpr double kFixedScale = 2097152.0;           // 2^21
+constexpr float kFixedInv = 4.76837158203125e-07f;  // 2^-21
+constexpr double kFixedRange = 1023.99;             // |x - centre| limit, A
+
+constexpr uint32_t kWireNonFinite = 1u;
+constexpr uint32_t kWireNbrOverflow = 2u;
+constexpr uint32_t kWireCellOverflow = 4u;
+constexpr uint32_t kWireRange = 8u;
+
+constexpr int kCellCap = 32;  // atoms per cell (one per lane in the sort and build)
+
+// meta word of an atom: wire index << 2 | kind (0 mobile, 1 left grip, 2 right grip)
+__host__ __device__ __forceinline__ uint32_t meta_wire(uint32_t m) { return m >> 2; }
+__host__ __device__ __forceinline__ uint32_t meta_kind(uint32_t m) { return m & 3u; }
+
+// Static description of one wire (set at init).
+struct WireDev {
+  int64_t offset;
+  int32_t n;
+  int32_t n_mobile;
+  double origin[3];  // fixed-point origin = centre of the initial bounding box
+  double glo[3];     // cell-grid lower corner relative to the origin
+  double einv[3];    // 1 / cell edge
+  int32_t nc[3];     // cells per direction
+  int32_t pad;
+  int64_t cell_base;  // index of the wire's first cell
+  uint64_t seed;
+  double L0, strain_rate, temperature, gamma;
+};
+
+// Per-wire constants that depend on dt.
+struct WireDyn {
+  double c1;     // exp(-gamma dt)
+  double c2sig;  // sqrt(1 - c1^2) * sqrt(kT/m)  (A/fs)
+  double delta;  // grip displacement per step, A
+  double pad;
+};
+
+// Constants of the pair kernels (Eq. 1-2 rewritten with exp2).
+struct PairConsts {
+  // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-p s} = 2^(-kp (r - r0))
+  float rc2f, r0f, kgf, kpf, xi2f, Af, fpf, fgf;  // fpf = 2 p A / r0, fgf = 2 q xi^2 / r0
+  // FP64 path
+  double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
+};
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// -> 64-bit multiplies on counter words 0 and 2, the high halves xored into
+// the other two words with the round key, the key advanced by the Weyl
+// increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 thermostat_bits(uint64_t seed, uint32_t atom, uint64_t step,
+                                                 uint32_t tag) {
+  return philox4x32_10(make_uint4(atom, (uint32_t)step, (uint32_t)(step >> 32), tag),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Box-Muller: u = (bits + 1/2) 2^-32 in (0,1); (u0,u1) -> n0, n1; (u2,u3) -> n2.
+__device__ __forceinline__ double3 normals3_f64(uint4 b) {
+  const double s = 2.3283064365386962890625e-10;  // 2^-32
+  const double two_pi = 6.283185307179586476925286766559;
+  const double u0 = ((double)b.x + 0.5) * s, u1 = ((double)b.y + 0.5) * s;
+  const double u2 = ((double)b.z + 0.5) * s, u3 = ((double)b.w + 0.5) * s;
+  const double a = sqrt(-2.0 * log(u0)), c = sqrt(-2.0 * log(u2));
+  double sn, cs, sn2, cs2;
+  sincos(two_pi * u1, &sn, &cs);
+  sincos(two_pi * u3, &sn2, &cs2);
+  return make_double3(a * cs, a * sn, c * cs2);
+}
+
+__device__ __forceinline__ float3 normals3_f32(uint4 b) {
+  const float s = 2.3283064365386963e-10f, h = 1.16415321826934814e-10f;  // 2^-32, 2^-33
+  const float u0 = fmaf((float)b.x, s, h), u1 = fmaf((float)b.y, s, h);
+  const float u2 = fmaf((float)b.z, s, h), u3 = fmaf((float)b.w, s, h);
+  const float a = sqrtf(-2.0f * logf(u0)), c = sqrtf(-2.0f * logf(u2));
+  float sn, cs, sn2, cs2;
+  sincospif(2.0f * u1, &sn, &cs);
+  sincospif(2.0f * u3, &sn2, &cs2);
+  return make_float3(a * cs, a * sn, c * cs2);
+}
+
+}  // namespace tbsma

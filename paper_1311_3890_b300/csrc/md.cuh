@@ -1,0 +1,414 @@
+// Integrator, thermostat, grips, packing and per-wire reductions.
+//
+// Methods, "Simulation details": velocity Verlet with dt = 2 fs; two rigid
+// gripping layers at each end displaced in opposite directions along [100];
+// random Gaussian initial velocities.  The thermostat is Langevin, applied
+// as the O step of a B A O A B splitting (gamma = 0 is plain velocity
+// Verlet), with Gaussian noise from a counter-based Philox4x32-10 stream
+// keyed by the wire's seed and counted by (atom index in wire, step, tag).
+//
+// Positions and velocities are FP64 throughout; the pair kernels read a
+// packed copy written here (int4 fixed point for MIXED, double4_32a for FP64).
+#pragma once
+
+#include "device.cuh"
+#include "../../include/tbsma.h"
+
+namespace tbsma {
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  // fixed-order tree over the block (blockDim.x a power of two <= 1024)
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  const T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (t < s) sh[t] = sh[t + s] > sh[t] ? sh[t + s] : sh[t];
+    __syncthreads();
+  }
+  const T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Block per wire: meta[i] = wire << 2 | kind[i].
+__global__ void k_meta(int W, const WireDev* __restrict__ wd, const uint8_t* __restrict__ kind,
+                       uint32_t* __restrict__ meta) {
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const int64_t o = wd[w].offset;
+    for (int a = threadIdx.x; a < wd[w].n; a += blockDim.x)
+      meta[o + a] = ((uint32_t)w << 2) | (uint32_t)(kind[o + a] & 3u);
+  }
+}
+
+// Block per wire: bounding box and mobile count, out[w*7 ..] = lo xyz, hi xyz, n_mobile.
+__global__ void __launch_bounds__(256)
+    k_bbox(int W, const tbsma_wire* __restrict__ wires, const double* __restrict__ x, int64_t N,
+           const uint8_t* __restrict__ kind, double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const int64_t o = wires[w].atom_offset;
+    const int n = wires[w].n_atoms;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    double nm = 0.0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+      for (int d = 0; d < 3; ++d) {
+        const double v = x[d * N + o + a];
+        lo[d] = fmin(lo[d], v);
+        hi[d] = fmax(hi[d], v);
+      }
+      nm += kind[o + a] == 0 ? 1.0 : 0.0;
+    }
+    for (int d = 0; d < 3; ++d) {
+      const double l = -block_max(-lo[d], sh);
+      const double h = block_max(hi[d], sh);
+      if (threadIdx.x == 0) {
+        out[w * 7 + d] = l;
+        out[w * 7 + 3 + d] = h;
+      }
+    }
+    const double m = block_sum(nm, sh);
+    if (threadIdx.x == 0) out[w * 7 + 6] = m;
+  }
+}
+
+__device__ __forceinline__ int to_fixed(double rel, uint32_t& bad) {
+  if (!(fabs(rel) < kFixedRange)) {
+    bad = 1;
+    rel = rel != rel ? 0.0 : fmin(fmax(rel, -kFixedRange), kFixedRange);
+  }
+  return __double2int_rn(rel * kFixedScale);
+}
+
+template <int PREC>
+__device__ __forceinline__ void pack_and_check(int64_t i, uint32_t m, const WireDev& w, double px,
+                                               double py, double pz, int4* xq, double4_32a* xd,
+                                               const int4* xq_b, const double4_32a* xd_b,
+                                               double half_skin2, int check, int32_t* flag,
+                                               uint32_t* wire_status) {
+  const uint32_t wi = meta_wire(m);
+  bool moved = false;
+  if (PREC == TBSMA_MIXED) {
+    uint32_t bad = 0;
+    const int4 q = make_int4(to_fixed(px - w.origin[0], bad), to_fixed(py - w.origin[1], bad),
+                             to_fixed(pz - w.origin[2], bad), (int)m);
+    if (bad) atomicOr(&wire_status[wi], kWireRange);
+    xq[i] = q;
+    if (check) {
+      const int4 b = xq_b[i];
+      const float dx = (float)(q.x - b.x) * kFixedInv, dy = (float)(q.y - b.y) * kFixedInv,
+                  dz = (float)(q.z - b.z) * kFixedInv;
+      moved = dx * dx + dy * dy + dz * dz > (float)half_skin2;
+    }
+  } else {
+    const double4_32a q = make_double4_32a(px, py, pz, __longlong_as_double((long long)m));
+    xd[i] = q;
+    if (check) {
+      const double4_32a b = xd_b[i];
+      const double dx = q.x - b.x, dy = q.y - b.y, dz = q.z - b.z;
+      moved = dx * dx + dy * dy + dz * dz > half_skin2;
+    }
+  }
+  if (moved) flag[wi] = 1;
+}
+
+// Pack the caller's positions for the pair kernels (both layouts), and, if
+// `check`, flag wires whose atoms moved past r_skin/2 since their last build.
+template <int PREC>
+__global__ void k_pack(int64_t N, const double* __restrict__ x, const uint32_t* __restrict__ meta,
+                       const WireDev* __restrict__ wd, int4* xq, double4_32a* xd, const int4* xq_b,
+                       const double4_32a* xd_b, double half_skin2, int check, int32_t* flag,
+                       uint32_t* wire_status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t m = meta[i];
+  const WireDev& w = wd[meta_wire(m)];
+  const double px = x[i], py = x[N + i], pz = x[2 * N + i];
+  if (!isfinite(px) || !isfinite(py) || !isfinite(pz))
+    atomicOr(&wire_status[meta_wire(m)], kWireNonFinite);
+  // the context's own layout carries the displacement check; the other is a plain copy
+  pack_and_check<PREC>(i, m, w, px, py, pz, xq, xd, xq_b, xd_b, half_skin2, check, flag,
+                       wire_status);
+  if (PREC == TBSMA_MIXED) {
+    xd[i] = make_double4_32a(px, py, pz, __longlong_as_double((long long)m));
+  } else {
+    uint32_t bad = 0;
+    xq[i] = make_int4(to_fixed(px - w.origin[0], bad), to_fixed(py - w.origin[1], bad),
+                      to_fixed(pz - w.origin[2], bad), (int)m);
+    if (bad) atomicOr(&wire_status[meta_wire(m)], kWireRange);
+  }
+}
+
+// One step's B(kick) A O A for mobile atoms, rigid shift for grips, then
+// pack + displacement check.  KICK = 1: half kick dt/2 (first step of a
+// sequence); KICK = 2: the previous step's closing half kick merged with
+// this step's opening one (both use the same force).
+template <int PREC, int KICK>
+__global__ void __launch_bounds__(256)
+    k_integrate(int64_t N, double* __restrict__ x, double* __restrict__ v,
+                const float* __restrict__ f32, const double* __restrict__ f64,
+                const uint32_t* __restrict__ meta, const WireDev* __restrict__ wd,
+                const WireDyn* __restrict__ wdyn, double dt, double inv_m,
+                const int64_t* __restrict__ step_counter, int4* xq, double4_32a* xd,
+                const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
+                int32_t* flag, uint32_t* wire_status, double* d_grip) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t m = meta[i];
+  const uint32_t wi = meta_wire(m), kind = meta_kind(m);
+  const WireDev& w = wd[wi];
+  const WireDyn dy = wdyn[wi];
+  double px = x[i], py = x[N + i], pz = x[2 * N + i];
+  double vx, vy, vz;
+  if (kind == 0) {
+    vx = v[i];
+    vy = v[N + i];
+    vz = v[2 * N + i];
+    double fx, fy, fz;
+    if (PREC == TBSMA_MIXED) {
+      fx = f32[i];
+      fy = f32[N + i];
+      fz = f32[2 * N + i];
+    } else {
+      fx = f64[i];
+      fy = f64[N + i];
+      fz = f64[2 * N + i];
+    }
+    const double hk = 0.5 * KICK * dt * inv_m;
+    vx += hk * fx;
+    vy += hk * fy;
+    vz += hk * fz;
+    const double hd = 0.5 * dt;
+    px += hd * vx;
+    py += hd * vy;
+    pz += hd * vz;
+    if (dy.c2sig != 0.0 || dy.c1 != 1.0) {
+      double nx = 0.0, ny = 0.0, nz = 0.0;
+      if (dy.c2sig != 0.0) {
+        const uint4 b = thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step_counter[0], 0u);
+        if (PREC == TBSMA_MIXED) {
+          const float3 g = normals3_f32(b);
+          nx = g.x;
+          ny = g.y;
+          nz = g.z;
+        } else {
+          const double3 g = normals3_f64(b);
+          nx = g.x;
+          ny = g.y;
+          nz = g.z;
+        }
+      }
+      vx = dy.c1 * vx + dy.c2sig * nx;
+      vy = dy.c1 * vy + dy.c2sig * ny;
+      vz = dy.c1 * vz + dy.c2sig * nz;
+    }
+    px += hd * vx;
+    py += hd * vy;
+    pz += hd * vz;
+  } else {
+    px += (kind == 1) ? -dy.delta : dy.delta;
+    vx = vy = vz = 0.0;
+  }
+  x[i] = px;
+  x[N + i] = py;
+  x[2 * N + i] = pz;
+  v[i] = vx;
+  v[N + i] = vy;
+  v[2 * N + i] = vz;
+  if (!isfinite(px + py + pz + vx + vy + vz)) atomicOr(&wire_status[wi], kWireNonFinite);
+  pack_and_check<PREC>(i, m, w, px, py, pz, xq, xd, xq_b, xd_b, half_skin2, 1, flag, wire_status);
+  if (i == w.offset) d_grip[wi] += dy.delta;
+}
+
+// Closing half kick of the last step of a sequence.
+template <int PREC>
+__global__ void k_half_kick(int64_t N, double* __restrict__ v, const float* __restrict__ f32,
+                            const double* __restrict__ f64, const uint32_t* __restrict__ meta,
+                            double hk) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N || meta_kind(meta[i]) != 0) return;
+  for (int d = 0; d < 3; ++d) {
+    const double f = PREC == TBSMA_MIXED ? (double)f32[d * N + i] : f64[d * N + i];
+    v[d * N + i] += hk * f;
+  }
+}
+
+// Block per wire: initial velocities (Philox tag 1), mobile COM removed,
+// scaled to the exact target temperature.
+__global__ void __launch_bounds__(256)
+    k_init_velocities(int W, const WireDev* __restrict__ wd, const uint32_t* __restrict__ meta,
+                      int64_t N, double* __restrict__ v, double m_e) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    const double sig = sqrt(kBoltzmann * wr.temperature / m_e);
+    double s[3] = {0.0, 0.0, 0.0}, nm = 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      if (meta_kind(meta[i]) != 0) {
+        v[i] = v[N + i] = v[2 * N + i] = 0.0;
+        continue;
+      }
+      const double3 g = normals3_f64(thermostat_bits(wr.seed, (uint32_t)a, 0, 1u));
+      v[i] = sig * g.x;
+      v[N + i] = sig * g.y;
+      v[2 * N + i] = sig * g.z;
+      s[0] += v[i];
+      s[1] += v[N + i];
+      s[2] += v[2 * N + i];
+      nm += 1.0;
+    }
+    const double n_mob = block_sum(nm, sh);
+    double mean[3];
+    for (int d = 0; d < 3; ++d) mean[d] = n_mob > 0 ? block_sum(s[d], sh) / n_mob : 0.0;
+    double v2 = 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      if (meta_kind(meta[i]) != 0) continue;
+      for (int d = 0; d < 3; ++d) {
+        const double u = v[d * N + i] - mean[d];
+        v[d * N + i] = u;
+        v2 += u * u;
+      }
+    }
+    const double ekin = 0.5 * m_e * block_sum(v2, sh);
+    const double target = 1.5 * n_mob * kBoltzmann * wr.temperature;
+    const double scale = ekin > 0.0 ? sqrt(target / ekin) : 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      if (meta_kind(meta[i]) != 0) continue;
+      for (int d = 0; d < 3; ++d) v[d * N + i] *= scale;
+    }
+  }
+}
+
+// Block per wire: Eq. 3-5 reductions in FP64 with a fixed summation order.
+__global__ void __launch_bounds__(256)
+    k_observe(int W, const WireDev* __restrict__ wd, const uint32_t* __restrict__ meta, int64_t N,
+              const double* __restrict__ e_atom, const double* __restrict__ w_atom,
+              const double* __restrict__ v, const double* __restrict__ d_grip,
+              const int32_t* __restrict__ n_rebuilds, const uint32_t* __restrict__ wire_status,
+              int64_t steps, double m_e, double v_atom, tbsma_obs* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    double e = 0.0, vir = 0.0, v2 = 0.0, vx2 = 0.0, nm = 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      e += e_atom[i];
+      vir += w_atom[i];
+      if (meta_kind(meta[i]) == 0) {
+        const double ux = v[i], uy = v[N + i], uz = v[2 * N + i];
+        v2 += ux * ux + uy * uy + uz * uz;
+        vx2 += ux * ux;
+        nm += 1.0;
+      }
+    }
+    e = block_sum(e, sh);
+    vir = block_sum(vir, sh);
+    v2 = block_sum(v2, sh);
+    vx2 = block_sum(vx2, sh);
+    nm = block_sum(nm, sh);
+    if (threadIdx.x == 0) {
+      tbsma_obs o;
+      o.step = steps;
+      o.strain = 2.0 * d_grip[w] / wr.L0;
+      o.e_pot = e;
+      o.e_kin = 0.5 * m_e * v2;
+      o.temp = nm > 0 ? 2.0 * o.e_kin / (3.0 * nm * kBoltzmann) : 0.0;
+      o.sigma_xx = (vir - m_e * vx2) / (v_atom * wr.n);
+      o.virial_xx = vir;
+      o.n_rebuilds = n_rebuilds[w];
+      o.status = (int32_t)wire_status[w];
+      out[w] = o;
+    }
+  }
+}
+
+// Block per wire: mixed vs FP64 force errors.
+__global__ void __launch_bounds__(256)
+    k_force_check(int W, const WireDev* __restrict__ wd, int64_t N, const float* __restrict__ f32,
+                  const double* __restrict__ f64, const double* __restrict__ s_atom,
+                  tbsma_fcheck* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    double es = 0.0, er = 0.0, ea = 0.0, d2 = 0.0, f2 = 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      double dd = 0.0, ff = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double r = f64[d * N + i];
+        const double e = (double)f32[d * N + i] - r;
+        dd += e * e;
+        ff += r * r;
+      }
+      const double de = sqrt(dd), fm = sqrt(ff);
+      if (s_atom[i] > 0.0) es = fmax(es, de / s_atom[i]);
+      if (fm > 0.0) er = fmax(er, de / fm);
+      ea = fmax(ea, de);
+      d2 += dd;
+      f2 += ff;
+    }
+    es = block_max(es, sh);
+    er = block_max(er, sh);
+    ea = block_max(ea, sh);
+    d2 = block_sum(d2, sh);
+    f2 = block_sum(f2, sh);
+    if (threadIdx.x == 0) {
+      tbsma_fcheck o;
+      o.max_err_scaled = es;
+      o.max_err_raw = er;
+      o.norm_err = f2 > 0.0 ? sqrt(d2 / f2) : 0.0;
+      o.max_abs_err = ea;
+      out[w] = o;
+    }
+  }
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                         int64_t n, uint32_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]),
+                                make_uint2(key[2 * i], key[2 * i + 1]));
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+template <int PREC>
+__global__ void k_normals(uint64_t seed, const uint32_t* __restrict__ atoms, int64_t n,
+                          uint64_t step, uint32_t tag, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 b = thermostat_bits(seed, atoms[i], step, tag);
+  if (PREC == TBSMA_MIXED) {
+    const float3 g = normals3_f32(b);
+    out[3 * i] = g.x;
+    out[3 * i + 1] = g.y;
+    out[3 * i + 2] = g.z;
+  } else {
+    const double3 g = normals3_f64(b);
+    out[3 * i] = g.x;
+    out[3 * i + 1] = g.y;
+    out[3 * i + 2] = g.z;
+  }
+}
+
+}  // namespace tbsma

@@ -1,0 +1,260 @@
+// Per-wire cell lists and Verlet neighbour lists (Results, "TB-SMA
+// benchmarks": a neighbour list with buffer radius r_buff; atoms kept in
+// their [100] order, no re-sorting).
+//
+// Only wires whose rebuild flag is set are processed.  k_nl_plan turns the
+// flags into a compact work list (flagged wires with prefix sums of their
+// cells and atoms); the other kernels stride over that list, so a step in
+// which no wire moved far enough costs four near-empty launches.
+//
+// Cells: a fixed grid per wire (edge >= list radius), atoms outside the grid
+// clamped into edge cells (clamping is monotone, so two atoms within one
+// edge of each other still land in adjacent cells).  Each cell holds up to
+// kCellCap atom indices, sorted ascending so that the list order, and hence
+// every force sum, is deterministic.
+#pragma once
+
+#include "device.cuh"
+
+namespace tbsma {
+
+struct NlWork {
+  int32_t* flag;        // [W] rebuild requested
+  int32_t* wl_wire;     // [W] flagged wires
+  int64_t* wl_cell;     // [W+1] prefix of their cell counts
+  int64_t* wl_atom;     // [W+1] prefix of their atom counts
+  int32_t* n_flagged;   // [1]
+  int32_t* n_rebuilds;  // [W]
+};
+
+// Binary search: largest k < nf with pre[k] <= idx.
+__device__ __forceinline__ int wl_find(const int64_t* pre, int nf, int64_t idx) {
+  int lo = 0, hi = nf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One block of 1024 threads: compact flagged wires, clear their flags,
+// count the rebuild, and (in the step loop) advance the step counter.
+__global__ void __launch_bounds__(1024)
+    k_nl_plan(int W, NlWork nw, const WireDev* __restrict__ wd, int force_all, int count_rebuild,
+              int64_t* step_counter) {
+  __shared__ int64_t s_cells[1024], s_atoms[1024];
+  __shared__ int32_t s_cnt[1024];
+  const int t = threadIdx.x;
+  const int chunk = (W + 1023) / 1024;
+  const int w0 = min(W, t * chunk), w1 = min(W, w0 + chunk);
+  int64_t cells = 0, atoms = 0;
+  int cnt = 0;
+  for (int w = w0; w < w1; ++w) {
+    if (force_all || nw.flag[w]) {
+      ++cnt;
+      cells += (int64_t)wd[w].nc[0] * wd[w].nc[1] * wd[w].nc[2];
+      atoms += wd[w].n;
+    }
+  }
+  s_cells[t] = cells;
+  s_atoms[t] = atoms;
+  s_cnt[t] = cnt;
+  __syncthreads();
+  // inclusive Hillis-Steele scan over the 1024 partial sums
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t c = 0, a = 0;
+    int k = 0;
+    if (t >= off) {
+      c = s_cells[t - off];
+      a = s_atoms[t - off];
+      k = s_cnt[t - off];
+    }
+    __syncthreads();
+    s_cells[t] += c;
+    s_atoms[t] += a;
+    s_cnt[t] += k;
+    __syncthreads();
+  }
+  int64_t c_pre = s_cells[t] - cells, a_pre = s_atoms[t] - atoms;
+  int k = s_cnt[t] - cnt;
+  for (int w = w0; w < w1; ++w) {
+    if (force_all || nw.flag[w]) {
+      nw.wl_wire[k] = w;
+      nw.wl_cell[k] = c_pre;
+      nw.wl_atom[k] = a_pre;
+      c_pre += (int64_t)wd[w].nc[0] * wd[w].nc[1] * wd[w].nc[2];
+      a_pre += wd[w].n;
+      ++k;
+      nw.flag[w] = 0;
+      if (count_rebuild) nw.n_rebuilds[w] += 1;
+    }
+  }
+  if (t == 1023) {
+    nw.n_flagged[0] = s_cnt[1023];
+    nw.wl_cell[s_cnt[1023]] = s_cells[1023];
+    nw.wl_atom[s_cnt[1023]] = s_atoms[1023];
+  }
+  if (t == 0 && step_counter) step_counter[0] += 1;
+}
+
+__global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* cell_count) {
+  const int nf = nw.n_flagged[0];
+  if (nf == 0) return;
+  const int64_t total = nw.wl_cell[nf];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = wl_find(nw.wl_cell, nf, idx);
+    const WireDev& w = wd[nw.wl_wire[k]];
+    cell_count[w.cell_base + (idx - nw.wl_cell[k])] = 0;
+  }
+}
+
+__device__ __forceinline__ int cell_coord(double rel, double lo, double einv, int n) {
+  const int c = (int)floor((rel - lo) * einv);
+  return min(max(c, 0), n - 1);
+}
+
+// Bin the atoms of flagged wires (positions from the caller's FP64 array).
+__global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+                         int64_t N, int32_t* cell_count, int32_t* cell_atoms,
+                         uint32_t* wire_status) {
+  const int nf = nw.n_flagged[0];
+  if (nf == 0) return;
+  const int64_t total = nw.wl_atom[nf];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = wl_find(nw.wl_atom, nf, idx);
+    const int wi = nw.wl_wire[k];
+    const WireDev& w = wd[wi];
+    const int64_t i = w.offset + (idx - nw.wl_atom[k]);
+    const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0]);
+    const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1]);
+    const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
+    const int64_t c = w.cell_base + ((int64_t)cx * w.nc[1] + cy) * w.nc[2] + cz;
+    const int slot = atomicAdd(&cell_count[c], 1);
+    if (slot < kCellCap) cell_atoms[c * kCellCap + slot] = (int32_t)i;
+    else atomicOr(&wire_status[wi], kWireCellOverflow);
+  }
+}
+
+// Warp per flagged cell: sort its members ascending (rank by counting).
+__global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32_t* cell_count,
+                          int32_t* cell_atoms) {
+  const int nf = nw.n_flagged[0];
+  if (nf == 0) return;
+  const int64_t total = nw.wl_cell[nf];
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
+       idx += warps) {
+    const int k = wl_find(nw.wl_cell, nf, idx);
+    const int64_t c = wd[nw.wl_wire[k]].cell_base + (idx - nw.wl_cell[k]);
+    const int cnt = min(cell_count[c], kCellCap);
+    const int32_t m = lane < cnt ? cell_atoms[c * kCellCap + lane] : INT32_MAX;
+    int rank = 0;
+    for (int l = 0; l < cnt; ++l) rank += (__shfl_sync(0xffffffffu, m, l) < m) ? 1 : 0;
+    __syncwarp();
+    if (lane < cnt) cell_atoms[c * kCellCap + rank] = m;
+  }
+}
+
+constexpr int kBuildWarps = 4;
+constexpr int kBuildMaxCand = 27 * kCellCap;
+constexpr size_t kBuildSmem = (size_t)kBuildWarps * kBuildMaxCand * (sizeof(int32_t) + sizeof(float4));
+
+// Warp per flagged cell.  The members of the 27 surrounding cells are staged
+// in shared memory (index + position relative to the cell centre, FP32),
+// then each atom of the cell tests all candidates 32 at a time; accepted
+// indices are compacted with a ballot and written with coalesced stores.
+// The packed position of each rebuilt atom is copied to the build snapshot
+// used by the displacement check.
+template <typename PosT>
+__global__ void __launch_bounds__(kBuildWarps * 32)
+    k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x, int64_t N,
+               const int32_t* __restrict__ cell_count, const int32_t* __restrict__ cell_atoms,
+               float rlist2, int32_t* nbr, int32_t* n_nbr, int cap, const PosT* __restrict__ pos,
+               PosT* pos_build, uint32_t* wire_status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* s_pos = reinterpret_cast<float4*>(smem_raw) + warp * kBuildMaxCand;
+  int32_t* s_idx = reinterpret_cast<int32_t*>(smem_raw + kBuildWarps * kBuildMaxCand * sizeof(float4)) +
+                   warp * kBuildMaxCand;
+
+  const int nf = nw.n_flagged[0];
+  if (nf == 0) return;
+  const int64_t total = nw.wl_cell[nf];
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
+       idx += warps) {
+    const int k = wl_find(nw.wl_cell, nf, idx);
+    const int wi = nw.wl_wire[k];
+    const WireDev& w = wd[wi];
+    const int64_t local = idx - nw.wl_cell[k];
+    const int cz = (int)(local % w.nc[2]);
+    const int cy = (int)((local / w.nc[2]) % w.nc[1]);
+    const int cx = (int)(local / ((int64_t)w.nc[2] * w.nc[1]));
+    const int64_t c = w.cell_base + local;
+    const int cnt_c = min(cell_count[c], kCellCap);
+    if (cnt_c == 0) continue;
+    // centre of this cell relative to the wire origin (staging reference)
+    const double ref0 = w.glo[0] + (cx + 0.5) / w.einv[0];
+    const double ref1 = w.glo[1] + (cy + 0.5) / w.einv[1];
+    const double ref2 = w.glo[2] + (cz + 0.5) / w.einv[2];
+    int ncand = 0, own_base = 0;
+    for (int ox = -1; ox <= 1; ++ox) {
+      const int nx = cx + ox;
+      if (nx < 0 || nx >= w.nc[0]) continue;
+      for (int oy = -1; oy <= 1; ++oy) {
+        const int ny = cy + oy;
+        if (ny < 0 || ny >= w.nc[1]) continue;
+        for (int oz = -1; oz <= 1; ++oz) {
+          const int nz = cz + oz;
+          if (nz < 0 || nz >= w.nc[2]) continue;
+          const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
+          const int cnt = min(cell_count[cn], kCellCap);
+          if (ox == 0 && oy == 0 && oz == 0) own_base = ncand;
+          if (lane < cnt) {
+            const int32_t j = cell_atoms[cn * kCellCap + lane];
+            s_idx[ncand + lane] = j;
+            s_pos[ncand + lane] = make_float4((float)(x[j] - w.origin[0] - ref0),
+                                              (float)(x[N + j] - w.origin[1] - ref1),
+                                              (float)(x[2 * N + j] - w.origin[2] - ref2), 0.f);
+          }
+          ncand += cnt;
+        }
+      }
+    }
+    __syncwarp();
+    for (int a = 0; a < cnt_c; ++a) {
+      const int32_t i = s_idx[own_base + a];
+      const float4 pi = s_pos[own_base + a];
+      int count = 0;
+      for (int base = 0; base < ncand; base += 32) {
+        const int kk = base + lane;
+        bool ok = false;
+        int32_t j = -1;
+        if (kk < ncand) {
+          j = s_idx[kk];
+          const float4 pj = s_pos[kk];
+          const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+          ok = (j != i) && (dx * dx + dy * dy + dz * dz <= rlist2);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int p = count + __popc(bal & ((1u << lane) - 1u));
+          if (p < cap) nbr[(int64_t)i * cap + p] = j;
+        }
+        count += __popc(bal);
+      }
+      if (lane == 0) {
+        n_nbr[i] = min(count, cap);
+        if (count > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
+        pos_build[i] = pos[i];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace tbsma

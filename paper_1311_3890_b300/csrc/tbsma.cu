@@ -1,0 +1,689 @@
+// Host side of the TB-SMA wire MD library: the C ABI of include/tbsma.h.
+//
+// One context holds a ragged batch of wires packed atom-wise.  Every kernel
+// runs over the flat atom array (pair, integrator) or over per-wire work
+// lists (neighbour build, reductions), so a batch of thousands of wires of
+// uneven size costs the same launches as a single wire.  The step loop is
+// captured once per (dt, chunk) as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tbsma.h"
+#include "device.cuh"
+#include "md.cuh"
+#include "nlist.cuh"
+#include "pair.cuh"
+
+using namespace tbsma;
+
+namespace {
+
+constexpr int kGraphChunk = 50;  // steps per captured graph
+constexpr int kDefaultCap = 64;  // neighbour-list row length
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  int steps = 0;
+};
+
+}  // namespace
+
+struct tbsma_ctx {
+  tbsma_params P{};
+  int prec = TBSMA_MIXED;
+  int W = 0;
+  int64_t N = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int sm_count = 148;
+  int tpa = 8, block = 128;
+  int cap = kDefaultCap;
+  int64_t n_cells = 0;
+  int64_t steps_done = 0;
+  double dt_dyn = -1.0;  // dt the per-wire dynamic table was filled for
+  std::string err;
+
+  // caller-owned
+  double* x = nullptr;
+  double* v = nullptr;
+  const uint8_t* kind = nullptr;
+
+  // library-owned device memory
+  std::vector<void*> allocs;
+  WireDev* wd = nullptr;
+  WireDyn* wdyn = nullptr;
+  uint32_t* meta = nullptr;
+  int4* xq = nullptr;
+  int4* xq_b = nullptr;
+  double4_32a* xd = nullptr;
+  double4_32a* xd_b = nullptr;
+  float* f32 = nullptr;
+  double* f64 = nullptr;
+  float* inv32 = nullptr;
+  double* inv64 = nullptr;
+  double* e_band = nullptr;
+  double* e_atom = nullptr;
+  double* w_atom = nullptr;
+  double* s_atom = nullptr;
+  int32_t* nbr = nullptr;
+  int32_t* n_nbr = nullptr;
+  int32_t* cell_count = nullptr;
+  int32_t* cell_atoms = nullptr;
+  int32_t* flag = nullptr;
+  int32_t* wl_wire = nullptr;
+  int64_t* wl_cell = nullptr;
+  int64_t* wl_atom = nullptr;
+  int32_t* n_flagged = nullptr;
+  int32_t* n_rebuilds = nullptr;
+  uint32_t* wire_status = nullptr;
+  double* d_grip = nullptr;
+  int64_t* step_counter = nullptr;
+  tbsma_obs* obs_d = nullptr;
+  tbsma_fcheck* fcheck_d = nullptr;
+
+  std::vector<WireDev> wires_h;
+  Graph graph;
+  double graph_dt = -1.0;
+
+  PairConsts pc{};
+  float rlist2 = 0.f;
+  double half_skin2 = 0.0;
+  double inv_m = 0.0;
+
+  NlWork nw() const { return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds}; }
+};
+
+namespace {
+
+tbsma_status fail(tbsma_ctx* c, tbsma_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+tbsma_status cuda_fail(tbsma_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TBSMA_ENOMEM : TBSMA_ECUDA;
+}
+
+#define TB_CUDA(c, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+  } while (0)
+
+template <typename T>
+tbsma_status alloc(tbsma_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return TBSMA_OK;
+}
+
+#define TB_TRY(expr)                      \
+  do {                                    \
+    tbsma_status s_ = (expr);             \
+    if (s_ != TBSMA_OK) return s_;        \
+  } while (0)
+
+inline unsigned grid_for(int64_t threads, int block) {
+  return (unsigned)std::max<int64_t>(1, (threads + block - 1) / block);
+}
+
+void fill_pair_consts(tbsma_ctx* c) {
+  const tbsma_params& P = c->P;
+  const double log2e = 1.4426950408889634073599246810019;
+  PairConsts& k = c->pc;
+  k.rc2f = (float)(P.r_cut * P.r_cut);
+  k.r0f = (float)P.r0;
+  k.kgf = (float)(2.0 * P.q / P.r0 * log2e);
+  k.kpf = (float)(P.p / P.r0 * log2e);
+  k.xi2f = (float)(P.xi * P.xi);
+  k.Af = (float)P.A;
+  k.fpf = (float)(2.0 * P.p * P.A / P.r0);
+  k.fgf = (float)(2.0 * P.q * P.xi * P.xi / P.r0);
+  k.rc2 = P.r_cut * P.r_cut;
+  k.r0 = P.r0;
+  k.A = P.A;
+  k.xi2 = P.xi * P.xi;
+  k.p = P.p;
+  k.q = P.q;
+  k.fp = 2.0 * P.p / P.r0;
+  k.fg = 2.0 * P.q / P.r0;
+  // list radius with a 1e-3 A guard so rounding in the build or in the
+  // displacement check can never drop a pair that reaches r_cut
+  const double rl = P.r_cut + P.r_skin + 1e-3;
+  c->rlist2 = (float)(rl * rl);
+  c->half_skin2 = 0.25 * P.r_skin * P.r_skin;
+  c->inv_m = 1.0 / (P.mass * kMvv2e);
+}
+
+// ------------------------------------------------------------- launchers
+tbsma_status launch_pack(tbsma_ctx* c, cudaStream_t s, int check) {
+  const unsigned g = grid_for(c->N, 256);
+  if (c->prec == TBSMA_MIXED)
+    k_pack<TBSMA_MIXED><<<g, 256, 0, s>>>(c->N, c->x, c->meta, c->wd, c->xq, c->xd, c->xq_b,
+                                          c->xd_b, c->half_skin2, check, c->flag, c->wire_status);
+  else
+    k_pack<TBSMA_FP64><<<g, 256, 0, s>>>(c->N, c->x, c->meta, c->wd, c->xq, c->xd, c->xq_b,
+                                         c->xd_b, c->half_skin2, check, c->flag, c->wire_status);
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
+tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_rebuild,
+                       int64_t* step_counter) {
+  k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, force_all, count_rebuild, step_counter);
+  const unsigned gs = (unsigned)(c->sm_count * 4);
+  k_nl_clear<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->cell_count);
+  k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
+                              c->wire_status);
+  k_nl_sort<<<gs * 2, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms);
+  const unsigned gb = (unsigned)(c->sm_count * 3);
+  if (c->prec == TBSMA_MIXED)
+    k_nl_build<int4><<<gb, kBuildWarps * 32, kBuildSmem, s>>>(
+        c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms, c->rlist2, c->nbr, c->n_nbr,
+        c->cap, c->xq, c->xq_b, c->wire_status);
+  else
+    k_nl_build<double4_32a><<<gb, kBuildWarps * 32, kBuildSmem, s>>>(
+        c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms, c->rlist2, c->nbr, c->n_nbr,
+        c->cap, c->xd, c->xd_b, c->wire_status);
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
+template <int TPA, bool OBS>
+void pair_f32(tbsma_ctx* c, cudaStream_t s) {
+  const unsigned g = grid_for(c->N * TPA, c->block);
+  k_density_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                 c->inv32, c->e_band);
+  k_force_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
+                                               c->inv32, c->f32, c->e_band, c->e_atom, c->w_atom,
+                                               c->s_atom);
+}
+
+template <int TPA, bool OBS>
+void pair_f64(tbsma_ctx* c, cudaStream_t s) {
+  const unsigned g = grid_for(c->N * TPA, c->block);
+  k_density_f64<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                 c->inv64, c->e_band);
+  k_force_f64<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
+                                               c->inv64, c->f64, c->e_band, c->e_atom, c->w_atom,
+                                               c->s_atom);
+}
+
+template <bool OBS>
+tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec) {
+  if (prec == TBSMA_MIXED) {
+    switch (c->tpa) {
+      case 4: pair_f32<4, OBS>(c, s); break;
+      case 8: pair_f32<8, OBS>(c, s); break;
+      case 16: pair_f32<16, OBS>(c, s); break;
+      default: pair_f32<32, OBS>(c, s); break;
+    }
+  } else {
+    switch (c->tpa) {
+      case 4: pair_f64<4, OBS>(c, s); break;
+      case 8: pair_f64<8, OBS>(c, s); break;
+      case 16: pair_f64<16, OBS>(c, s); break;
+      default: pair_f64<32, OBS>(c, s); break;
+    }
+  }
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
+template <int KICK>
+void integrate(tbsma_ctx* c, cudaStream_t s, double dt) {
+  const unsigned g = grid_for(c->N, 256);
+  if (c->prec == TBSMA_MIXED)
+    k_integrate<TBSMA_MIXED, KICK><<<g, 256, 0, s>>>(
+        c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
+        c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip);
+  else
+    k_integrate<TBSMA_FP64, KICK><<<g, 256, 0, s>>>(
+        c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
+        c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip);
+}
+
+// n consecutive steps: first integrate with a half kick, the rest with a
+// merged full kick, and a closing half kick after the last force pass.
+tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
+  for (int k = 0; k < n; ++k) {
+    if (k == 0) integrate<1>(c, s, dt);
+    else integrate<2>(c, s, dt);
+    TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
+    TB_TRY(launch_pair<false>(c, s, c->prec));
+  }
+  const unsigned g = grid_for(c->N, 256);
+  const double hk = 0.5 * dt * c->inv_m;
+  if (c->prec == TBSMA_MIXED)
+    k_half_kick<TBSMA_MIXED><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+  else
+    k_half_kick<TBSMA_FP64><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
+void drop_graph(tbsma_ctx* c) {
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  c->graph = Graph{};
+  c->graph_dt = -1.0;
+}
+
+tbsma_status set_dt(tbsma_ctx* c, double dt) {
+  if (dt == c->dt_dyn) return TBSMA_OK;
+  std::vector<WireDyn> dyn(c->W);
+  for (int w = 0; w < c->W; ++w) {
+    const WireDev& d = c->wires_h[w];
+    const double c1 = std::exp(-d.gamma * dt);
+    const double sig = std::sqrt(kBoltzmann * d.temperature * c->inv_m);
+    dyn[w].c1 = c1;
+    dyn[w].c2sig = std::sqrt(std::max(0.0, 1.0 - c1 * c1)) * sig;
+    dyn[w].delta = d.strain_rate * 1.0e-15 * d.L0 * dt / 2.0;
+    dyn[w].pad = 0.0;
+  }
+  TB_CUDA(c, cudaMemcpyAsync(c->wdyn, dyn.data(), sizeof(WireDyn) * c->W, cudaMemcpyHostToDevice,
+                             c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->dt_dyn = dt;
+  drop_graph(c);
+  return TBSMA_OK;
+}
+
+tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr;
+  TB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  tbsma_status st = enqueue_steps(c, c->cap_stream, steps, dt);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != TBSMA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  c->graph.steps = steps;
+  c->graph_dt = dt;
+  return TBSMA_OK;
+}
+
+tbsma_status read_status(tbsma_ctx* c, std::vector<uint32_t>& st) {
+  st.resize(c->W);
+  TB_CUDA(c, cudaMemcpyAsync(st.data(), c->wire_status, sizeof(uint32_t) * c->W,
+                             cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status status_verdict(tbsma_ctx* c) {
+  std::vector<uint32_t> st;
+  TB_TRY(read_status(c, st));
+  uint32_t any = 0;
+  int first = -1;
+  for (int w = 0; w < c->W; ++w) {
+    any |= st[w];
+    if (st[w] && first < 0) first = w;
+  }
+  if (!any) return TBSMA_OK;
+  char buf[160];
+  snprintf(buf, sizeof buf, "wire %d status 0x%x (bits over all wires 0x%x)", first, st[first], any);
+  if (any & (kWireNbrOverflow | kWireCellOverflow)) return fail(c, TBSMA_EOVERFLOW, buf);
+  return fail(c, TBSMA_EWIRE, buf);
+}
+
+// Re-read positions, rebuild flagged (or all) wires, forces in `prec`.
+tbsma_status refresh(tbsma_ctx* c, int force_all) {
+  TB_TRY(launch_pack(c, c->stream, force_all ? 0 : 1));
+  TB_TRY(launch_nl(c, c->stream, force_all, 0, nullptr));
+  return TBSMA_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, int32_t n_wires,
+                        const tbsma_wire* wires, double* x, double* v, const uint8_t* kind,
+                        void* cuda_stream, tbsma_ctx** out) {
+  if (!out) return TBSMA_EINVAL;
+  *out = nullptr;
+  if (!params || !wires || !x || !v || !kind || n_wires < 1) return TBSMA_EINVAL;
+  if (precision != TBSMA_FP64 && precision != TBSMA_MIXED) return TBSMA_EINVAL;
+  const tbsma_params& P = *params;
+  if (!(P.r0 > 0 && P.r_cut > 0 && P.r_skin >= 0 && P.mass > 0 && P.xi > 0 && P.A >= 0))
+    return TBSMA_EINVAL;
+  int64_t N = 0;
+  for (int w = 0; w < n_wires; ++w) {
+    if (wires[w].atom_offset != N || wires[w].n_atoms < 1 || wires[w].reserved != 0 ||
+        !(wires[w].L0 > 0) || wires[w].gamma < 0 || wires[w].temperature < 0)
+      return TBSMA_EINVAL;
+    N += wires[w].n_atoms;
+  }
+  if (N >= (int64_t)1 << 31) return TBSMA_EINVAL;  // neighbour indices are int32
+
+  tbsma_ctx* c = new tbsma_ctx();
+  c->P = P;
+  c->prec = precision;
+  c->W = n_wires;
+  c->N = N;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->x = x;
+  c->v = v;
+  c->kind = kind;
+  fill_pair_consts(c);
+
+  auto bail = [&](tbsma_status s) {
+    tbsma_destroy(c);
+    return s;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bail(TBSMA_ECUDA);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
+  if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBuildSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBuildSmem) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
+
+  const int W = n_wires;
+  tbsma_status s = TBSMA_OK;
+#define ALLOC(ptr, n)                          \
+  if ((s = alloc(c, &(ptr), (n))) != TBSMA_OK) \
+    return bail(s);
+  // per-wire bounding boxes on the device (init only)
+  tbsma_wire* wires_d = nullptr;
+  double* bbox_d = nullptr;
+  ALLOC(wires_d, W);
+  ALLOC(bbox_d, (size_t)W * 7);
+  if (cudaMemcpyAsync(wires_d, wires, sizeof(tbsma_wire) * W, cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess)
+    return bail(TBSMA_ECUDA);
+  k_bbox<<<std::min(W, 65535), 256, 0, c->stream>>>(W, wires_d, x, N, kind, bbox_d);
+  std::vector<double> bbox((size_t)W * 7);
+  if (cudaMemcpyAsync(bbox.data(), bbox_d, sizeof(double) * 7 * W, cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
+
+  // per-wire cell grids: edge >= list radius (with a 1e-4 relative guard so
+  // rounding in the cell coordinate never separates two atoms by two cells)
+  const double rl = std::sqrt((double)c->rlist2) * 1.0001;
+  c->wires_h.resize(W);
+  int64_t cells = 0;
+  for (int w = 0; w < W; ++w) {
+    WireDev& d = c->wires_h[w];
+    std::memset(&d, 0, sizeof d);
+    d.offset = wires[w].atom_offset;
+    d.n = wires[w].n_atoms;
+    d.n_mobile = (int32_t)bbox[w * 7 + 6];
+    d.seed = wires[w].seed;
+    d.L0 = wires[w].L0;
+    d.strain_rate = wires[w].strain_rate;
+    d.temperature = wires[w].temperature;
+    d.gamma = wires[w].gamma;
+    for (int k = 0; k < 3; ++k) {
+      const double lo = bbox[w * 7 + k], hi = bbox[w * 7 + 3 + k];
+      if (!std::isfinite(lo) || !std::isfinite(hi)) return bail(fail(c, TBSMA_EINVAL, "non-finite positions"));
+      d.origin[k] = 0.5 * (lo + hi);
+      // along the axis leave room for strain up to 1.0 (each end +L/2)
+      const double margin = (k == 0 ? 0.5 * (hi - lo) : 0.0) + rl;
+      const double glo = lo - d.origin[k] - margin, ghi = hi - d.origin[k] + margin;
+      const int n = std::max(1, (int)std::floor((ghi - glo) / rl));
+      d.glo[k] = glo;
+      d.einv[k] = n / (ghi - glo);
+      d.nc[k] = n;
+      if (std::fabs(lo - d.origin[k]) > kFixedRange || std::fabs(hi - d.origin[k]) > kFixedRange)
+        return bail(fail(c, TBSMA_EINVAL, "wire longer than the fixed-point range (2048 A)"));
+    }
+    d.cell_base = cells;
+    cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
+  }
+  c->n_cells = cells;
+
+  ALLOC(c->wd, W);
+  ALLOC(c->wdyn, W);
+  ALLOC(c->meta, N);
+  ALLOC(c->xq, N);
+  ALLOC(c->xq_b, N);
+  ALLOC(c->xd, N);
+  ALLOC(c->xd_b, N);
+  ALLOC(c->f32, 3 * N);
+  ALLOC(c->f64, 3 * N);
+  ALLOC(c->inv32, N);
+  ALLOC(c->inv64, N);
+  ALLOC(c->e_band, N);
+  ALLOC(c->e_atom, N);
+  ALLOC(c->w_atom, N);
+  ALLOC(c->s_atom, N);
+  ALLOC(c->nbr, (size_t)N * c->cap);
+  ALLOC(c->n_nbr, N);
+  ALLOC(c->cell_count, cells);
+  ALLOC(c->cell_atoms, (size_t)cells * kCellCap);
+  ALLOC(c->flag, W);
+  ALLOC(c->wl_wire, W);
+  ALLOC(c->wl_cell, W + 1);
+  ALLOC(c->wl_atom, W + 1);
+  ALLOC(c->n_flagged, 1);
+  ALLOC(c->n_rebuilds, W);
+  ALLOC(c->wire_status, W);
+  ALLOC(c->d_grip, W);
+  ALLOC(c->step_counter, 1);
+  ALLOC(c->obs_d, W);
+  ALLOC(c->fcheck_d, W);
+#undef ALLOC
+
+  cudaStream_t st = c->stream;
+  bool ok = cudaMemcpyAsync(c->wd, c->wires_h.data(), sizeof(WireDev) * W, cudaMemcpyHostToDevice,
+                            st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->d_grip, 0, sizeof(double) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->step_counter, 0, sizeof(int64_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * N, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->f32, 0, sizeof(float) * 3 * N, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->f64, 0, sizeof(double) * 3 * N, st) == cudaSuccess;
+  if (!ok) return bail(TBSMA_ECUDA);
+  k_meta<<<std::min(W, 65535), 256, 0, st>>>(W, c->wd, kind, c->meta);
+  if ((s = refresh(c, 1)) != TBSMA_OK) return bail(s);
+  if ((s = launch_pair<false>(c, st, c->prec)) != TBSMA_OK) return bail(s);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(TBSMA_ECUDA);
+  if ((s = status_verdict(c)) != TBSMA_OK && s != TBSMA_EWIRE && s != TBSMA_EOVERFLOW)
+    return bail(s);
+  *out = c;
+  return s;
+}
+
+tbsma_status tbsma_init_velocities(tbsma_ctx* c) {
+  if (!c) return TBSMA_EINVAL;
+  k_init_velocities<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->meta, c->N, c->v,
+                                                                  c->P.mass * kMvv2e);
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_build_neighbors(tbsma_ctx* c, int32_t force_all, int32_t* n_rebuilt) {
+  if (!c) return TBSMA_EINVAL;
+  TB_TRY(refresh(c, force_all ? 1 : 0));
+  if (n_rebuilt) {
+    TB_CUDA(c, cudaMemcpyAsync(n_rebuilt, c->n_flagged, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c->stream));
+    TB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return status_verdict(c);
+  }
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_compute_forces(tbsma_ctx* c, float* f32_out, double* f64_out) {
+  if (!c) return TBSMA_EINVAL;
+  TB_TRY(refresh(c, 0));
+  const int other = c->prec == TBSMA_MIXED ? TBSMA_FP64 : TBSMA_MIXED;
+  if ((other == TBSMA_MIXED && f32_out) || (other == TBSMA_FP64 && f64_out))
+    TB_TRY(launch_pair<false>(c, c->stream, other));
+  TB_TRY(launch_pair<false>(c, c->stream, c->prec));
+  const size_t n3 = 3 * (size_t)c->N;
+  if (f32_out)
+    TB_CUDA(c, cudaMemcpyAsync(f32_out, c->f32, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  if (f64_out)
+    TB_CUDA(c, cudaMemcpyAsync(f64_out, c->f64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_atom_energies(tbsma_ctx* c, double* e_out, double* w_out) {
+  if (!c) return TBSMA_EINVAL;
+  TB_TRY(refresh(c, 0));
+  TB_TRY(launch_pair<true>(c, c->stream, c->prec));
+  if (e_out)
+    TB_CUDA(c, cudaMemcpyAsync(e_out, c->e_atom, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if (w_out)
+    TB_CUDA(c, cudaMemcpyAsync(w_out, c->w_atom, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
+  if (!c) return TBSMA_EINVAL;
+  if (n_steps < 0 || !(dt_fs > 0.0)) return fail(c, TBSMA_EINVAL, "n_steps < 0 or dt <= 0");
+  if (n_steps == 0) return TBSMA_OK;
+  TB_TRY(set_dt(c, dt_fs));
+  const int chunk = (int)std::min<int64_t>(n_steps, kGraphChunk);
+  if (!c->graph.exec || c->graph_dt != dt_fs || c->graph.steps != chunk) TB_TRY(capture(c, chunk, dt_fs));
+  int64_t left = n_steps;
+  while (left >= c->graph.steps) {
+    TB_CUDA(c, cudaGraphLaunch(c->graph.exec, c->stream));
+    left -= c->graph.steps;
+  }
+  if (left > 0) TB_TRY(enqueue_steps(c, c->stream, (int)left, dt_fs));
+  c->steps_done += n_steps;
+  return status_verdict(c);
+}
+
+tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
+  if (!c || !out) return TBSMA_EINVAL;
+  TB_TRY(refresh(c, 0));
+  TB_TRY(launch_pair<true>(c, c->stream, c->prec));
+  const double rhs = 0.5 * c->P.r0;
+  const double v_atom = 4.0 / 3.0 * 3.141592653589793238462643383279 * rhs * rhs * rhs;
+  k_observe<<<std::min(c->W, 65535), 256, 0, c->stream>>>(
+      c->W, c->wd, c->meta, c->N, c->e_atom, c->w_atom, c->v, c->d_grip, c->n_rebuilds,
+      c->wire_status, c->steps_done, c->P.mass * kMvv2e, v_atom, c->obs_d);
+  TB_CUDA(c, cudaGetLastError());
+  TB_CUDA(c, cudaMemcpyAsync(out, c->obs_d, sizeof(tbsma_obs) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return status_verdict(c);
+}
+
+tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
+  if (!c || !out) return TBSMA_EINVAL;
+  TB_TRY(refresh(c, 0));
+  TB_TRY(launch_pair<false>(c, c->stream, TBSMA_MIXED));
+  TB_TRY(launch_pair<true>(c, c->stream, TBSMA_FP64));
+  k_force_check<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->N, c->f32, c->f64,
+                                                              c->s_atom, c->fcheck_d);
+  TB_CUDA(c, cudaGetLastError());
+  TB_CUDA(c, cudaMemcpyAsync(out, c->fcheck_d, sizeof(tbsma_fcheck) * c->W, cudaMemcpyDeviceToHost,
+                             c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return status_verdict(c);
+}
+
+tbsma_status tbsma_upload_state(tbsma_ctx* c, const double* x_host, const double* v_host) {
+  if (!c) return TBSMA_EINVAL;
+  const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+  if (x_host) TB_CUDA(c, cudaMemcpyAsync(c->x, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (v_host) TB_CUDA(c, cudaMemcpyAsync(c->v, v_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (x_host) {
+    TB_TRY(refresh(c, 0));
+    TB_TRY(launch_pair<false>(c, c->stream, c->prec));
+  }
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_download_state(tbsma_ctx* c, double* x_host, double* v_host) {
+  if (!c) return TBSMA_EINVAL;
+  const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+  if (x_host) TB_CUDA(c, cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (v_host) TB_CUDA(c, cudaMemcpyAsync(v_host, c->v, bytes, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_get_wire_status(tbsma_ctx* c, int32_t* status_host) {
+  if (!c || !status_host) return TBSMA_EINVAL;
+  std::vector<uint32_t> st;
+  TB_TRY(read_status(c, st));
+  for (int w = 0; w < c->W; ++w) status_host[w] = (int32_t)st[w];
+  return TBSMA_OK;
+}
+
+int32_t tbsma_nbr_capacity(const tbsma_ctx* c) { return c ? c->cap : 0; }
+
+tbsma_status tbsma_get_neighbors(tbsma_ctx* c, int32_t* n_nbr, int32_t* nbr, int32_t cap) {
+  if (!c || cap != c->cap) return TBSMA_EINVAL;
+  if (n_nbr)
+    TB_CUDA(c, cudaMemcpyAsync(n_nbr, c->n_nbr, c->N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+  if (nbr)
+    TB_CUDA(c, cudaMemcpyAsync(nbr, c->nbr, (size_t)c->N * c->cap * sizeof(int32_t),
+                               cudaMemcpyDeviceToDevice, c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_set_launch(tbsma_ctx* c, int32_t lanes_per_atom, int32_t block_threads) {
+  if (!c) return TBSMA_EINVAL;
+  if (lanes_per_atom != 4 && lanes_per_atom != 8 && lanes_per_atom != 16 && lanes_per_atom != 32)
+    return fail(c, TBSMA_EINVAL, "lanes_per_atom must be 4, 8, 16 or 32");
+  if (block_threads < 64 || block_threads > 256 || block_threads % 32)
+    return fail(c, TBSMA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
+  c->tpa = lanes_per_atom;
+  c->block = block_threads;
+  drop_graph(c);
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                                 void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return TBSMA_EINVAL;
+  if (n == 0) return TBSMA_OK;
+  k_philox<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(ctr, key, n, out);
+  return cudaGetLastError() == cudaSuccess ? TBSMA_OK : TBSMA_ECUDA;
+}
+
+tbsma_status tbsma_normals(uint64_t seed, const uint32_t* atoms, int64_t n, int64_t step, uint32_t tag,
+                           tbsma_precision precision, double* out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!atoms || !out)) || step < 0) return TBSMA_EINVAL;
+  if (n == 0) return TBSMA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (precision == TBSMA_MIXED)
+    k_normals<TBSMA_MIXED><<<grid_for(n, 256), 256, 0, s>>>(seed, atoms, n, (uint64_t)step, tag, out);
+  else if (precision == TBSMA_FP64)
+    k_normals<TBSMA_FP64><<<grid_for(n, 256), 256, 0, s>>>(seed, atoms, n, (uint64_t)step, tag, out);
+  else
+    return TBSMA_EINVAL;
+  return cudaGetLastError() == cudaSuccess ? TBSMA_OK : TBSMA_ECUDA;
+}
+
+const char* tbsma_last_error(const tbsma_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void tbsma_destroy(tbsma_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"
