@@ -126,7 +126,9 @@ typedef struct {
  * 1.0 along x; atoms outside are clamped into edge cells), builds all
  * neighbour lists and computes the initial forces.  Synchronises.
  * Errors: EINVAL (null pointers, n_wires < 1, wires not packed back to back,
- * bad parameters), ENOMEM, ECUDA.  On error *out is NULL. */
+ * bad parameters), ENOMEM, ECUDA: *out is NULL.  EWIRE / EOVERFLOW (a wire
+ * was flagged by the initial build): *out is a valid context that the
+ * caller inspects (tbsma_get_wire_status) and destroys. */
 tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, int32_t n_wires,
                         const tbsma_wire* wires, double* x, double* v, const uint8_t* kind,
                         void* cuda_stream, tbsma_ctx** out);
@@ -195,6 +197,13 @@ tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, i
  * (4, 8, 16 or 32) and threads per block (64..256, multiple of 32).
  * Invalidates captured graphs. */
 tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t lanes_per_atom, int32_t block_threads);
+
+/* Enqueue `reps` launches of one pair pass on the context's stream, on the
+ * current packed positions and lists, in the context's precision and launch
+ * shape: pass 1 = density (Eq. 1), pass 2 = force.  Both are idempotent, so a
+ * caller can bracket this call with CUDA events on the same stream to time a
+ * pass alone.  Errors: EINVAL (pass not 1 or 2, reps < 1). */
+tbsma_status tbsma_run_pass(tbsma_ctx* ctx, int32_t pass, int32_t reps);
 
 /* Philox4x32-10 (Salmon et al., SC'11) on the device, as the thermostat
  * uses it: out[4i..4i+4) = philox(ctr[4i..4i+4), key[2i..2i+2)).  Device

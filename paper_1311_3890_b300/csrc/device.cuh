@@ -100,11 +100,19 @@ __device__ __forceinline__ double3 normals3_f64(uint4 b) {
   return make_double3(a * cs, a * sn, c * cs2);
 }
 
-__device__ __forceinline__ float3 normals3_f32(uint4 b) {
+// -ln(u) for u = (b + 1/2) 2^-32 in FP32.  Above u = 1/2 the complement
+// 1 - u = (~b + 1/2) 2^-32 is formed from the integer and passed to log1pf, so
+// u never rounds to 1 and -ln(u) keeps full relative precision near 0.
+__device__ __forceinline__ float neg_log_u32(uint32_t b) {
   const float s = 2.3283064365386963e-10f, h = 1.16415321826934814e-10f;  // 2^-32, 2^-33
-  const float u0 = fmaf((float)b.x, s, h), u1 = fmaf((float)b.y, s, h);
-  const float u2 = fmaf((float)b.z, s, h), u3 = fmaf((float)b.w, s, h);
-  const float a = sqrtf(-2.0f * logf(u0)), c = sqrtf(-2.0f * logf(u2));
+  if (b < 0x80000000u) return -logf(fmaf((float)b, s, h));
+  return -log1pf(-fmaf((float)(0xFFFFFFFFu - b), s, h));
+}
+
+__device__ __forceinline__ float3 normals3_f32(uint4 b) {
+  const float s = 2.3283064365386963e-10f, h = 1.16415321826934814e-10f;
+  const float u1 = fmaf((float)b.y, s, h), u3 = fmaf((float)b.w, s, h);
+  const float a = sqrtf(2.0f * neg_log_u32(b.x)), c = sqrtf(2.0f * neg_log_u32(b.z));
   float sn, cs, sn2, cs2;
   sincospif(2.0f * u1, &sn, &cs);
   sincospif(2.0f * u3, &sn2, &cs2);

@@ -241,6 +241,39 @@ tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec) {
   return TBSMA_OK;
 }
 
+template <int TPA>
+void one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
+  const unsigned g = grid_for(c->N * TPA, c->block);
+  if (c->prec == TBSMA_MIXED) {
+    if (pass == 1)
+      k_density_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                        c->inv32, c->e_band);
+    else
+      k_force_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                      c->inv32, c->f32, c->e_band, c->e_atom,
+                                                      c->w_atom, c->s_atom);
+  } else {
+    if (pass == 1)
+      k_density_f64<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                        c->inv64, c->e_band);
+    else
+      k_force_f64<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
+                                                      c->inv64, c->f64, c->e_band, c->e_atom,
+                                                      c->w_atom, c->s_atom);
+  }
+}
+
+tbsma_status launch_one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
+  switch (c->tpa) {
+    case 4: one_pass<4>(c, s, pass); break;
+    case 8: one_pass<8>(c, s, pass); break;
+    case 16: one_pass<16>(c, s, pass); break;
+    default: one_pass<32>(c, s, pass); break;
+  }
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
 template <int KICK>
 void integrate(tbsma_ctx* c, cudaStream_t s, double dt) {
   const unsigned g = grid_for(c->N, 256);
@@ -650,6 +683,12 @@ tbsma_status tbsma_set_launch(tbsma_ctx* c, int32_t lanes_per_atom, int32_t bloc
   c->tpa = lanes_per_atom;
   c->block = block_threads;
   drop_graph(c);
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_run_pass(tbsma_ctx* c, int32_t pass, int32_t reps) {
+  if (!c || (pass != 1 && pass != 2) || reps < 1) return TBSMA_EINVAL;
+  for (int r = 0; r < reps; ++r) TB_TRY(launch_one_pass(c, c->stream, pass));
   return TBSMA_OK;
 }
 
