@@ -1,0 +1,302 @@
+"""ctypes binding of libtbsma.so (include/tbsma.h).
+
+Argument marshalling only: every step of the MD path runs in the CUDA
+library.  Device memory and streams come from PyTorch.  There is no CPU
+fallback: if the compiled library is missing or fails to load, the first
+call that needs it raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtbsma.so")
+
+FP64 = 0
+MIXED = 1
+
+STATUS_NAMES = {
+    0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "ETIMEOUT", 6: "EWIRE",
+    7: "ESTATE",
+}
+WIRE_NONFINITE, WIRE_NBR_OVERFLOW, WIRE_CELL_OVERFLOW, WIRE_RANGE = 1, 2, 4, 8
+
+
+class TbsmaError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: TBSMA_{STATUS_NAMES.get(status, status)} {detail}".rstrip())
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("A", "xi", "p", "q", "r0", "r_cut", "r_skin", "mass")]
+
+
+def au_params(**over) -> Params:
+    """TB-SMA Au (Table 1, r0 read as the nearest-neighbour distance 2.884 A),
+    r_cut 5.8 A, list skin 0.29 A, Au mass 196.966569 amu."""
+    d = dict(A=0.2061, xi=1.790, p=10.229, q=4.036, r0=2.884, r_cut=5.8, r_skin=0.29,
+             mass=196.966569)
+    d.update(over)
+    return Params(**d)
+
+
+class WireC(ctypes.Structure):
+    _fields_ = [
+        ("atom_offset", ctypes.c_int64),
+        ("n_atoms", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("L0", ctypes.c_double),
+        ("strain_rate", ctypes.c_double),
+        ("temperature", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class ObsC(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64),
+        ("strain", ctypes.c_double),
+        ("e_pot", ctypes.c_double),
+        ("e_kin", ctypes.c_double),
+        ("temp", ctypes.c_double),
+        ("sigma_xx", ctypes.c_double),
+        ("virial_xx", ctypes.c_double),
+        ("n_rebuilds", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class FCheckC(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("max_err_scaled", "max_err_raw", "norm_err", "max_abs_err")]
+
+
+_P = ctypes.c_void_p
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/tbsma.h
+SIGNATURES = [
+    ("tbsma_init", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
+    ("tbsma_init_velocities", ctypes.c_int, [_P]),
+    ("tbsma_build_neighbors", ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    ("tbsma_compute_forces", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_atom_energies", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_step_nvt_pull", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    ("tbsma_reduce_observables", ctypes.c_int, [_P, _P]),
+    ("tbsma_force_check", ctypes.c_int, [_P, _P]),
+    ("tbsma_upload_state", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_download_state", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_get_wire_status", ctypes.c_int, [_P, _P]),
+    ("tbsma_nbr_capacity", ctypes.c_int32, [_P]),
+    ("tbsma_get_neighbors", ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    ("tbsma_set_launch", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    ("tbsma_normals", ctypes.c_int, [ctypes.c_uint64, _P, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_uint32, ctypes.c_int, _P, _P]),
+    ("tbsma_last_error", ctypes.c_char_p, [_P]),
+    ("tbsma_destroy", None, [_P]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtbsma.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing; build it with `python -m paper_1311_3890_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream_ptr(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+class Engine:
+    """A batch of wires on one GPU, driven through the C ABI.
+
+    batch: an inputs.Batch (positions (N,3) float64, kind, per-wire table).
+    precision: "mixed" or "fp64".
+    """
+
+    def __init__(self, batch, precision: str = "mixed", params: Params | None = None,
+                 device: str = "cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.batch = batch
+        self.N = int(batch.n_atoms)
+        self.W = int(batch.n_wires)
+        self.precision = MIXED if precision == "mixed" else FP64
+        self.params = params if params is not None else au_params()
+        self.stream = stream
+        self.ctx = ctypes.c_void_p()
+        # SoA device state: x[0:N] = x coords, x[N:2N] = y, x[2N:3N] = z
+        self.x = torch.from_numpy(np.ascontiguousarray(batch.x.T).reshape(-1)).to(self.device)
+        self.v = torch.zeros(3 * self.N, dtype=torch.float64, device=self.device)
+        self.kind = torch.from_numpy(np.ascontiguousarray(batch.kind, dtype=np.uint8)).to(self.device)
+        wires = (WireC * self.W)()
+        for w in range(self.W):
+            wires[w] = WireC(int(batch.offset[w]), int(batch.n[w]), 0, float(batch.L0[w]),
+                             float(batch.strain_rate[w]), float(batch.temperature[w]),
+                             float(batch.gamma[w]), int(batch.seed[w]))
+        self._wires = wires
+        st = lib().tbsma_init(ctypes.byref(self.params), self.precision, self.W, wires,
+                              _ptr(self.x), _ptr(self.v), _ptr(self.kind),
+                              _stream_ptr(stream), ctypes.byref(self.ctx))
+        if st != 0:
+            detail = ""
+            if self.ctx:
+                detail = lib().tbsma_last_error(self.ctx).decode()
+                lib().tbsma_destroy(self.ctx)
+                self.ctx = ctypes.c_void_p()
+            raise TbsmaError(st, "tbsma_init", detail)
+
+    # ----------------------------------------------------------- plumbing
+    def _check(self, st, where):
+        if st != 0:
+            raise TbsmaError(st, where, lib().tbsma_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().tbsma_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ the path
+    def init_velocities(self):
+        self._check(lib().tbsma_init_velocities(self.ctx), "tbsma_init_velocities")
+
+    def build_neighbors(self, force_all: bool = False) -> int:
+        n = ctypes.c_int32(0)
+        self._check(lib().tbsma_build_neighbors(self.ctx, int(force_all), ctypes.byref(n)),
+                    "tbsma_build_neighbors")
+        return int(n.value)
+
+    def step(self, n_steps: int, dt: float = 2.0, check: bool = True) -> int:
+        st = lib().tbsma_step_nvt_pull(self.ctx, int(n_steps), float(dt))
+        if check:
+            self._check(st, "tbsma_step_nvt_pull")
+        return st
+
+    def forces(self, f32: bool = True, f64: bool = True):
+        """(F_mixed float32 (N,3) or None, F_fp64 float64 (N,3) or None)."""
+        t = self.torch
+        a = t.empty(3 * self.N, dtype=t.float32, device=self.device) if f32 else None
+        b = t.empty(3 * self.N, dtype=t.float64, device=self.device) if f64 else None
+        self._check(lib().tbsma_compute_forces(self.ctx, _ptr(a), _ptr(b)), "tbsma_compute_forces")
+        return (a.view(3, self.N).T if f32 else None, b.view(3, self.N).T if f64 else None)
+
+    def atom_energies(self):
+        t = self.torch
+        e = t.empty(self.N, dtype=t.float64, device=self.device)
+        w = t.empty(self.N, dtype=t.float64, device=self.device)
+        self._check(lib().tbsma_atom_energies(self.ctx, _ptr(e), _ptr(w)), "tbsma_atom_energies")
+        return e, w
+
+    def observables(self, check: bool = True) -> np.ndarray:
+        out = (ObsC * self.W)()
+        st = lib().tbsma_reduce_observables(self.ctx, out)
+        if check:
+            self._check(st, "tbsma_reduce_observables")
+        return np.ctypeslib.as_array(out).copy()
+
+    def force_check(self) -> np.ndarray:
+        out = (FCheckC * self.W)()
+        self._check(lib().tbsma_force_check(self.ctx, out), "tbsma_force_check")
+        return np.ctypeslib.as_array(out).copy()
+
+    def upload(self, x_host=None, v_host=None):
+        """x_host, v_host: host float64 arrays of 3N (SoA); pinned torch tensors or numpy."""
+        self._check(lib().tbsma_upload_state(self.ctx, _hptr(x_host), _hptr(v_host)),
+                    "tbsma_upload_state")
+
+    def download(self, x_host=None, v_host=None):
+        self._check(lib().tbsma_download_state(self.ctx, _hptr(x_host), _hptr(v_host)),
+                    "tbsma_download_state")
+
+    def wire_status(self) -> np.ndarray:
+        out = np.zeros(self.W, dtype=np.int32)
+        self._check(lib().tbsma_get_wire_status(self.ctx, out.ctypes.data_as(ctypes.c_void_p)),
+                    "tbsma_get_wire_status")
+        return out
+
+    def neighbors(self):
+        t = self.torch
+        cap = lib().tbsma_nbr_capacity(self.ctx)
+        n = t.empty(self.N, dtype=t.int32, device=self.device)
+        nb = t.empty(self.N * cap, dtype=t.int32, device=self.device)
+        self._check(lib().tbsma_get_neighbors(self.ctx, _ptr(n), _ptr(nb), cap), "tbsma_get_neighbors")
+        return n, nb.view(self.N, cap)
+
+    def set_launch(self, lanes_per_atom: int, block_threads: int):
+        self._check(lib().tbsma_set_launch(self.ctx, lanes_per_atom, block_threads), "tbsma_set_launch")
+
+    def run_pass(self, which: int, reps: int = 1):
+        """Enqueue `reps` launches of pass 1 (density) or 2 (force) alone."""
+        self._check(lib().tbsma_run_pass(self.ctx, which, reps), "tbsma_run_pass")
+
+    # ------------------------------------------------------------- views
+    def positions(self) -> np.ndarray:
+        return self.x.view(3, self.N).T.cpu().numpy()
+
+    def velocities(self) -> np.ndarray:
+        return self.v.view(3, self.N).T.cpu().numpy()
+
+
+def philox4x32_10(ctr, key, stream=None):
+    """ctr (n,4) int32 cuda tensor (bit patterns), key (n,2) -> (n,4) int32 bits."""
+    import torch
+
+    out = torch.empty_like(ctr)
+    st = lib().tbsma_philox4x32_10(_ptr(ctr), _ptr(key), ctr.shape[0], _ptr(out), _stream_ptr(stream))
+    if st != 0:
+        raise TbsmaError(st, "tbsma_philox4x32_10")
+    return out
+
+
+def normals(seed: int, atoms, step: int, tag: int, precision: str = "fp64", stream=None):
+    """(n,3) float64 cuda tensor of the thermostat's Gaussian triples."""
+    import torch
+
+    n = atoms.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float64, device=atoms.device)
+    st = lib().tbsma_normals(seed, _ptr(atoms), n, step, tag,
+                             MIXED if precision == "mixed" else FP64, _ptr(out), _stream_ptr(stream))
+    if st != 0:
+        raise TbsmaError(st, "tbsma_normals")
+    return out
