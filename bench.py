@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Aggregate TB-SMA atom-steps/s of the batched mixed-precision wire MD step.
+
+Workload: 256 independent Au [100] wires, D = 3 nm, L = 40 nm (17435 atoms
+each, 4.46M atoms), Philox seeds 0..255, 10 K, strain rate 1e8 1/s, dt = 2 fs,
+synthetic fcc geometry.  One bench step = one MD step of every wire: B A O A,
+displacement check, list rebuilds as they occur, density pass, force pass,
+B.  Inputs (4.46M atoms, ~1.6 GB of state and lists) are far larger than the
+126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own full batch (seeds offset by rank):
+weak scaling, no collective on the data path; rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on this host's cores (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch256_d3_l40"
+LAUNCH = (8, 128)  # lanes per atom, threads per block of the pair kernels
+GRAPH_CHUNK = 50  # steps per captured graph (library constant)
+KERNELS_PER_STEP = 8  # integrate, plan, clear, bin, sort, build, density, force
+METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"
+UNIT = "atom-steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--e2e-seg", type=int, default=100, help="MD steps per end-to-end segment")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the cpu baseline, fp64 comparison and e2e legs")
+    return p.parse_args()
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------- CPU oracle leg
+def oracle_sample(batch, budget_s: float, steps: int | None = None):
+    """Time the FP64 oracle on the first wires of the batch, one per thread.
+
+    Returns (atom-steps/s, threads used, description, atoms, steps)."""
+    import oracle
+
+    threads = oracle.max_threads()
+    W = min(threads, batch.n_wires)
+    n = batch.n[:W]
+    N = int(n.sum())
+    x = batch.x[:N].copy()
+    v = np.zeros_like(x)
+    args = (batch.kind[:N], batch.offset[:W], n, batch.L0[:W], batch.strain_rate[:W],
+            batch.temperature[:W], batch.gamma[:W], batch.seed[:W])
+    F, xb, dg, nr = oracle.md_batch(x, v, *args, 0, 1, 2.0, brute_max=0)  # includes first forces
+    t = time.perf_counter()
+    oracle.md_batch(x, v, *args, 1, 1, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg, n_rebuild=nr)
+    per_step = time.perf_counter() - t
+    if steps is None:
+        steps = int(max(2, min(500, budget_s / max(per_step, 1e-6))))
+    t = time.perf_counter()
+    oracle.md_batch(x, v, *args, 2, steps, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg,
+                    n_rebuild=nr)
+    el = time.perf_counter() - t
+    desc = f"{W} of {batch.n_wires} wires ({N} atoms, one per thread) x {steps} MD steps"
+    return N * steps / el, W, desc, N, steps
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from inputs import workload
+
+    batch = workload(args.workload)
+    # bound each step so that warmup + steps finish within ~2 minutes
+    import oracle
+
+    threads = oracle.max_threads()
+    per_step_budget = 120.0 / max(1, args.steps + args.warmup)
+    rate_guess = 1.8e5 * threads  # atom-steps/s of the oracle on this workload
+    n_w = int(max(1, min(threads, batch.n_wires, per_step_budget * rate_guess / batch.n[0])))
+    from inputs.wires import Batch
+
+    sub = Batch(x=batch.x[: int(batch.n[:n_w].sum())], kind=batch.kind, offset=batch.offset[:n_w],
+                n=batch.n[:n_w], L0=batch.L0, strain_rate=batch.strain_rate,
+                temperature=batch.temperature, gamma=batch.gamma, seed=batch.seed)
+    N = int(sub.n.sum())
+    x = sub.x.copy()
+    v = np.zeros_like(x)
+    a = (sub.kind[:N], sub.offset, sub.n, sub.L0[:n_w], sub.strain_rate[:n_w],
+         sub.temperature[:n_w], sub.gamma[:n_w], sub.seed[:n_w])
+    F, xb, dg, nr = oracle.md_batch(x, v, *a, 0, max(1, args.warmup), 2.0, brute_max=0)
+    t = time.perf_counter()
+    oracle.md_batch(x, v, *a, args.warmup, args.steps, 2.0, brute_max=0, F=F, x_build=xb,
+                    d_grip=dg, n_rebuild=nr)
+    el = time.perf_counter() - t
+    value = N * args.steps / el
+    sample = f"{n_w} of {batch.n_wires} wires ({N} atoms, one wire per thread) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "wires": int(batch.n_wires),
+                   "atoms": int(batch.n_atoms), "dt_fs": 2.0},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_w, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our path
+def launches_in(K: int) -> int:
+    full, rem = divmod(K, GRAPH_CHUNK) if K >= GRAPH_CHUNK else (0, K)
+    n = full * (KERNELS_PER_STEP * GRAPH_CHUNK + 1)
+    if rem:
+        n += KERNELS_PER_STEP * rem + 1
+    return n
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from inputs.configs import WORKLOADS, WireSpec, build
+    import paper_1311_3890_b300 as tb
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    specs = WORKLOADS[args.workload]()
+    if rank:
+        specs = [WireSpec(s.diameter_nm, s.length_nm, s.temperature, s.strain_rate,
+                          s.seed + rank * len(specs), s.gamma) for s in specs]
+    batch = build(specs)
+    N, W = batch.n_atoms, batch.n_wires
+    eng = tb.Engine(batch, precision="mixed")
+    eng.set_launch(*LAUNCH)
+    eng.init_velocities()
+    eng.step(max(3, args.warmup), 2.0)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record()
+    eng.step(args.steps, 2.0)
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * N * args.steps / (t_max / 1e3)
+
+    # force-error gate on the final state (same positions, same list)
+    fc = eng.force_check()
+    ob = eng.observables()
+
+    # dominant kernel (force pass) timed alone with CUDA events on the library's stream
+    n_nbr, _ = eng.neighbors()
+    n_list = float(n_nbr.double().mean().item())
+    reps = 20
+    res = {}
+    for which in (1, 2):
+        eng.run_pass(which, 3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        eng.run_pass(which, reps)
+        b.record()
+        torch.cuda.synchronize()
+        res[which] = a.elapsed_time(b) / reps
+    # algorithmic bytes per atom of the force pass: own list row (4 n_list) +
+    # n_nbr (4) + own packed position (16) + inv_i (4) + F (12); neighbour
+    # positions and inv_j are re-reads served by L1/L2
+    bytes_force = N * (4.0 * n_list + 4 + 16 + 4 + 12)
+    hbm_peak, peak_kind = _peaks()
+    achieved = bytes_force / (res[2] * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "mixed f32 pair / f64 state",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
+                   "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
+                   "lanes_per_atom": LAUNCH[0], "block": LAUNCH[1],
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
+        "roofline": {"kernel": "k_force_f32", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "ms_per_launch": res[2], "density_ms_per_launch": res[1],
+                     "mean_list_len": n_list},
+        "clocks": ck,
+        "gpu_launches": launches_in(args.steps),
+        "force_check": {"max_err_scaled": float(fc["max_err_scaled"].max()),
+                        "norm_err": float(fc["norm_err"].max()),
+                        "max_err_raw": float(fc["max_err_raw"].max())},
+        "rebuilds_per_wire": float(ob["n_rebuilds"].mean()),
+    }
+
+    if not args.no_extras and rank == 0:
+        # end to end through the public API: pinned host state in, K steps in
+        # segments, per-wire observables and state out every segment
+        seg = max(1, min(args.e2e_seg, args.steps))
+        n_seg = max(1, args.steps // seg)
+        xh = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        vh = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        eng.download(xh, vh)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n_seg):
+            eng.upload(xh, vh)
+            eng.step(seg, 2.0)
+            eng.observables()
+            eng.download(xh, vh)
+        el = time.perf_counter() - t
+        obs_bytes = W * 64
+        line["e2e"] = {"value": N * seg * n_seg / el, "unit": UNIT,
+                       "h2d_bytes_per_step": 48.0 * N / seg,
+                       "d2h_bytes_per_step": (48.0 * N + obs_bytes) / seg,
+                       "segment_steps": seg}
+        # plain FP64, one wire per launch, on a sample of the same wires
+        from inputs.wires import Wire, pack
+
+        tot_as, tot_ms = 0.0, 0.0
+        for w in range(8):
+            s = batch.wire_slice(w)
+            one = pack([Wire(x=batch.x[s].copy(), kind=batch.kind[s].copy(), diameter_nm=3.0,
+                             length_nm=40.0, L0=float(batch.L0[w]), temperature=10.0,
+                             strain_rate=1e8, gamma=float(batch.gamma[w]), seed=int(batch.seed[w]))])
+            e1 = tb.Engine(one, precision="fp64")
+            e1.init_velocities()
+            e1.step(5, 2.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            e1.step(20, 2.0)
+            b.record()
+            torch.cuda.synchronize()
+            tot_ms += a.elapsed_time(b)
+            tot_as += one.n_atoms * 20
+            e1.close()
+        line["fp64_one_wire_per_launch"] = {
+            "value": tot_as / (tot_ms / 1e3), "unit": UNIT,
+            "sample": "8 of the 256 wires, each alone in its own context, 20 steps"}
+        if world == 1:
+            v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": desc}
+    eng.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
