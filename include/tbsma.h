@@ -76,7 +76,7 @@ typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
 #define TBSMA_WIRE_NONFINITE 1u     /* NaN/Inf position or velocity */
 #define TBSMA_WIRE_NBR_OVERFLOW 2u  /* an atom has more neighbours than the list holds */
 #define TBSMA_WIRE_CELL_OVERFLOW 4u /* a cell holds more atoms than its capacity */
-#define TBSMA_WIRE_RANGE 8u         /* an atom left the fixed-point range (+-1024 A of the wire centre) */
+#define TBSMA_WIRE_RANGE 8u         /* an atom is more than 1e9 A from its wire's centre */
 
 /* TB-SMA parameters (Table 1; r_cut after Eq. 3), list skin and mass.
  * Au: A = 0.2061 eV, xi = 1.790 eV, p = 10.229, q = 4.036, r0 = 2.884 A
@@ -172,7 +172,12 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
 tbsma_status tbsma_reduce_observables(tbsma_ctx* ctx, tbsma_obs* out);
 
 /* Compare MIXED and FP64 forces at the current positions on the same list,
- * per wire, into out[n_wires] (host).  Synchronises. */
+ * per wire, into out[n_wires] (host).  Whether a pair is inside r_cut is
+ * decided once, by the MIXED path's FP32 rule, for both arms (a pair within
+ * ~1e-6 A of r_cut may fall either way in different precisions; both are
+ * valid), so the comparison measures the pair arithmetic alone.  The
+ * context's own force buffer is left in the context's precision.
+ * Synchronises. */
 tbsma_status tbsma_force_check(tbsma_ctx* ctx, tbsma_fcheck* out);
 
 /* Copy the state from / to host buffers of 3*N doubles (SoA, as x and v).

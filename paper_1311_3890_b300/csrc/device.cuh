@@ -14,11 +14,16 @@ constexpr double kAmuKg = 1.66053906660e-27;
 constexpr double kElectronVoltJ = 1.602176634e-19;
 constexpr double kMvv2e = kAmuKg * 1.0e10 / kElectronVoltJ;
 
-// Fixed-point positions: 2^21 units per Angstrom relative to the wire centre.
-// A neighbour difference below 8 A (2^24 units) converts to float exactly.
-constexpr double kFixedScale = 2097152.0;           // 2^21
-constexpr float kFixedInv = 4.76837158203125e-07f;  // 2^-21
-constexpr double kFixedRange = 1023.99;             // |x - centre| limit, A
+// Modular fixed-point positions for the FP32 pair kernels: 2^26 units per
+// Angstrom relative to the wire centre, kept modulo 2^32 (int32 wrap-around).
+// The wrap-around difference of two coordinates is their exact difference
+// whenever that is below 2^31 units = 32 A, which holds for every list pair
+// and for every displacement check; its conversion to float is the correctly
+// rounded FP32 difference.  The grid error (2^-27 A) is ~100x below an FP32
+// ulp of a neighbour distance, so positions carry no coherent error.
+constexpr double kFixedScale = 67108864.0;                 // 2^26
+constexpr float kFixedInv = 1.4901161193847656e-08f;       // 2^-26
+constexpr double kFixedRange = 1.0e9;                      // |x - centre| sanity limit, A
 
 constexpr uint32_t kWireNonFinite = 1u;
 constexpr uint32_t kWireNbrOverflow = 2u;
@@ -56,11 +61,16 @@ struct WireDyn {
 
 // Constants of the pair kernels (Eq. 1-2 rewritten with exp2).
 struct PairConsts {
-  // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-p s} = 2^(-kp (r - r0))
-  float rc2f, r0f, kgf, kpf, xi2f, Af, fpf, fgf;  // fpf = 2 p A / r0, fgf = 2 q xi^2 / r0
+  // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-(p-2q) s} = 2^(-kh (r - r0))
+  float rc2f, r0f, kgf, khf, xi2f, Af, fpf, fgf;  // fpf = 2 p A / r0, fgf = 2 q xi^2 / r0
   // FP64 path
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };
+
+// Exact wrap-around difference of two modular fixed-point coordinates, in A.
+__device__ __forceinline__ float fixed_diff(int a, int b) {
+  return (float)(int)((unsigned)a - (unsigned)b) * kFixedInv;
+}
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32

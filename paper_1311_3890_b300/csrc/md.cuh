@@ -8,7 +8,8 @@
 // keyed by the wire's seed and counted by (atom index in wire, step, tag).
 //
 // Positions and velocities are FP64 throughout; the pair kernels read a
-// packed copy written here (int4 fixed point for MIXED, double4_32a for FP64).
+// packed copy written here (int4 modular fixed point for MIXED, 32-byte aligned
+// double4 for FP64).
 #pragma once
 
 #include "device.cuh"
@@ -86,12 +87,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Modular fixed point: low 32 bits of round(rel * 2^26).
 __device__ __forceinline__ int to_fixed(double rel, uint32_t& bad) {
   if (!(fabs(rel) < kFixedRange)) {
     bad = 1;
     rel = rel != rel ? 0.0 : fmin(fmax(rel, -kFixedRange), kFixedRange);
   }
-  return __double2int_rn(rel * kFixedScale);
+  return (int)(unsigned)(unsigned long long)__double2ll_rn(rel * kFixedScale);
 }
 
 template <int PREC>
@@ -110,8 +112,8 @@ __device__ __forceinline__ void pack_and_check(int64_t i, uint32_t m, const Wire
     xq[i] = q;
     if (check) {
       const int4 b = xq_b[i];
-      const float dx = (float)(q.x - b.x) * kFixedInv, dy = (float)(q.y - b.y) * kFixedInv,
-                  dz = (float)(q.z - b.z) * kFixedInv;
+      const float dx = fixed_diff(q.x, b.x), dy = fixed_diff(q.y, b.y),
+                  dz = fixed_diff(q.z, b.z);
       moved = dx * dx + dy * dy + dz * dz > (float)half_skin2;
     }
   } else {

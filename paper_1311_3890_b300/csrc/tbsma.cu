@@ -145,7 +145,7 @@ void fill_pair_consts(tbsma_ctx* c) {
   k.rc2f = (float)(P.r_cut * P.r_cut);
   k.r0f = (float)P.r0;
   k.kgf = (float)(2.0 * P.q / P.r0 * log2e);
-  k.kpf = (float)(P.p / P.r0 * log2e);
+  k.khf = (float)((P.p - 2.0 * P.q) / P.r0 * log2e);
   k.xi2f = (float)(P.xi * P.xi);
   k.Af = (float)P.A;
   k.fpf = (float)(2.0 * P.p * P.A / P.r0);
@@ -210,18 +210,19 @@ void pair_f32(tbsma_ctx* c, cudaStream_t s) {
                                                c->s_atom);
 }
 
-template <int TPA, bool OBS>
+template <int TPA, bool OBS, bool DECIDE32>
 void pair_f64(tbsma_ctx* c, cudaStream_t s) {
   const unsigned g = grid_for(c->N * TPA, c->block);
-  k_density_f64<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                 c->inv64, c->e_band);
-  k_force_f64<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
-                                               c->inv64, c->f64, c->e_band, c->e_atom, c->w_atom,
-                                               c->s_atom);
+  k_density_f64<TPA, OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                           c->cap, c->pc, c->inv64, c->e_band);
+  k_force_f64<TPA, OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                         c->cap, c->pc, c->inv64, c->f64,
+                                                         c->e_band, c->e_atom, c->w_atom, c->s_atom);
 }
 
+// prec: arithmetic of the pass; decide32: FP64 pass taking the FP32 cutoff rule
 template <bool OBS>
-tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec) {
+tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec, bool decide32 = false) {
   if (prec == TBSMA_MIXED) {
     switch (c->tpa) {
       case 4: pair_f32<4, OBS>(c, s); break;
@@ -229,12 +230,19 @@ tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec) {
       case 16: pair_f32<16, OBS>(c, s); break;
       default: pair_f32<32, OBS>(c, s); break;
     }
+  } else if (decide32) {
+    switch (c->tpa) {
+      case 4: pair_f64<4, OBS, true>(c, s); break;
+      case 8: pair_f64<8, OBS, true>(c, s); break;
+      case 16: pair_f64<16, OBS, true>(c, s); break;
+      default: pair_f64<32, OBS, true>(c, s); break;
+    }
   } else {
     switch (c->tpa) {
-      case 4: pair_f64<4, OBS>(c, s); break;
-      case 8: pair_f64<8, OBS>(c, s); break;
-      case 16: pair_f64<16, OBS>(c, s); break;
-      default: pair_f64<32, OBS>(c, s); break;
+      case 4: pair_f64<4, OBS, false>(c, s); break;
+      case 8: pair_f64<8, OBS, false>(c, s); break;
+      case 16: pair_f64<16, OBS, false>(c, s); break;
+      default: pair_f64<32, OBS, false>(c, s); break;
     }
   }
   TB_CUDA(c, cudaGetLastError());
@@ -254,12 +262,13 @@ void one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
                                                       c->w_atom, c->s_atom);
   } else {
     if (pass == 1)
-      k_density_f64<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                        c->inv64, c->e_band);
+      k_density_f64<TPA, false, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                               c->cap, c->pc, c->inv64, c->e_band);
     else
-      k_force_f64<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                      c->inv64, c->f64, c->e_band, c->e_atom,
-                                                      c->w_atom, c->s_atom);
+      k_force_f64<TPA, false, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                             c->cap, c->pc, c->inv64, c->f64,
+                                                             c->e_band, c->e_atom, c->w_atom,
+                                                             c->s_atom);
   }
 }
 
@@ -479,8 +488,6 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       d.glo[k] = glo;
       d.einv[k] = n / (ghi - glo);
       d.nc[k] = n;
-      if (std::fabs(lo - d.origin[k]) > kFixedRange || std::fabs(hi - d.origin[k]) > kFixedRange)
-        return bail(fail(c, TBSMA_EINVAL, "wire longer than the fixed-point range (2048 A)"));
     }
     d.cell_base = cells;
     cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
@@ -623,7 +630,7 @@ tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
   if (!c || !out) return TBSMA_EINVAL;
   TB_TRY(refresh(c, 0));
   TB_TRY(launch_pair<false>(c, c->stream, TBSMA_MIXED));
-  TB_TRY(launch_pair<true>(c, c->stream, TBSMA_FP64));
+  TB_TRY(launch_pair<true>(c, c->stream, TBSMA_FP64, true));
   k_force_check<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->N, c->f32, c->f64,
                                                               c->s_atom, c->fcheck_d);
   TB_CUDA(c, cudaGetLastError());

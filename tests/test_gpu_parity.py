@@ -409,3 +409,31 @@ def test_full_size_batch_sampled_against_oracle(tb, orc):
         assert np.max(d[ok] / ref.S[ok]) <= 1e-5
         assert norm <= 1e-5
     eng.close()
+
+
+def test_force_error_gate_on_thermalised_wires(tb, orc):
+    """The mixed-precision force check (same positions, same list, same
+    cutoff decisions) on 8 D3 x L40 wires after 1000 steps at 10 K, where
+    near-equilibrium forces are smallest relative to their pair terms, and
+    one of those wires against the oracle."""
+    from inputs.configs import WORKLOADS, build
+
+    b = build(WORKLOADS["batch256_d3_l40"]()[:8])
+    eng = tb.Engine(b, precision="mixed")
+    eng.init_velocities()
+    eng.step(1000, 2.0)
+    fc = eng.force_check()
+    assert fc["max_err_scaled"].max() <= 1e-5
+    assert fc["norm_err"].max() <= 1e-5
+    x = eng.positions()
+    F32, _ = eng.forces(f32=True, f64=False)
+    F32 = F32.double().cpu().numpy()
+    s = b.wire_slice(3)
+    ref = orc.tbsma(x[s], brute_max=0)
+    amb = ambiguous_atoms(orc, x[s], orc.AU.r_cut, 5e-6)
+    ok = np.ones(int(b.n[3]), bool)
+    ok[amb] = False
+    d, fm, _ = force_errors(F32[s], ref.F)
+    assert np.max(d[ok] / ref.S[ok]) <= 1e-5
+    assert np.linalg.norm(d[ok]) <= 1e-5 * np.linalg.norm(fm[ok])
+    eng.close()
