@@ -224,6 +224,35 @@ tbsma_status tbsma_normals(uint64_t seed, const uint32_t* atoms, int64_t n, int6
                            uint32_t tag, tbsma_precision precision, double* out,
                            void* cuda_stream);
 
+/* Allocation-free forces.  The paper has no counterpart to this call; it
+ * exists for callers that may not allocate device memory when they need
+ * forces: a host program that gives its plug-ins a fixed, pre-reserved slice
+ * of the GPU's memory, or code inside a latency-critical loop where a
+ * cudaMalloc would stall the whole device.  It needs no context and no
+ * device allocation (no cudaMalloc or cudaFree, no allocating library call).
+ *
+ * FP64 TB-SMA forces (Eq. 1-3, two passes, hard cutoff) of ONE cluster of
+ * n_atoms <= TBSMA_NOALLOC_MAX_ATOMS atoms; every pair is tested (no list),
+ * so the cost grows as n_atoms^2.  x: device, 3*n_atoms doubles, SoA as
+ * everywhere in this header; f_out: device, 3*n_atoms doubles, written.
+ * The per-atom density scratch lives in one file-scope device array of
+ * TBSMA_NOALLOC_MAX_ATOMS doubles (128 KiB) that every GPU loading this
+ * library holds until the process exits.
+ *   - The first call on each device looks that array up (a CUDA runtime
+ *     query with the device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the array: two calls whose kernels overlap on the GPU
+ *     (e.g. issued on different streams) race and give wrong forces.
+ *     Calls on one stream are ordered and safe.  Each call rewrites every
+ *     slot it reads, so nothing carries over between calls.
+ * Errors: EOVERFLOW if n_atoms > TBSMA_NOALLOC_MAX_ATOMS (nothing launched),
+ * EINVAL for null pointers, n_atoms < 0 or bad parameters, ECUDA if the
+ * lookup or a launch fails.  n_atoms == 0 is a no-op.  Asynchronous on
+ * cuda_stream. */
+#define TBSMA_NOALLOC_MAX_ATOMS 16384
+tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t n_atoms, const double* x,
+                                  double* f_out, void* cuda_stream);
+
 const char* tbsma_last_error(const tbsma_ctx* ctx);
 void tbsma_destroy(tbsma_ctx* ctx);
 

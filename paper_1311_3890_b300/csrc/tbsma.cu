@@ -733,3 +733,100 @@ void tbsma_destroy(tbsma_ctx* c) {
 }
 
 }  // extern "C"
+
+// ======================================================= allocation-free forces
+// Some callers cannot allocate device memory at the point where they need
+// forces: a host application that hands the GPU a fixed, pre-reserved memory
+// budget to plug-ins, or a caller in the middle of a latency-critical loop where
+// cudaMalloc would synchronise the device.  tbsma_forces_noalloc serves them:
+// the FP64 two-pass force of one cluster, pairs found by brute force, with the
+// only scratch (1/(2 sqrt(rho_i)) per atom) in the file-scope array below.
+// Every GPU that loads this library keeps that array until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxAtoms = TBSMA_NOALLOC_MAX_ATOMS;
+static __device__ __align__(256) double g_noalloc_inv[kNoAllocMaxAtoms];
+
+// Device address of g_noalloc_inv, looked up once per device with that
+// device current (in host code the symbol's name is only a host-side stand-in).
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_density(int n, const double* __restrict__ x, PairConsts pc,
+                                  double* __restrict__ inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double xi = x[i], yi = x[n + i], zi = x[2 * n + i];
+  double rho = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const double dx = x[j] - xi, dy = x[n + j] - yi, dz = x[2 * n + j] - zi;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 <= pc.rc2) {
+      const double s = sqrt(r2) / pc.r0 - 1.0;
+      rho += pc.xi2 * exp(-2.0 * pc.q * s);
+    }
+  }
+  inv[i] = rho > 0.0 ? 1.0 / (2.0 * sqrt(rho)) : 0.0;
+}
+
+__global__ void k_noalloc_force(int n, const double* __restrict__ x, PairConsts pc,
+                                const double* __restrict__ inv, double* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double xi = x[i], yi = x[n + i], zi = x[2 * n + i], inv_i = inv[i];
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const double dx = xi - x[j], dy = yi - x[n + j], dz = zi - x[2 * n + j];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 <= pc.rc2) {
+      const double r = sqrt(r2);
+      const double s = r / pc.r0 - 1.0;
+      const double phi = pc.A * exp(-pc.p * s);
+      const double g = pc.xi2 * exp(-2.0 * pc.q * s);
+      const double f = pc.fp * phi - pc.fg * g * (inv_i + inv[j]);
+      fx += f * dx / r;
+      fy += f * dy / r;
+      fz += f * dz / r;
+    }
+  }
+  F[i] = fx;
+  F[n + i] = fy;
+  F[2 * n + i] = fz;
+}
+
+}  // namespace
+
+extern "C" tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t n_atoms,
+                                             const double* x, double* f_out, void* cuda_stream) {
+  if (!params || n_atoms < 0) return TBSMA_EINVAL;
+  if (n_atoms > kNoAllocMaxAtoms) return TBSMA_EOVERFLOW;
+  if (n_atoms == 0) return TBSMA_OK;
+  if (!x || !f_out) return TBSMA_EINVAL;
+  const tbsma_params& P = *params;
+  if (!(P.r0 > 0 && P.r_cut > 0 && P.xi > 0 && P.A >= 0)) return TBSMA_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return TBSMA_ECUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_inv) != cudaSuccess || !p) return TBSMA_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  PairConsts pc{};
+  pc.rc2 = P.r_cut * P.r_cut;
+  pc.r0 = P.r0;
+  pc.A = P.A;
+  pc.xi2 = P.xi * P.xi;
+  pc.p = P.p;
+  pc.q = P.q;
+  pc.fp = 2.0 * P.p / P.r0;
+  pc.fg = 2.0 * P.q / P.r0;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int block = 128;
+  const unsigned grid = (unsigned)((n_atoms + block - 1) / block);
+  // every inv slot the force pass reads is written by the density pass first
+  k_noalloc_density<<<grid, block, 0, s>>>(n_atoms, x, pc, g_noalloc_ptr[dev]);
+  k_noalloc_force<<<grid, block, 0, s>>>(n_atoms, x, pc, g_noalloc_ptr[dev], f_out);
+  return cudaGetLastError() == cudaSuccess ? TBSMA_OK : TBSMA_ECUDA;
+}

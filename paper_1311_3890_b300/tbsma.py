@@ -99,6 +99,7 @@ SIGNATURES = [
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     ("tbsma_normals", ctypes.c_int, [ctypes.c_uint64, _P, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_uint32, ctypes.c_int, _P, _P]),
+    ("tbsma_forces_noalloc", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     ("tbsma_last_error", ctypes.c_char_p, [_P]),
     ("tbsma_destroy", None, [_P]),
 ]
