@@ -64,6 +64,10 @@ def _batch256_d3_l40() -> list[WireSpec]:
     return [WireSpec(3.0, 40.0, 10.0, 1.0e8, s) for s in range(256)]
 
 
+def _batch32_d3_l40() -> list[WireSpec]:
+    return [WireSpec(3.0, 40.0, 10.0, 1.0e8, s) for s in range(32)]
+
+
 def _ragged512() -> list[WireSpec]:
     rng = np.random.default_rng(0xC4)
     d = rng.choice([2.0, 3.0, 4.0], size=512)
@@ -103,6 +107,8 @@ WORKLOADS = {
     "wire_d3_l40": _single_d3_l40,
     # 256 D3 x L40 wires (4.46M atoms), seeds 0..255, 10 K, 1e8 1/s, mixed
     "batch256_d3_l40": _batch256_d3_l40,
+    # 32 D3 x L40 wires (558k atoms): a smaller case of the same kernel shapes
+    "batch32_d3_l40": _batch32_d3_l40,
     # 512 wires, D in {2,3,4} nm, L in [10,60] nm, T in {10,298} K, mixed
     "ragged512": _ragged512,
     # 2048 trajectories over D {2,3,4} x 24 lengths 5..120 nm x T {10,298}

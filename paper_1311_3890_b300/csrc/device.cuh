@@ -42,6 +42,7 @@ struct WireDev {
   int32_t n;
   int32_t n_mobile;
   double origin[3];  // fixed-point origin = centre of the initial bounding box
+  double ofix[3];    // -origin * 2^26 (fixed-point offset, for one FMA per coordinate)
   double glo[3];     // cell-grid lower corner relative to the origin
   double einv[3];    // 1 / cell edge
   int32_t nc[3];     // cells per direction
@@ -56,7 +57,8 @@ struct WireDyn {
   double c1;     // exp(-gamma dt)
   double c2sig;  // sqrt(1 - c1^2) * sqrt(kT/m)  (A/fs)
   double delta;  // grip displacement per step, A
-  double pad;
+  float c1m1f;   // c1 - 1 (FP32 increment form of the O step)
+  float c2sigf;  // c2sig in FP32
 };
 
 // Constants of the pair kernels (Eq. 1-2 rewritten with exp2).

@@ -236,6 +236,84 @@ __global__ void __launch_bounds__(256)
   if (i == w.offset) d_grip[wi] += dy.delta;
 }
 
+// Non-finite test on the exponent bits (integer ops, no FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double a) {
+  return ((__double2hiint(a) >> 20) & 0x7ff) != 0x7ff;
+}
+
+// MIXED step: B A O A with the state accumulated in FP64 and each step's
+// increments formed in FP32 (they come from FP32 forces and noise; their
+// FP32 rounding is ~6e-8 of an increment, far below the force error).
+//   B    v1 = v + dv,            dv = (KICK dt/2m) F
+//   O    v2 = v1 + D,            D  = (c1 - 1) v1 + c2 sqrt(kT/m) n
+//   A+A  x2 = x + dx,            dx = (dt/2)(v1 + v2)
+// This keeps the FP64 work at one add per coordinate and update (B300's FP64
+// pipe is ~1/64 of its FP32 rate).  The packed fixed-point position is one
+// FMA and a conversion per coordinate; the displacement check is integer.
+template <int KICK>
+__global__ void __launch_bounds__(256)
+    k_integrate_mixed(int64_t N, double* __restrict__ x, double* __restrict__ v,
+                      const float* __restrict__ f32, const uint32_t* __restrict__ meta,
+                      const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk,
+                      float hd, const int64_t* __restrict__ step_counter, int4* __restrict__ xq,
+                      const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
+                      uint32_t* wire_status, double* d_grip) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t m = meta[i];
+  const uint32_t wi = meta_wire(m), kind = meta_kind(m);
+  const WireDev& w = wd[wi];
+  double px = x[i], py = x[N + i], pz = x[2 * N + i];
+  double vx = 0.0, vy = 0.0, vz = 0.0;
+  if (kind == 0) {
+    const float c1m1 = wdyn[wi].c1m1f, c2sig = wdyn[wi].c2sigf;
+    vx = v[i] + (double)(hk * f32[i]);
+    vy = v[N + i] + (double)(hk * f32[N + i]);
+    vz = v[2 * N + i] + (double)(hk * f32[2 * N + i]);
+    const float v1x = (float)vx, v1y = (float)vy, v1z = (float)vz;
+    float Dx = 0.f, Dy = 0.f, Dz = 0.f;
+    if (c2sig != 0.f) {
+      const float3 g = normals3_f32(
+          thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step_counter[0], 0u));
+      Dx = fmaf(c1m1, v1x, c2sig * g.x);
+      Dy = fmaf(c1m1, v1y, c2sig * g.y);
+      Dz = fmaf(c1m1, v1z, c2sig * g.z);
+    } else if (c1m1 != 0.f) {
+      Dx = c1m1 * v1x;
+      Dy = c1m1 * v1y;
+      Dz = c1m1 * v1z;
+    }
+    vx += (double)Dx;
+    vy += (double)Dy;
+    vz += (double)Dz;
+    px += (double)(hd * fmaf(2.f, v1x, Dx));
+    py += (double)(hd * fmaf(2.f, v1y, Dy));
+    pz += (double)(hd * fmaf(2.f, v1z, Dz));
+  } else {
+    const double delta = wdyn[wi].delta;
+    px += (kind == 1) ? -delta : delta;
+  }
+  if (i == w.offset) d_grip[wi] += wdyn[wi].delta;
+  x[i] = px;
+  x[N + i] = py;
+  x[2 * N + i] = pz;
+  v[i] = vx;
+  v[N + i] = vy;
+  v[2 * N + i] = vz;
+  if (!(finite_bits(px) & finite_bits(py) & finite_bits(pz) & finite_bits(vx) & finite_bits(vy) &
+        finite_bits(vz)))
+    atomicOr(&wire_status[wi], kWireNonFinite);
+  const double s = kFixedScale;
+  const int4 q = make_int4((int)(unsigned)(unsigned long long)__double2ll_rn(fma(px, s, w.ofix[0])),
+                           (int)(unsigned)(unsigned long long)__double2ll_rn(fma(py, s, w.ofix[1])),
+                           (int)(unsigned)(unsigned long long)__double2ll_rn(fma(pz, s, w.ofix[2])),
+                           (int)m);
+  xq[i] = q;
+  const int4 b = xq_b[i];
+  const float ex = fixed_diff(q.x, b.x), ey = fixed_diff(q.y, b.y), ez = fixed_diff(q.z, b.z);
+  if (ex * ex + ey * ey + ez * ez > half_skin2) flag[wi] = 1;
+}
+
 // Closing half kick of the last step of a sequence.
 template <int PREC>
 __global__ void k_half_kick(int64_t N, double* __restrict__ v, const float* __restrict__ f32,

@@ -65,7 +65,6 @@ struct tbsma_ctx {
   double4_32a* xd_b = nullptr;
   float* f32 = nullptr;
   double* f64 = nullptr;
-  float* inv32 = nullptr;
   double* inv64 = nullptr;
   double* e_band = nullptr;
   double* e_atom = nullptr;
@@ -204,10 +203,9 @@ template <int TPA, bool OBS>
 void pair_f32(tbsma_ctx* c, cudaStream_t s) {
   const unsigned g = grid_for(c->N * TPA, c->block);
   k_density_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                 c->inv32, c->e_band);
+                                                 c->e_band);
   k_force_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                               c->inv32, c->f32, c->e_band, c->e_atom, c->w_atom,
-                                               c->s_atom);
+                                               c->f32, c->e_band, c->e_atom, c->w_atom, c->s_atom);
 }
 
 template <int TPA, bool OBS, bool DECIDE32>
@@ -255,11 +253,11 @@ void one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
   if (c->prec == TBSMA_MIXED) {
     if (pass == 1)
       k_density_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                        c->inv32, c->e_band);
+                                                        c->e_band);
     else
       k_force_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                      c->inv32, c->f32, c->e_band, c->e_atom,
-                                                      c->w_atom, c->s_atom);
+                                                      c->f32, c->e_band, c->e_atom, c->w_atom,
+                                                      c->s_atom);
   } else {
     if (pass == 1)
       k_density_f64<TPA, false, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
@@ -287,9 +285,10 @@ template <int KICK>
 void integrate(tbsma_ctx* c, cudaStream_t s, double dt) {
   const unsigned g = grid_for(c->N, 256);
   if (c->prec == TBSMA_MIXED)
-    k_integrate<TBSMA_MIXED, KICK><<<g, 256, 0, s>>>(
-        c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
-        c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip);
+    k_integrate_mixed<KICK><<<g, 256, 0, s>>>(
+        c->N, c->x, c->v, c->f32, c->meta, c->wd, c->wdyn, (float)(0.5 * KICK * dt * c->inv_m),
+        (float)(0.5 * dt), c->step_counter, c->xq, c->xq_b, (float)c->half_skin2, c->flag,
+        c->wire_status, c->d_grip);
   else
     k_integrate<TBSMA_FP64, KICK><<<g, 256, 0, s>>>(
         c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
@@ -331,7 +330,8 @@ tbsma_status set_dt(tbsma_ctx* c, double dt) {
     dyn[w].c1 = c1;
     dyn[w].c2sig = std::sqrt(std::max(0.0, 1.0 - c1 * c1)) * sig;
     dyn[w].delta = d.strain_rate * 1.0e-15 * d.L0 * dt / 2.0;
-    dyn[w].pad = 0.0;
+    dyn[w].c1m1f = (float)std::expm1(-d.gamma * dt);
+    dyn[w].c2sigf = (float)dyn[w].c2sig;
   }
   TB_CUDA(c, cudaMemcpyAsync(c->wdyn, dyn.data(), sizeof(WireDyn) * c->W, cudaMemcpyHostToDevice,
                              c->stream));
@@ -481,6 +481,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       const double lo = bbox[w * 7 + k], hi = bbox[w * 7 + 3 + k];
       if (!std::isfinite(lo) || !std::isfinite(hi)) return bail(fail(c, TBSMA_EINVAL, "non-finite positions"));
       d.origin[k] = 0.5 * (lo + hi);
+      d.ofix[k] = -d.origin[k] * kFixedScale;
       // along the axis leave room for strain up to 1.0 (each end +L/2)
       const double margin = (k == 0 ? 0.5 * (hi - lo) : 0.0) + rl;
       const double glo = lo - d.origin[k] - margin, ghi = hi - d.origin[k] + margin;
@@ -503,7 +504,6 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->xd_b, N);
   ALLOC(c->f32, 3 * N);
   ALLOC(c->f64, 3 * N);
-  ALLOC(c->inv32, N);
   ALLOC(c->inv64, N);
   ALLOC(c->e_band, N);
   ALLOC(c->e_atom, N);
