@@ -159,49 +159,52 @@ __global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32
   }
 }
 
-constexpr int kBuildWarps = 4;
-constexpr int kBuildMaxCand = 27 * kCellCap;
-constexpr size_t kBuildSmem = (size_t)kBuildWarps * kBuildMaxCand * (sizeof(int32_t) + sizeof(float4));
+// Distance test of the list build on the packed positions (modular fixed
+// point: exact differences; FP64 copies in an FP64 context).
+__device__ __forceinline__ float build_d2(int4 a, int4 b) {
+  const float dx = fixed_diff(b.x, a.x), dy = fixed_diff(b.y, a.y), dz = fixed_diff(b.z, a.z);
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+__device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
+  const double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+  return (float)(dx * dx + dy * dy + dz * dz);
+}
 
-// Warp per flagged cell.  The members of the 27 surrounding cells are staged
-// in shared memory (index + position relative to the cell centre, FP32),
-// then each atom of the cell tests all candidates 32 at a time; accepted
-// indices are compacted with a ballot and written with coalesced stores.
-// The packed position of each rebuilt atom is copied to the build snapshot
-// used by the displacement check.
+constexpr int kBuildLanes = 16;  // lanes cooperating on one atom's list
+
+// kBuildLanes lanes per atom of a flagged wire.  The atom's own cell is
+// recomputed with the binning rule; the 27 surrounding cells are visited in a
+// fixed order and their (sorted) members tested kBuildLanes at a time; the
+// accepted indices are compacted with a ballot and appended with coalesced
+// stores, so the list order is deterministic.  No shared memory, so many
+// warps per SM hide the latency of the cell loads.  The packed position of
+// the atom is copied to the build snapshot used by the displacement check.
 template <typename PosT>
-__global__ void __launch_bounds__(kBuildWarps * 32)
+__global__ void __launch_bounds__(256, 2)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x, int64_t N,
                const int32_t* __restrict__ cell_count, const int32_t* __restrict__ cell_atoms,
-               float rlist2, int32_t* nbr, int32_t* n_nbr, int cap, const PosT* __restrict__ pos,
-               PosT* pos_build, uint32_t* wire_status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* s_pos = reinterpret_cast<float4*>(smem_raw) + warp * kBuildMaxCand;
-  int32_t* s_idx = reinterpret_cast<int32_t*>(smem_raw + kBuildWarps * kBuildMaxCand * sizeof(float4)) +
-                   warp * kBuildMaxCand;
-
+               float rlist2, int32_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
+               const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
+               uint32_t* wire_status) {
+  constexpr int L = kBuildLanes;
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
-  const int64_t total = nw.wl_cell[nf];
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
-       idx += warps) {
-    const int k = wl_find(nw.wl_cell, nf, idx);
+  const int64_t total = nw.wl_atom[nf];
+  const int lane = threadIdx.x & (L - 1);
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1)));
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / L;
+  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L; idx < total;
+       idx += groups) {
+    const int k = wl_find(nw.wl_atom, nf, idx);
     const int wi = nw.wl_wire[k];
     const WireDev& w = wd[wi];
-    const int64_t local = idx - nw.wl_cell[k];
-    const int cz = (int)(local % w.nc[2]);
-    const int cy = (int)((local / w.nc[2]) % w.nc[1]);
-    const int cx = (int)(local / ((int64_t)w.nc[2] * w.nc[1]));
-    const int64_t c = w.cell_base + local;
-    const int cnt_c = min(cell_count[c], kCellCap);
-    if (cnt_c == 0) continue;
-    // centre of this cell relative to the wire origin (staging reference)
-    const double ref0 = w.glo[0] + (cx + 0.5) / w.einv[0];
-    const double ref1 = w.glo[1] + (cy + 0.5) / w.einv[1];
-    const double ref2 = w.glo[2] + (cz + 0.5) / w.einv[2];
-    int ncand = 0, own_base = 0;
+    const int64_t i = w.offset + (idx - nw.wl_atom[k]);
+    const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0]);
+    const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1]);
+    const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
+    const PosT pi = pos[i];
+    int count = 0;
     for (int ox = -1; ox <= 1; ++ox) {
       const int nx = cx + ox;
       if (nx < 0 || nx >= w.nc[0]) continue;
@@ -213,47 +216,29 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
           if (nz < 0 || nz >= w.nc[2]) continue;
           const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
           const int cnt = min(cell_count[cn], kCellCap);
-          if (ox == 0 && oy == 0 && oz == 0) own_base = ncand;
-          if (lane < cnt) {
-            const int32_t j = cell_atoms[cn * kCellCap + lane];
-            s_idx[ncand + lane] = j;
-            s_pos[ncand + lane] = make_float4((float)(x[j] - w.origin[0] - ref0),
-                                              (float)(x[N + j] - w.origin[1] - ref1),
-                                              (float)(x[2 * N + j] - w.origin[2] - ref2), 0.f);
+          for (int base = 0; base < cnt; base += L) {
+            const int kk = base + lane;
+            bool ok = false;
+            int32_t j = -1;
+            if (kk < cnt) {
+              j = cell_atoms[cn * kCellCap + kk];
+              ok = (j != i) && (build_d2(pi, pos[j]) <= rlist2);
+            }
+            const unsigned bal = __ballot_sync(gmask, ok) >> (threadIdx.x & 31 & ~(L - 1));
+            if (ok) {
+              const int p = count + __popc(bal & below);
+              if (p < cap) nbr[i * cap + p] = j;
+            }
+            count += __popc(bal);
           }
-          ncand += cnt;
         }
       }
     }
-    __syncwarp();
-    for (int a = 0; a < cnt_c; ++a) {
-      const int32_t i = s_idx[own_base + a];
-      const float4 pi = s_pos[own_base + a];
-      int count = 0;
-      for (int base = 0; base < ncand; base += 32) {
-        const int kk = base + lane;
-        bool ok = false;
-        int32_t j = -1;
-        if (kk < ncand) {
-          j = s_idx[kk];
-          const float4 pj = s_pos[kk];
-          const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-          ok = (j != i) && (dx * dx + dy * dy + dz * dz <= rlist2);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-          const int p = count + __popc(bal & ((1u << lane) - 1u));
-          if (p < cap) nbr[(int64_t)i * cap + p] = j;
-        }
-        count += __popc(bal);
-      }
-      if (lane == 0) {
-        n_nbr[i] = min(count, cap);
-        if (count > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
-        pos_build[i] = pos[i];
-      }
+    if (lane == 0) {
+      n_nbr[i] = min(count, cap);
+      if (count > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
+      pos_build[i] = pi;
     }
-    __syncwarp();
   }
 }
 

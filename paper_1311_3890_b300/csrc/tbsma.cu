@@ -186,15 +186,15 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
                               c->wire_status);
   k_nl_sort<<<gs * 2, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms);
-  const unsigned gb = (unsigned)(c->sm_count * 3);
+  const unsigned gb = (unsigned)(c->sm_count * 8);
   if (c->prec == TBSMA_MIXED)
-    k_nl_build<int4><<<gb, kBuildWarps * 32, kBuildSmem, s>>>(
-        c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms, c->rlist2, c->nbr, c->n_nbr,
-        c->cap, c->xq, c->xq_b, c->wire_status);
+    k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
+                                        c->rlist2, c->nbr, c->n_nbr, c->cap, c->xq, c->xq_b,
+                                        c->wire_status);
   else
-    k_nl_build<double4_32a><<<gb, kBuildWarps * 32, kBuildSmem, s>>>(
-        c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms, c->rlist2, c->nbr, c->n_nbr,
-        c->cap, c->xd, c->xd_b, c->wire_status);
+    k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count,
+                                               c->cell_atoms, c->rlist2, c->nbr, c->n_nbr, c->cap,
+                                               c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
@@ -435,12 +435,6 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(TBSMA_ECUDA);
-  if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kBuildSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kBuildSmem) != cudaSuccess)
-    return bail(TBSMA_ECUDA);
-
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
 #define ALLOC(ptr, n)                          \
