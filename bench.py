@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "batch256_d3_l40"
-LAUNCH = (8, 128)  # lanes per atom, threads per block of the pair kernels
+LAUNCH = (256, 1024)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
 GRAPH_CHUNK = 50  # steps per captured graph (library constant)
 KERNELS_PER_STEP = 8  # integrate, plan, clear, bin, sort, build, density, force
 METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"
@@ -277,7 +277,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
-                   "lanes_per_atom": LAUNCH[0], "block": LAUNCH[1],
+                   "tile_atoms": LAUNCH[0], "window_atoms": LAUNCH[1],
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
         "roofline": {"kernel": "k_force_f32", "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,

@@ -194,14 +194,17 @@ tbsma_status tbsma_get_wire_status(tbsma_ctx* ctx, int32_t* status_host);
 
 /* Neighbour lists (device): n_nbr[N] and nbr[N * cap] (row i holds atom i's
  * neighbours within r_cut + r_skin, in the library's deterministic order;
- * unused entries undefined).  cap must equal tbsma_nbr_capacity(ctx). */
+ * unused entries -1).  cap must equal tbsma_nbr_capacity(ctx). */
 int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
 tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, int32_t cap);
 
-/* Launch shape of the pair kernels: lanes cooperating on one atom
- * (4, 8, 16 or 32) and threads per block (64..256, multiple of 32).
- * Invalidates captured graphs. */
-tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t lanes_per_atom, int32_t block_threads);
+/* Launch shape of the pair passes: threads per block (64, 128 or 256; one
+ * atom per thread, a block is a tile of consecutive atoms) and the tile's
+ * shared-memory window in atoms (0..4096, 0 = read neighbours from global
+ * memory): a tile whose neighbours span at most that many consecutive atoms
+ * stages their packed positions in shared memory.  Invalidates captured
+ * graphs.  Defaults: 256, 1024. */
+tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t block_threads, int32_t window_atoms);
 
 /* Enqueue `reps` launches of one pair pass on the context's stream, on the
  * current packed positions and lists, in the context's precision and launch

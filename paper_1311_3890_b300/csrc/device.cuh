@@ -69,6 +69,12 @@ struct PairConsts {
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };
 
+// Index of entry k of atom i in the warp-tiled transposed neighbour list:
+// entries k of atoms 32t .. 32t+31 are contiguous (one 128-byte line).
+__host__ __device__ __forceinline__ int64_t nbr_slot(int64_t i, int k, int cap) {
+  return (((i >> 5) * cap + k) << 5) + (i & 31);
+}
+
 // Exact wrap-around difference of two modular fixed-point coordinates, in A.
 __device__ __forceinline__ float fixed_diff(int a, int b) {
   return (float)(int)((unsigned)a - (unsigned)b) * kFixedInv;

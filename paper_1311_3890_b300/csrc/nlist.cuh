@@ -14,6 +14,8 @@
 // every force sum, is deterministic.
 #pragma once
 
+#include <climits>
+
 #include "device.cuh"
 
 namespace tbsma {
@@ -172,7 +174,9 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
 
 constexpr int kBuildLanes = 16;  // lanes cooperating on one atom's list
 
-// kBuildLanes lanes per atom of a flagged wire.  The atom's own cell is
+// kBuildLanes lanes per atom of a flagged wire.  Also records the range
+// [jmin, jmax] of the atom's neighbour indices (the pair passes stage the
+// union of a tile's ranges in shared memory).  The atom's own cell is
 // recomputed with the binning rule; the 27 surrounding cells are visited in a
 // fixed order and their (sorted) members tested kBuildLanes at a time; the
 // accepted indices are compacted with a ballot and appended with coalesced
@@ -184,8 +188,8 @@ __global__ void __launch_bounds__(256, 2)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x, int64_t N,
                const int32_t* __restrict__ cell_count, const int32_t* __restrict__ cell_atoms,
                float rlist2, int32_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
-               const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
-               uint32_t* wire_status) {
+               int2* __restrict__ jrange, const PosT* __restrict__ pos,
+               PosT* __restrict__ pos_build, uint32_t* wire_status) {
   constexpr int L = kBuildLanes;
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
@@ -205,6 +209,7 @@ __global__ void __launch_bounds__(256, 2)
     const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
     const PosT pi = pos[i];
     int count = 0;
+    int jmin = INT_MAX, jmax = INT_MIN;
     for (int ox = -1; ox <= 1; ++ox) {
       const int nx = cx + ox;
       if (nx < 0 || nx >= w.nc[0]) continue;
@@ -227,19 +232,37 @@ __global__ void __launch_bounds__(256, 2)
             const unsigned bal = __ballot_sync(gmask, ok) >> (threadIdx.x & 31 & ~(L - 1));
             if (ok) {
               const int p = count + __popc(bal & below);
-              if (p < cap) nbr[i * cap + p] = j;
+              if (p < cap) nbr[nbr_slot(i, p, cap)] = j;
+              jmin = min(jmin, j);
+              jmax = max(jmax, j);
             }
             count += __popc(bal);
           }
         }
       }
     }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+      jmin = min(jmin, __shfl_xor_sync(gmask, jmin, o));
+      jmax = max(jmax, __shfl_xor_sync(gmask, jmax, o));
+    }
     if (lane == 0) {
       n_nbr[i] = min(count, cap);
+      jrange[i] = make_int2(jmin, jmax);
       if (count > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
       pos_build[i] = pi;
     }
   }
+}
+
+// Row-major copy of the tiled lists (for the list accessor).
+__global__ void k_list_rows(int64_t N, int cap, const int32_t* __restrict__ nbr,
+                            const int32_t* __restrict__ n_nbr, int32_t* __restrict__ rows) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * cap) return;
+  const int64_t i = t / cap;
+  const int k = (int)(t - i * cap);
+  rows[t] = k < n_nbr[i] ? nbr[nbr_slot(i, k, cap)] : -1;
 }
 
 }  // namespace tbsma

@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kGraphChunk = 50;  // steps per captured graph
 constexpr int kDefaultCap = 64;  // neighbour-list row length
+constexpr int kMaxWindow = 4096; // largest shared-memory window of a pair-pass tile, atoms
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
@@ -42,7 +43,8 @@ struct tbsma_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int sm_count = 148;
-  int tpa = 8, block = 128;
+  int block = 256;   // atoms per tile of the pair passes
+  int wcap = 1024;   // shared-memory window of a tile, atoms
   int cap = kDefaultCap;
   int64_t n_cells = 0;
   int64_t steps_done = 0;
@@ -72,6 +74,7 @@ struct tbsma_ctx {
   double* s_atom = nullptr;
   int32_t* nbr = nullptr;
   int32_t* n_nbr = nullptr;
+  int2* jrange = nullptr;
   int32_t* cell_count = nullptr;
   int32_t* cell_atoms = nullptr;
   int32_t* flag = nullptr;
@@ -189,94 +192,55 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   const unsigned gb = (unsigned)(c->sm_count * 8);
   if (c->prec == TBSMA_MIXED)
     k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
-                                        c->rlist2, c->nbr, c->n_nbr, c->cap, c->xq, c->xq_b,
-                                        c->wire_status);
+                                        c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange, c->xq,
+                                        c->xq_b, c->wire_status);
   else
     k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count,
                                                c->cell_atoms, c->rlist2, c->nbr, c->n_nbr, c->cap,
-                                               c->xd, c->xd_b, c->wire_status);
+                                               c->jrange, c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
 
-template <int TPA, bool OBS>
-void pair_f32(tbsma_ctx* c, cudaStream_t s) {
-  const unsigned g = grid_for(c->N * TPA, c->block);
-  k_density_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                 c->e_band);
-  k_force_f32<TPA, OBS><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                               c->f32, c->e_band, c->e_atom, c->w_atom, c->s_atom);
+template <bool OBS>
+void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
+  const unsigned g = grid_for(c->N, c->block);
+  const size_t smem = (size_t)c->wcap * sizeof(int4);
+  if (which & 1)
+    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->jrange, c->cap,
+                                                 c->wcap, c->pc, c->e_band);
+  if (which & 2)
+    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->jrange, c->cap,
+                                               c->wcap, c->pc, c->f32, c->e_band, c->e_atom,
+                                               c->w_atom, c->s_atom);
 }
 
-template <int TPA, bool OBS, bool DECIDE32>
-void pair_f64(tbsma_ctx* c, cudaStream_t s) {
-  const unsigned g = grid_for(c->N * TPA, c->block);
-  k_density_f64<TPA, OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                           c->cap, c->pc, c->inv64, c->e_band);
-  k_force_f64<TPA, OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                         c->cap, c->pc, c->inv64, c->f64,
-                                                         c->e_band, c->e_atom, c->w_atom, c->s_atom);
+template <bool OBS, bool DECIDE32>
+void pair_f64(tbsma_ctx* c, cudaStream_t s, int which = 3) {
+  const unsigned g = grid_for(c->N, c->block);
+  if (which & 1)
+    k_density_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                         c->cap, c->pc, c->inv64, c->e_band);
+  if (which & 2)
+    k_force_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                       c->cap, c->pc, c->inv64, c->f64, c->e_band,
+                                                       c->e_atom, c->w_atom, c->s_atom);
 }
 
 // prec: arithmetic of the pass; decide32: FP64 pass taking the FP32 cutoff rule
 template <bool OBS>
 tbsma_status launch_pair(tbsma_ctx* c, cudaStream_t s, int prec, bool decide32 = false) {
-  if (prec == TBSMA_MIXED) {
-    switch (c->tpa) {
-      case 4: pair_f32<4, OBS>(c, s); break;
-      case 8: pair_f32<8, OBS>(c, s); break;
-      case 16: pair_f32<16, OBS>(c, s); break;
-      default: pair_f32<32, OBS>(c, s); break;
-    }
-  } else if (decide32) {
-    switch (c->tpa) {
-      case 4: pair_f64<4, OBS, true>(c, s); break;
-      case 8: pair_f64<8, OBS, true>(c, s); break;
-      case 16: pair_f64<16, OBS, true>(c, s); break;
-      default: pair_f64<32, OBS, true>(c, s); break;
-    }
-  } else {
-    switch (c->tpa) {
-      case 4: pair_f64<4, OBS, false>(c, s); break;
-      case 8: pair_f64<8, OBS, false>(c, s); break;
-      case 16: pair_f64<16, OBS, false>(c, s); break;
-      default: pair_f64<32, OBS, false>(c, s); break;
-    }
-  }
+  if (prec == TBSMA_MIXED) pair_f32<OBS>(c, s);
+  else if (decide32) pair_f64<OBS, true>(c, s);
+  else pair_f64<OBS, false>(c, s);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
 
-template <int TPA>
-void one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
-  const unsigned g = grid_for(c->N * TPA, c->block);
-  if (c->prec == TBSMA_MIXED) {
-    if (pass == 1)
-      k_density_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                        c->e_band);
-    else
-      k_force_f32<TPA, false><<<g, c->block, 0, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->cap, c->pc,
-                                                      c->f32, c->e_band, c->e_atom, c->w_atom,
-                                                      c->s_atom);
-  } else {
-    if (pass == 1)
-      k_density_f64<TPA, false, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                               c->cap, c->pc, c->inv64, c->e_band);
-    else
-      k_force_f64<TPA, false, false><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                             c->cap, c->pc, c->inv64, c->f64,
-                                                             c->e_band, c->e_atom, c->w_atom,
-                                                             c->s_atom);
-  }
-}
-
+// One pass alone (1 = density, 2 = force), context precision.
 tbsma_status launch_one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
-  switch (c->tpa) {
-    case 4: one_pass<4>(c, s, pass); break;
-    case 8: one_pass<8>(c, s, pass); break;
-    case 16: one_pass<16>(c, s, pass); break;
-    default: one_pass<32>(c, s, pass); break;
-  }
+  if (c->prec == TBSMA_MIXED) pair_f32<false>(c, s, pass);
+  else pair_f64<false, false>(c, s, pass);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
@@ -435,6 +399,12 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(TBSMA_ECUDA);
+  const int smem_max = kMaxWindow * (int)sizeof(int4);
+  if (cudaFuncSetAttribute(k_density_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_density_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
 #define ALLOC(ptr, n)                          \
@@ -503,7 +473,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->e_atom, N);
   ALLOC(c->w_atom, N);
   ALLOC(c->s_atom, N);
-  ALLOC(c->nbr, (size_t)N * c->cap);
+  ALLOC(c->nbr, (size_t)((N + 31) / 32) * 32 * c->cap);
+  ALLOC(c->jrange, N);
   ALLOC(c->n_nbr, N);
   ALLOC(c->cell_count, cells);
   ALLOC(c->cell_atoms, (size_t)cells * kCellCap);
@@ -529,6 +500,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->d_grip, 0, sizeof(double) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->step_counter, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * N, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->jrange, 0, sizeof(int2) * N, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->f32, 0, sizeof(float) * 3 * N, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->f64, 0, sizeof(double) * 3 * N, st) == cudaSuccess;
   if (!ok) return bail(TBSMA_ECUDA);
@@ -669,20 +641,21 @@ tbsma_status tbsma_get_neighbors(tbsma_ctx* c, int32_t* n_nbr, int32_t* nbr, int
   if (!c || cap != c->cap) return TBSMA_EINVAL;
   if (n_nbr)
     TB_CUDA(c, cudaMemcpyAsync(n_nbr, c->n_nbr, c->N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
-  if (nbr)
-    TB_CUDA(c, cudaMemcpyAsync(nbr, c->nbr, (size_t)c->N * c->cap * sizeof(int32_t),
-                               cudaMemcpyDeviceToDevice, c->stream));
+  if (nbr) {
+    k_list_rows<<<grid_for(c->N * c->cap, 256), 256, 0, c->stream>>>(c->N, c->cap, c->nbr, c->n_nbr, nbr);
+    TB_CUDA(c, cudaGetLastError());
+  }
   return TBSMA_OK;
 }
 
-tbsma_status tbsma_set_launch(tbsma_ctx* c, int32_t lanes_per_atom, int32_t block_threads) {
+tbsma_status tbsma_set_launch(tbsma_ctx* c, int32_t block_threads, int32_t window_atoms) {
   if (!c) return TBSMA_EINVAL;
-  if (lanes_per_atom != 4 && lanes_per_atom != 8 && lanes_per_atom != 16 && lanes_per_atom != 32)
-    return fail(c, TBSMA_EINVAL, "lanes_per_atom must be 4, 8, 16 or 32");
-  if (block_threads < 64 || block_threads > 256 || block_threads % 32)
-    return fail(c, TBSMA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
-  c->tpa = lanes_per_atom;
+  if (block_threads != 64 && block_threads != 128 && block_threads != 256)
+    return fail(c, TBSMA_EINVAL, "block_threads must be 64, 128 or 256");
+  if (window_atoms < 0 || window_atoms > kMaxWindow)
+    return fail(c, TBSMA_EINVAL, "window_atoms must be in [0, 4096]");
   c->block = block_threads;
+  c->wcap = window_atoms;
   drop_graph(c);
   return TBSMA_OK;
 }

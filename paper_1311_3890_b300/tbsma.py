@@ -264,8 +264,9 @@ class Engine:
         self._check(lib().tbsma_get_neighbors(self.ctx, _ptr(n), _ptr(nb), cap), "tbsma_get_neighbors")
         return n, nb.view(self.N, cap)
 
-    def set_launch(self, lanes_per_atom: int, block_threads: int):
-        self._check(lib().tbsma_set_launch(self.ctx, lanes_per_atom, block_threads), "tbsma_set_launch")
+    def set_launch(self, block_threads: int, window_atoms: int):
+        """Pair-pass tile size (atoms per block) and shared-memory window (atoms)."""
+        self._check(lib().tbsma_set_launch(self.ctx, block_threads, window_atoms), "tbsma_set_launch")
 
     def run_pass(self, which: int, reps: int = 1):
         """Enqueue `reps` launches of pass 1 (density) or 2 (force) alone."""

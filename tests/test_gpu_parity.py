@@ -91,11 +91,11 @@ def _check_fp64(F, ref, amb):
     return d
 
 
-@pytest.mark.parametrize("tpa", [4, 8, 32])
-def test_forces_fp64_match_oracle(tb, orc, tpa):
+@pytest.mark.parametrize("block,window", [(64, 0), (128, 2048), (256, 512)])
+def test_forces_fp64_match_oracle(tb, orc, block, window):
     b = _jittered_batch()
     eng = tb.Engine(b, precision="fp64")
-    eng.set_launch(tpa, 128)
+    eng.set_launch(block, window)
     _, F64 = eng.forces(f32=False, f64=True)
     F64 = F64.cpu().numpy()
     for w, ref in enumerate(_oracle_forces(orc, b)):
@@ -110,6 +110,8 @@ def test_forces_mixed_match_oracle(tb, orc, sigma, seed):
     # far from the origin: fixed point is relative to each wire's centre
     b.x = b.x + np.array([1000.0, -350.0, 42.0])
     eng = tb.Engine(b, precision="mixed")
+    # staged window, global fallback (window too small), tiles of 64
+    eng.set_launch(*[(256, 2048), (128, 16), (64, 4096)][seed - 1])
     F32, F64 = eng.forces(f32=True, f64=True)
     F32, F64 = F32.double().cpu().numpy(), F64.cpu().numpy()
     n_amb = 0
