@@ -263,10 +263,10 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    # algorithmic bytes per atom of the force pass: own list row (4 n_list) +
-    # n_nbr (4) + own packed position (16) + inv_i (4) + F (12); neighbour
-    # positions and inv_j are re-reads served by L1/L2
-    bytes_force = N * (4.0 * n_list + 4 + 16 + 4 + 12)
+    # algorithmic bytes per atom of the force pass: own list entries (int16,
+    # 2 n_list) + count (4) + list index range (8) + own packed position and
+    # inv (16) + F (12); neighbour positions are re-reads served on chip
+    bytes_force = N * (2.0 * n_list + 4 + 8 + 16 + 12)
     hbm_peak, peak_kind = _peaks()
     achieved = bytes_force / (res[2] * 1e-3) / 1e9
 

@@ -74,7 +74,8 @@ typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
 
 /* Per-wire status bits. */
 #define TBSMA_WIRE_NONFINITE 1u     /* NaN/Inf position or velocity */
-#define TBSMA_WIRE_NBR_OVERFLOW 2u  /* an atom has more neighbours than the list holds */
+#define TBSMA_WIRE_NBR_OVERFLOW 2u  /* an atom has more neighbours than the list holds, or a
+                                       neighbour more than 32767 positions away in the atom order */
 #define TBSMA_WIRE_CELL_OVERFLOW 4u /* a cell holds more atoms than its capacity */
 #define TBSMA_WIRE_RANGE 8u         /* an atom is more than 1e9 A from its wire's centre */
 

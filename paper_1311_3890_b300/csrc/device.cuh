@@ -69,10 +69,17 @@ struct PairConsts {
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };
 
-// Index of entry k of atom i in the warp-tiled transposed neighbour list:
-// entries k of atoms 32t .. 32t+31 are contiguous (one 128-byte line).
+// Neighbour lists hold int16 offsets j - i, warp-tiled and grouped by four:
+// entries 4g..4g+3 of atom i form one 8-byte group, and the groups g of the 32
+// atoms of a tile are contiguous (256 bytes), so a warp reads four entries of
+// each of its atoms with one coalesced load.  cap is a multiple of 4.
+constexpr int kMaxOffset = 32767;  // |j - i| an entry can hold
+
+__host__ __device__ __forceinline__ int64_t nbr_group(int64_t i, int g, int cap) {
+  return ((i >> 5) * (cap >> 2) + g) * 32 + (i & 31);  // in units of 4 entries
+}
 __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t i, int k, int cap) {
-  return (((i >> 5) * cap + k) << 5) + (i & 31);
+  return nbr_group(i, k >> 2, cap) * 4 + (k & 3);  // in entries
 }
 
 // Exact wrap-around difference of two modular fixed-point coordinates, in A.

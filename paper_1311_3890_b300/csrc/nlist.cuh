@@ -187,7 +187,7 @@ template <typename PosT>
 __global__ void __launch_bounds__(256, 2)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x, int64_t N,
                const int32_t* __restrict__ cell_count, const int32_t* __restrict__ cell_atoms,
-               float rlist2, int32_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
+               float rlist2, int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
                int2* __restrict__ jrange, const PosT* __restrict__ pos,
                PosT* __restrict__ pos_build, uint32_t* wire_status) {
   constexpr int L = kBuildLanes;
@@ -228,11 +228,16 @@ __global__ void __launch_bounds__(256, 2)
             if (kk < cnt) {
               j = cell_atoms[cn * kCellCap + kk];
               ok = (j != i) && (build_d2(pi, pos[j]) <= rlist2);
+              if (ok && (j - i > kMaxOffset || i - j > kMaxOffset)) {
+                // not representable as an int16 offset: flag the wire, drop the pair
+                atomicOr(&wire_status[wi], kWireNbrOverflow);
+                ok = false;
+              }
             }
             const unsigned bal = __ballot_sync(gmask, ok) >> (threadIdx.x & 31 & ~(L - 1));
             if (ok) {
               const int p = count + __popc(bal & below);
-              if (p < cap) nbr[nbr_slot(i, p, cap)] = j;
+              if (p < cap) nbr[nbr_slot(i, p, cap)] = (int16_t)(j - i);
               jmin = min(jmin, j);
               jmax = max(jmax, j);
             }
@@ -256,13 +261,13 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // Row-major copy of the tiled lists (for the list accessor).
-__global__ void k_list_rows(int64_t N, int cap, const int32_t* __restrict__ nbr,
+__global__ void k_list_rows(int64_t N, int cap, const int16_t* __restrict__ nbr,
                             const int32_t* __restrict__ n_nbr, int32_t* __restrict__ rows) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= N * cap) return;
   const int64_t i = t / cap;
   const int k = (int)(t - i * cap);
-  rows[t] = k < n_nbr[i] ? nbr[nbr_slot(i, k, cap)] : -1;
+  rows[t] = k < n_nbr[i] ? (int32_t)(i + nbr[nbr_slot(i, k, cap)]) : -1;
 }
 
 }  // namespace tbsma

@@ -72,7 +72,7 @@ struct tbsma_ctx {
   double* e_atom = nullptr;
   double* w_atom = nullptr;
   double* s_atom = nullptr;
-  int32_t* nbr = nullptr;
+  int16_t* nbr = nullptr;
   int32_t* n_nbr = nullptr;
   int2* jrange = nullptr;
   int32_t* cell_count = nullptr;
