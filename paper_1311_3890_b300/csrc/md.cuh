@@ -241,15 +241,40 @@ __device__ __forceinline__ bool finite_bits(double a) {
   return ((__double2hiint(a) >> 20) & 0x7ff) != 0x7ff;
 }
 
+// float -> double by re-biasing the exponent field on the integer pipe (exact
+// for normal numbers; zero and subnormals give a signed zero, Inf/NaN stay
+// Inf/NaN).  B300 runs double conversions on its small FP64 pipe.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned ex = e == 0xffu ? 0x7ff00000u : ((e + 896u) << 20);
+  const unsigned hi = (u & 0x80000000u) | (e ? (ex | ((u >> 3) & 0xfffffu)) : 0u);
+  const unsigned lo = e ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float by truncating the mantissa on the integer pipe (|d| below
+// the float range gives 0, above it Inf; non-finite values are caught by
+// finite_bits on the double).  Used only for FP32 increments of a velocity.
+__device__ __forceinline__ float narrow(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned body = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : (((unsigned)e << 23) | m));
+  return __uint_as_float((hi & 0x80000000u) | body);
+}
+
 // MIXED step: B A O A with the state accumulated in FP64 and each step's
 // increments formed in FP32 (they come from FP32 forces and noise; their
-// FP32 rounding is ~6e-8 of an increment, far below the force error).
-//   B    v1 = v + dv,            dv = (KICK dt/2m) F
-//   O    v2 = v1 + D,            D  = (c1 - 1) v1 + c2 sqrt(kT/m) n
-//   A+A  x2 = x + dx,            dx = (dt/2)(v1 + v2)
-// This keeps the FP64 work at one add per coordinate and update (B300's FP64
-// pipe is ~1/64 of its FP32 rate).  The packed fixed-point position is one
-// FMA and a conversion per coordinate; the displacement check is integer.
+// FP32 rounding is ~1e-7 of an increment, far below the force error):
+//   B    v1 = v + dv,                 dv = (KICK dt/2m) F
+//   O    v2 = v1 + D,                 D  = (c1 - 1) v1 + c2 sqrt(kT/m) n
+//   A+A  x2 = x + (dt/2)(v1 + v2) = x + (dt/2)(2 v1 + D)
+// so that v and x each take one FP64 add (v2 = v + (dv + D)); the FP32 value
+// of v1 is float(v) + dv.  Conversions run on the integer pipe (widen,
+// narrow); B300's FP64 pipe is ~1/64 of its FP32 rate.  The packed
+// fixed-point position is one FMA and a conversion per coordinate; the
+// displacement check is integer.
 template <int KICK>
 __global__ void __launch_bounds__(256)
     k_integrate_mixed(int64_t N, double* __restrict__ x, double* __restrict__ v,
@@ -267,10 +292,11 @@ __global__ void __launch_bounds__(256)
   double vx = 0.0, vy = 0.0, vz = 0.0;
   if (kind == 0) {
     const float c1m1 = wdyn[wi].c1m1f, c2sig = wdyn[wi].c2sigf;
-    vx = v[i] + (double)(hk * f32[i]);
-    vy = v[N + i] + (double)(hk * f32[N + i]);
-    vz = v[2 * N + i] + (double)(hk * f32[2 * N + i]);
-    const float v1x = (float)vx, v1y = (float)vy, v1z = (float)vz;
+    vx = v[i];
+    vy = v[N + i];
+    vz = v[2 * N + i];
+    const float dvx = hk * f32[i], dvy = hk * f32[N + i], dvz = hk * f32[2 * N + i];
+    const float v1x = narrow(vx) + dvx, v1y = narrow(vy) + dvy, v1z = narrow(vz) + dvz;
     float Dx = 0.f, Dy = 0.f, Dz = 0.f;
     if (c2sig != 0.f) {
       const float3 g = normals3_f32(
@@ -283,12 +309,12 @@ __global__ void __launch_bounds__(256)
       Dy = c1m1 * v1y;
       Dz = c1m1 * v1z;
     }
-    vx += (double)Dx;
-    vy += (double)Dy;
-    vz += (double)Dz;
-    px += (double)(hd * fmaf(2.f, v1x, Dx));
-    py += (double)(hd * fmaf(2.f, v1y, Dy));
-    pz += (double)(hd * fmaf(2.f, v1z, Dz));
+    vx += widen(dvx + Dx);
+    vy += widen(dvy + Dy);
+    vz += widen(dvz + Dz);
+    px += widen(hd * fmaf(2.f, v1x, Dx));
+    py += widen(hd * fmaf(2.f, v1y, Dy));
+    pz += widen(hd * fmaf(2.f, v1z, Dz));
   } else {
     const double delta = wdyn[wi].delta;
     px += (kind == 1) ? -delta : delta;
