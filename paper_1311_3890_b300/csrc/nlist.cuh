@@ -118,8 +118,9 @@ __device__ __forceinline__ int cell_coord(double rel, double lo, double einv, in
 }
 
 // Bin the atoms of flagged wires (positions from the caller's FP64 array).
+// The atom's cell coordinates are kept (packed cx << 20 | cy << 10 | cz) for the build.
 __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-                         int64_t N, int32_t* cell_count, int32_t* cell_atoms,
+                         int64_t N, int32_t* cell_count, int32_t* cell_atoms, int32_t* cell_of,
                          uint32_t* wire_status) {
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
@@ -134,6 +135,7 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
     const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1]);
     const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
     const int64_t c = w.cell_base + ((int64_t)cx * w.nc[1] + cy) * w.nc[2] + cz;
+    cell_of[i] = (cx << 20) | (cy << 10) | cz;
     const int slot = atomicAdd(&cell_count[c], 1);
     if (slot < kCellCap) cell_atoms[c * kCellCap + slot] = (int32_t)i;
     else atomicOr(&wire_status[wi], kWireCellOverflow);
@@ -172,44 +174,35 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
   return (float)(dx * dx + dy * dy + dz * dz);
 }
 
-constexpr int kBuildLanes = 16;  // lanes cooperating on one atom's list
-
-// kBuildLanes lanes per atom of a flagged wire.  Also records the range
+// One thread per atom of a flagged wire.  The atom's own cell comes from the
+// binning pass; the 27 surrounding cells are visited in a fixed order and
+// their (sorted) members tested in turn, so the list order is deterministic.
+// The 32 atoms of a warp are consecutive along the wire and share most of
+// their cells, so the cell and position reads hit L1.  Also records the range
 // [jmin, jmax] of the atom's neighbour indices (the pair passes stage the
-// union of a tile's ranges in shared memory).  The atom's own cell is
-// recomputed with the binning rule; the 27 surrounding cells are visited in a
-// fixed order and their (sorted) members tested kBuildLanes at a time; the
-// accepted indices are compacted with a ballot and appended with coalesced
-// stores, so the list order is deterministic.  No shared memory, so many
-// warps per SM hide the latency of the cell loads.  The packed position of
-// the atom is copied to the build snapshot used by the displacement check.
+// union of a tile's ranges in shared memory) and copies the atom's packed
+// position to the build snapshot used by the displacement check.
 template <typename PosT>
-__global__ void __launch_bounds__(256, 2)
-    k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x, int64_t N,
-               const int32_t* __restrict__ cell_count, const int32_t* __restrict__ cell_atoms,
+__global__ void __launch_bounds__(256)
+    k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
+               const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
                float rlist2, int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
                int2* __restrict__ jrange, const PosT* __restrict__ pos,
                PosT* __restrict__ pos_build, uint32_t* wire_status) {
-  constexpr int L = kBuildLanes;
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
   const int64_t total = nw.wl_atom[nf];
-  const int lane = threadIdx.x & (L - 1);
-  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1)));
-  const unsigned below = (1u << lane) - 1u;
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / L;
-  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L; idx < total;
-       idx += groups) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = wl_find(nw.wl_atom, nf, idx);
     const int wi = nw.wl_wire[k];
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (idx - nw.wl_atom[k]);
-    const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0]);
-    const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1]);
-    const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
+    const int co = cell_of[i];
+    const int cx = co >> 20, cy = (co >> 10) & 1023, cz = co & 1023;
     const PosT pi = pos[i];
-    int count = 0;
-    int jmin = INT_MAX, jmax = INT_MIN;
+    int count = 0, jmin = INT_MAX, jmax = INT_MIN;
+    bool far = false;
     for (int ox = -1; ox <= 1; ++ox) {
       const int nx = cx + ox;
       if (nx < 0 || nx >= w.nc[0]) continue;
@@ -221,42 +214,26 @@ __global__ void __launch_bounds__(256, 2)
           if (nz < 0 || nz >= w.nc[2]) continue;
           const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
           const int cnt = min(cell_count[cn], kCellCap);
-          for (int base = 0; base < cnt; base += L) {
-            const int kk = base + lane;
-            bool ok = false;
-            int32_t j = -1;
-            if (kk < cnt) {
-              j = cell_atoms[cn * kCellCap + kk];
-              ok = (j != i) && (build_d2(pi, pos[j]) <= rlist2);
-              if (ok && (j - i > kMaxOffset || i - j > kMaxOffset)) {
-                // not representable as an int16 offset: flag the wire, drop the pair
-                atomicOr(&wire_status[wi], kWireNbrOverflow);
-                ok = false;
-              }
+          const int32_t* members = cell_atoms + cn * kCellCap;
+          for (int m = 0; m < cnt; ++m) {
+            const int32_t j = members[m];
+            if (j == i || build_d2(pi, pos[j]) > rlist2) continue;
+            if (j - i > kMaxOffset || i - j > kMaxOffset) {
+              far = true;  // not representable as an int16 offset: dropped, wire flagged
+              continue;
             }
-            const unsigned bal = __ballot_sync(gmask, ok) >> (threadIdx.x & 31 & ~(L - 1));
-            if (ok) {
-              const int p = count + __popc(bal & below);
-              if (p < cap) nbr[nbr_slot(i, p, cap)] = (int16_t)(j - i);
-              jmin = min(jmin, j);
-              jmax = max(jmax, j);
-            }
-            count += __popc(bal);
+            if (count < cap) nbr[nbr_slot(i, count, cap)] = (int16_t)(j - i);
+            ++count;
+            jmin = min(jmin, j);
+            jmax = max(jmax, j);
           }
         }
       }
     }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) {
-      jmin = min(jmin, __shfl_xor_sync(gmask, jmin, o));
-      jmax = max(jmax, __shfl_xor_sync(gmask, jmax, o));
-    }
-    if (lane == 0) {
-      n_nbr[i] = min(count, cap);
-      jrange[i] = make_int2(jmin, jmax);
-      if (count > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
-      pos_build[i] = pi;
-    }
+    n_nbr[i] = min(count, cap);
+    jrange[i] = make_int2(jmin, jmax);
+    if (count > cap || far) atomicOr(&wire_status[wi], kWireNbrOverflow);
+    pos_build[i] = pi;
   }
 }
 

@@ -77,6 +77,7 @@ struct tbsma_ctx {
   int2* jrange = nullptr;
   int32_t* cell_count = nullptr;
   int32_t* cell_atoms = nullptr;
+  int32_t* cell_of = nullptr;
   int32_t* flag = nullptr;
   int32_t* wl_wire = nullptr;
   int64_t* wl_cell = nullptr;
@@ -187,16 +188,16 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   const unsigned gs = (unsigned)(c->sm_count * 4);
   k_nl_clear<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->cell_count);
   k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
-                              c->wire_status);
+                              c->cell_of, c->wire_status);
   k_nl_sort<<<gs * 2, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms);
   const unsigned gb = (unsigned)(c->sm_count * 8);
   if (c->prec == TBSMA_MIXED)
-    k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
+    k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
                                         c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange, c->xq,
                                         c->xq_b, c->wire_status);
   else
-    k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count,
-                                               c->cell_atoms, c->rlist2, c->nbr, c->n_nbr, c->cap,
+    k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
+                                               c->cell_of, c->rlist2, c->nbr, c->n_nbr, c->cap,
                                                c->jrange, c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
@@ -450,6 +451,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       const double margin = (k == 0 ? 0.5 * (hi - lo) : 0.0) + rl;
       const double glo = lo - d.origin[k] - margin, ghi = hi - d.origin[k] + margin;
       const int n = std::max(1, (int)std::floor((ghi - glo) / rl));
+      if (n > 1023) return bail(fail(c, TBSMA_EINVAL, "wire too large for the cell grid (1023 cells per axis)"));
       d.glo[k] = glo;
       d.einv[k] = n / (ghi - glo);
       d.nc[k] = n;
@@ -475,6 +477,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->s_atom, N);
   ALLOC(c->nbr, (size_t)((N + 31) / 32) * 32 * c->cap);
   ALLOC(c->jrange, N);
+  ALLOC(c->cell_of, N);
   ALLOC(c->n_nbr, N);
   ALLOC(c->cell_count, cells);
   ALLOC(c->cell_atoms, (size_t)cells * kCellCap);
