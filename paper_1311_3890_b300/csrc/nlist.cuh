@@ -174,7 +174,8 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
   return (float)(dx * dx + dy * dy + dz * dz);
 }
 
-// One thread per atom of a flagged wire.  The atom's own cell comes from the
+// One thread per atom of a flagged wire; the list is stored at the atom's
+// slot (see k_slot_order).  The atom's own cell comes from the
 // binning pass; the 27 surrounding cells are visited in a fixed order and
 // their (sorted) members tested in turn, so the list order is deterministic.
 // The 32 atoms of a warp are consecutive along the wire and share most of
@@ -186,9 +187,10 @@ template <typename PosT>
 __global__ void __launch_bounds__(256)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
                const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
-               float rlist2, int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
-               int2* __restrict__ jrange, const PosT* __restrict__ pos,
-               PosT* __restrict__ pos_build, uint32_t* wire_status) {
+               const int32_t* __restrict__ slot_of, float rlist2, int16_t* __restrict__ nbr,
+               int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
+               const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
+               uint32_t* wire_status) {
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
   const int64_t total = nw.wl_atom[nf];
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(256)
     const int wi = nw.wl_wire[k];
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (idx - nw.wl_atom[k]);
+    const int64_t t = slot_of[i];
     const int co = cell_of[i];
     const int cx = co >> 20, cy = (co >> 10) & 1023, cz = co & 1023;
     const PosT pi = pos[i];
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(256)
               far = true;  // not representable as an int16 offset: dropped, wire flagged
               continue;
             }
-            if (count < cap) nbr[nbr_slot(i, count, cap)] = (int16_t)(j - i);
+            if (count < cap) nbr[nbr_slot(t, count, cap)] = (int16_t)(j - i);
             ++count;
             jmin = min(jmin, j);
             jmax = max(jmax, j);
@@ -230,21 +233,57 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    n_nbr[i] = min(count, cap);
-    jrange[i] = make_int2(jmin, jmax);
+    n_nbr[t] = min(count, cap);
+    jrange[t] = make_int2(jmin, jmax);
     if (count > cap || far) atomicOr(&wire_status[wi], kWireNbrOverflow);
     pos_build[i] = pi;
   }
 }
 
 // Row-major copy of the tiled lists (for the list accessor).
+// Either output may be null: counts[N] per atom, rows[N * cap] row-major.
 __global__ void k_list_rows(int64_t N, int cap, const int16_t* __restrict__ nbr,
-                            const int32_t* __restrict__ n_nbr, int32_t* __restrict__ rows) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= N * cap) return;
-  const int64_t i = t / cap;
-  const int k = (int)(t - i * cap);
-  rows[t] = k < n_nbr[i] ? (int32_t)(i + nbr[nbr_slot(i, k, cap)]) : -1;
+                            const int32_t* __restrict__ n_nbr, const int32_t* __restrict__ slot_of,
+                            int32_t* __restrict__ counts, int32_t* __restrict__ rows) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= N * cap) return;
+  const int64_t i = u / cap;
+  const int k = (int)(u - i * cap);
+  const int64_t t = slot_of[i];
+  if (counts && k == 0) counts[i] = n_nbr[t];
+  if (rows) rows[u] = k < n_nbr[t] ? (int32_t)(i + nbr[nbr_slot(t, k, cap)]) : -1;
+}
+
+__global__ void k_iota(int64_t N, int32_t* a, int32_t* b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) a[i] = b[i] = (int32_t)i;
+}
+
+// Slot order of the pair passes.  Within each tile of kSlotTile consecutive
+// atoms the atoms are ranked by list length (longest first, ties by index),
+// so that the 32 threads of a warp walk lists of similar length (the core
+// and surface atoms of a wire alternate along its [100] order).  A tile keeps
+// its set of atoms, so its neighbour-index window is unchanged.  Only the
+// speed depends on this order, never a result: every atom's sums run over
+// its own list in list order.  n_nbr is read in the current slot order.
+constexpr int kSlotTile = 256;
+__global__ void __launch_bounds__(kSlotTile)
+    k_slot_order(int64_t N, const int32_t* __restrict__ n_nbr, int32_t* __restrict__ perm,
+                 int32_t* __restrict__ slot_of) {
+  __shared__ int sn[kSlotTile];
+  const int64_t base = (int64_t)blockIdx.x * kSlotTile;
+  const int a = threadIdx.x;
+  const int m = (int)(N - base < kSlotTile ? N - base : kSlotTile);
+  const int64_t i = base + a;
+  sn[a] = a < m ? n_nbr[slot_of[i]] : -1;
+  __syncthreads();
+  if (a < m) {
+    const int na = sn[a];
+    int rank = 0;
+    for (int b = 0; b < m; ++b) rank += (sn[b] > na) || (sn[b] == na && b < a);
+    perm[base + rank] = (int32_t)i;
+    slot_of[i] = (int32_t)(base + rank);
+  }
 }
 
 }  // namespace tbsma

@@ -78,6 +78,8 @@ struct tbsma_ctx {
   int32_t* cell_count = nullptr;
   int32_t* cell_atoms = nullptr;
   int32_t* cell_of = nullptr;
+  int32_t* perm = nullptr;     // slot -> atom of the pair passes
+  int32_t* slot_of = nullptr;  // atom -> slot
   int32_t* flag = nullptr;
   int32_t* wl_wire = nullptr;
   int64_t* wl_cell = nullptr;
@@ -193,11 +195,11 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   const unsigned gb = (unsigned)(c->sm_count * 8);
   if (c->prec == TBSMA_MIXED)
     k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
-                                        c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange, c->xq,
+                                        c->slot_of, c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange, c->xq,
                                         c->xq_b, c->wire_status);
   else
     k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
-                                               c->cell_of, c->rlist2, c->nbr, c->n_nbr, c->cap,
+                                               c->cell_of, c->slot_of, c->rlist2, c->nbr, c->n_nbr, c->cap,
                                                c->jrange, c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
@@ -208,10 +210,10 @@ void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
   const unsigned g = grid_for(c->N, c->block);
   const size_t smem = (size_t)c->wcap * sizeof(int4);
   if (which & 1)
-    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->jrange, c->cap,
+    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
                                                  c->wcap, c->pc, c->e_band);
   if (which & 2)
-    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->jrange, c->cap,
+    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
                                                c->wcap, c->pc, c->f32, c->e_band, c->e_atom,
                                                c->w_atom, c->s_atom);
 }
@@ -221,10 +223,10 @@ void pair_f64(tbsma_ctx* c, cudaStream_t s, int which = 3) {
   const unsigned g = grid_for(c->N, c->block);
   if (which & 1)
     k_density_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                         c->cap, c->pc, c->inv64, c->e_band);
+                                                         c->perm, c->cap, c->pc, c->inv64, c->e_band);
   if (which & 2)
     k_force_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                       c->cap, c->pc, c->inv64, c->f64, c->e_band,
+                                                       c->perm, c->cap, c->pc, c->inv64, c->f64, c->e_band,
                                                        c->e_atom, c->w_atom, c->s_atom);
 }
 
@@ -478,6 +480,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->nbr, (size_t)((N + 31) / 32) * 32 * c->cap);
   ALLOC(c->jrange, N);
   ALLOC(c->cell_of, N);
+  ALLOC(c->perm, N);
+  ALLOC(c->slot_of, N);
   ALLOC(c->n_nbr, N);
   ALLOC(c->cell_count, cells);
   ALLOC(c->cell_atoms, (size_t)cells * kCellCap);
@@ -508,6 +512,10 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->f64, 0, sizeof(double) * 3 * N, st) == cudaSuccess;
   if (!ok) return bail(TBSMA_ECUDA);
   k_meta<<<std::min(W, 65535), 256, 0, st>>>(W, c->wd, kind, c->meta);
+  // build once in atom order, rank each tile's atoms by list length, build again
+  k_iota<<<grid_for(N, 256), 256, 0, st>>>(N, c->perm, c->slot_of);
+  if ((s = refresh(c, 1)) != TBSMA_OK) return bail(s);
+  k_slot_order<<<grid_for(N, kSlotTile), kSlotTile, 0, st>>>(N, c->n_nbr, c->perm, c->slot_of);
   if ((s = refresh(c, 1)) != TBSMA_OK) return bail(s);
   if ((s = launch_pair<false>(c, st, c->prec)) != TBSMA_OK) return bail(s);
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(TBSMA_ECUDA);
@@ -642,12 +650,10 @@ int32_t tbsma_nbr_capacity(const tbsma_ctx* c) { return c ? c->cap : 0; }
 
 tbsma_status tbsma_get_neighbors(tbsma_ctx* c, int32_t* n_nbr, int32_t* nbr, int32_t cap) {
   if (!c || cap != c->cap) return TBSMA_EINVAL;
-  if (n_nbr)
-    TB_CUDA(c, cudaMemcpyAsync(n_nbr, c->n_nbr, c->N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
-  if (nbr) {
-    k_list_rows<<<grid_for(c->N * c->cap, 256), 256, 0, c->stream>>>(c->N, c->cap, c->nbr, c->n_nbr, nbr);
-    TB_CUDA(c, cudaGetLastError());
-  }
+  if (!n_nbr && !nbr) return TBSMA_OK;
+  k_list_rows<<<grid_for(c->N * c->cap, 256), 256, 0, c->stream>>>(c->N, c->cap, c->nbr, c->n_nbr,
+                                                                   c->slot_of, n_nbr, nbr);
+  TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
 
