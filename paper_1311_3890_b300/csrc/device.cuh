@@ -65,6 +65,7 @@ struct WireDyn {
 struct PairConsts {
   // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-(p-2q) s} = 2^(-kh (r - r0))
   float rc2f, r0f, kgf, khf, xi2f, Af, fpf, fgf;  // fpf = 2 p A / r0, fgf = 2 q xi^2 / r0
+                                                  // rc2f in fixed-point units^2 (2^52 / A^2)
   // FP64 path
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };

@@ -178,6 +178,8 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
 // slot (see k_slot_order).  The atom's own cell comes from the
 // binning pass; the 27 surrounding cells are visited in a fixed order and
 // their (sorted) members tested in turn, so the list order is deterministic.
+// Pairs inside r_cut at build time come first, skin pairs last, so that the
+// lanes of a warp mostly agree on which entries need the exponentials.
 // The 32 atoms of a warp are consecutive along the wire and share most of
 // their cells, so the cell and position reads hit L1.  Also records the range
 // [jmin, jmax] of the atom's neighbour indices (the pair passes stage the
@@ -187,7 +189,8 @@ template <typename PosT>
 __global__ void __launch_bounds__(256)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
                const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
-               const int32_t* __restrict__ slot_of, float rlist2, int16_t* __restrict__ nbr,
+               const int32_t* __restrict__ slot_of, float rlist2, float rcut2,
+               int16_t* __restrict__ nbr,
                int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
                const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
                uint32_t* wire_status) {
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(256)
     const int co = cell_of[i];
     const int cx = co >> 20, cy = (co >> 10) & 1023, cz = co & 1023;
     const PosT pi = pos[i];
-    int count = 0, jmin = INT_MAX, jmax = INT_MIN;
+    int cin = 0, cskin = 0, jmin = INT_MAX, jmax = INT_MIN;
     bool far = false;
     for (int ox = -1; ox <= 1; ++ox) {
       const int nx = cx + ox;
@@ -220,19 +223,30 @@ __global__ void __launch_bounds__(256)
           const int32_t* members = cell_atoms + cn * kCellCap;
           for (int m = 0; m < cnt; ++m) {
             const int32_t j = members[m];
-            if (j == i || build_d2(pi, pos[j]) > rlist2) continue;
+            const float d2 = build_d2(pi, pos[j]);
+            if (j == i || d2 > rlist2) continue;
             if (j - i > kMaxOffset || i - j > kMaxOffset) {
               far = true;  // not representable as an int16 offset: dropped, wire flagged
               continue;
             }
-            if (count < cap) nbr[nbr_slot(t, count, cap)] = (int16_t)(j - i);
-            ++count;
+            // pairs inside r_cut fill the row from the front, skin pairs from the back
+            if (d2 <= rcut2) {
+              if (cin + cskin < cap) nbr[nbr_slot(t, cin, cap)] = (int16_t)(j - i);
+              ++cin;
+            } else {
+              if (cin + cskin < cap) nbr[nbr_slot(t, cap - 1 - cskin, cap)] = (int16_t)(j - i);
+              ++cskin;
+            }
             jmin = min(jmin, j);
             jmax = max(jmax, j);
           }
         }
       }
     }
+    const int count = cin + cskin;
+    if (count <= cap)  // move the skin block next to the in-cutoff block (source ahead of target)
+      for (int q = 0; q < cskin; ++q)
+        nbr[nbr_slot(t, cin + q, cap)] = nbr[nbr_slot(t, cap - cskin + q, cap)];
     n_nbr[t] = min(count, cap);
     jrange[t] = make_int2(jmin, jmax);
     if (count > cap || far) atomicOr(&wire_status[wi], kWireNbrOverflow);
