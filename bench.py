@@ -202,6 +202,79 @@ def launches_in(K: int) -> int:
     return n
 
 
+# Algorithmic work of one force-pass launch (per atom, n_c list entries inside
+# r_cut, n_s skin entries):
+#   FP32 instructions  22 per in-cutoff entry (3 int->float, r^2 3, test 1,
+#                      r 1 + Newton 3, s 1, two exponent arguments 2, bracket 4,
+#                      f/r 1, F 3) and 7 per skin entry (3 + 3 + 1)
+#   MUFU               3 per in-cutoff entry (rsqrt, two ex2)
+#   HBM bytes          2 n_list (int16 list) + 4 (count) + 8 (index range)
+#                      + 16 (own packed position) + 12 (F)
+# Peaks: 128 FP32 lanes and 32 MUFU results per clock per SM (the MUFU rate
+# measured with an ex2 throughput probe on this GPU: 29.9/clk/SM), at the
+# median SM clock sampled during the timed region; HBM from MEASURED_PEAKS.
+# The roofline time is the slower of the ALU time (FP32 and MUFU pipes run
+# concurrently: the larger of the two) and the HBM time.
+FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 22, 7, 3
+
+
+def _list_census(eng, r_cut=5.8, chunk=1 << 20):
+    """Mean in-cutoff and skin entries per atom of the current lists (on the GPU)."""
+    import torch
+
+    n, nb = eng.neighbors()
+    N = eng.N
+    x = eng.x.view(3, N)
+    n_in = 0
+    for s in range(0, N, chunk):
+        rows = nb[s:s + chunk].long()
+        valid = rows >= 0
+        j = rows.clamp(min=0)
+        d2 = torch.zeros(rows.shape, dtype=torch.float64, device=rows.device)
+        for d in range(3):
+            d2 += (x[d][j] - x[d][s:s + chunk, None]) ** 2
+        n_in += int(((d2 <= r_cut * r_cut) & valid).sum().item())
+    n_all = int(n.long().sum().item())
+    return n_in / N, (n_all - n_in) / N
+
+
+def force_roofline(eng, ms, clocks):
+    import torch
+
+    n_c, n_s = _list_census(eng)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2032.0
+    f = mhz * 1e6
+    N = eng.N
+    fp32_ops = N * (FP32_PER_IN * n_c + FP32_PER_SKIN * n_s)
+    mufu_ops = N * MUFU_PER_IN * n_c
+    bytes_ = N * (2.0 * (n_c + n_s) + 4 + 8 + 16 + 12)
+    hbm, kind = _peaks()
+    t_fp32 = fp32_ops / (128 * sms * f)
+    t_mufu = mufu_ops / (32 * sms * f)
+    t_hbm = bytes_ / (hbm * 1e9)
+    t = ms * 1e-3
+    if max(t_fp32, t_mufu) >= t_hbm:
+        if t_fp32 >= t_mufu:
+            bound = {"bound": "alu", "achieved": fp32_ops / t / 1e12,
+                     "peak": 128 * sms * f / 1e12, "unit": "T FP32-inst/s"}
+        else:
+            bound = {"bound": "alu", "achieved": mufu_ops / t / 1e12,
+                     "peak": 32 * sms * f / 1e12, "unit": "T MUFU-op/s"}
+    else:
+        bound = {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s"}
+    bound["frac"] = bound["achieved"] / bound["peak"]
+    bound.update({
+        "kernel": "k_force_f32", "traffic": None, "ms_per_launch": ms,
+        "roofline_ms": 1e3 * max(t_fp32, t_mufu, t_hbm),
+        "t_fp32_ms": 1e3 * t_fp32, "t_mufu_ms": 1e3 * t_mufu, "t_hbm_ms": 1e3 * t_hbm,
+        "hbm_frac": bytes_ / t / 1e9 / hbm, "hbm_peak_kind": kind,
+        "entries_in_cutoff": n_c, "entries_skin": n_s, "sm_mhz": mhz,
+    })
+    return bound
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -251,8 +324,6 @@ def run_ours(args):
     ob = eng.observables()
 
     # dominant kernel (force pass) timed alone with CUDA events on the library's stream
-    n_nbr, _ = eng.neighbors()
-    n_list = float(n_nbr.double().mean().item())
     reps = 20
     res = {}
     for which in (1, 2):
@@ -263,13 +334,8 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    # algorithmic bytes per atom of the force pass: own list entries (int16,
-    # 2 n_list) + count (4) + list index range (8) + own packed position and
-    # inv (16) + F (12); neighbour positions are re-reads served on chip
-    bytes_force = N * (2.0 * n_list + 4 + 8 + 16 + 12)
-    hbm_peak, peak_kind = _peaks()
-    achieved = bytes_force / (res[2] * 1e-3) / 1e9
-
+    roof = force_roofline(eng, res[2], ck)
+    roof["density_ms_per_launch"] = res[1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -279,11 +345,7 @@ def run_ours(args):
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
                    "tile_atoms": LAUNCH[0], "window_atoms": LAUNCH[1],
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
-        "roofline": {"kernel": "k_force_f32", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": None, "peak_kind": peak_kind,
-                     "ms_per_launch": res[2], "density_ms_per_launch": res[1],
-                     "mean_list_len": n_list},
+        "roofline": roof,
         "clocks": ck,
         "gpu_launches": launches_in(args.steps),
         "force_check": {"max_err_scaled": float(fc["max_err_scaled"].max()),
@@ -323,6 +385,7 @@ def run_ours(args):
                              length_nm=40.0, L0=float(batch.L0[w]), temperature=10.0,
                              strain_rate=1e8, gamma=float(batch.gamma[w]), seed=int(batch.seed[w]))])
             e1 = tb.Engine(one, precision="fp64")
+            e1.set_launch(64, 0)  # one 17k-atom wire: small tiles to occupy every SM
             e1.init_velocities()
             e1.step(5, 2.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
