@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--e2e-seg", type=int, default=100, help="MD steps per end-to-end segment")
+    p.add_argument("--autotune", action="store_true",
+                   help="pick the pair passes' launch shape with the autotuner first")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the cpu baseline, fp64 comparison and e2e legs")
     return p.parse_args()
@@ -279,23 +281,27 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from inputs.configs import WORKLOADS, WireSpec, build
+    from inputs.configs import WORKLOADS, build
     import paper_1311_3890_b300 as tb
+    from paper_1311_3890_b300.shard import aggregate, replicate_specs
 
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    specs = WORKLOADS[args.workload]()
-    if rank:
-        specs = [WireSpec(s.diameter_nm, s.length_nm, s.temperature, s.strain_rate,
-                          s.seed + rank * len(specs), s.gamma) for s in specs]
+    specs = replicate_specs(WORKLOADS[args.workload](), rank, world)
     batch = build(specs)
     N, W = batch.n_atoms, batch.n_wires
     eng = tb.Engine(batch, precision="mixed")
-    eng.set_launch(*LAUNCH)
     eng.init_velocities()
     eng.step(max(3, args.warmup), 2.0)
+    launch = LAUNCH
+    if args.autotune:
+        from paper_1311_3890_b300.autotune import tune
+
+        launch, _ = tune(eng)
+    eng.set_launch(*launch)
+    eng.step(3, 2.0)  # capture the graph of the chosen shape outside the timed region
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -312,12 +318,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * N * args.steps / (t_max / 1e3)
+    t_max, atoms_all = aggregate(t_ms, N, device="cuda")
+    value = atoms_all * args.steps / (t_max / 1e3)
 
     # force-error gate on the final state (same positions, same list)
     fc = eng.force_check()
@@ -343,7 +345,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
-                   "tile_atoms": LAUNCH[0], "window_atoms": LAUNCH[1],
+                   "tile_atoms": launch[0], "window_atoms": launch[1],
+                   "launch": "autotuned" if args.autotune else "fixed",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
         "roofline": roof,
         "clocks": ck,

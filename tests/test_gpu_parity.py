@@ -439,3 +439,24 @@ def test_force_error_gate_on_thermalised_wires(tb, orc):
     assert np.max(d[ok] / ref.S[ok]) <= 1e-5
     assert np.linalg.norm(d[ok]) <= 1e-5 * np.linalg.norm(fm[ok])
     eng.close()
+
+
+def test_launch_shape_never_changes_forces_and_autotuner_picks_one(tb, tmp_path):
+    from paper_1311_3890_b300.autotune import CANDIDATES, tune
+
+    b = _jittered_batch(0.05, 17)
+    eng = tb.Engine(b, precision="mixed")
+    ref = None
+    for blk, win in CANDIDATES + [(64, 16)]:
+        eng.set_launch(blk, win)
+        F32, F64 = eng.forces(f32=True, f64=True)
+        cur = (F32.cpu().numpy(), F64.cpu().numpy())
+        if ref is None:
+            ref = cur
+        assert np.array_equal(cur[0], ref[0]) and np.array_equal(cur[1], ref[1])
+    cache = tmp_path / "tune.json"
+    best, entry = tune(eng, cache_path=str(cache), reps=2)
+    assert tuple(best) in CANDIDATES and cache.exists()
+    again, _ = tune(eng, cache_path=str(cache))
+    assert tuple(again) == tuple(best)
+    eng.close()
