@@ -301,7 +301,9 @@ def run_ours(args):
 
         launch, _ = tune(eng)
     eng.set_launch(*launch)
-    eng.step(3, 2.0)  # capture the graph of the chosen shape outside the timed region
+    # capture the step graph the timed call will replay (50-step chunks, or
+    # all K steps when K < 50) outside the timed region
+    eng.step(min(args.steps, GRAPH_CHUNK), 2.0)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
