@@ -77,7 +77,7 @@ typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
 #define TBSMA_WIRE_NBR_OVERFLOW 2u  /* an atom has more neighbours than the list holds, or a
                                        neighbour more than 32767 positions away in the atom order */
 #define TBSMA_WIRE_CELL_OVERFLOW 4u /* a cell holds more atoms than its capacity */
-#define TBSMA_WIRE_RANGE 8u         /* an atom is more than 1e9 A from its wire's centre */
+#define TBSMA_WIRE_RANGE 8u         /* an atom is more than 1e7 A from its wire's centre */
 
 /* TB-SMA parameters (Table 1; r_cut after Eq. 3), list skin and mass.
  * Au: A = 0.2061 eV, xi = 1.790 eV, p = 10.229, q = 4.036, r0 = 2.884 A
@@ -127,7 +127,8 @@ typedef struct {
  * 1.0 along x; atoms outside are clamped into edge cells), builds all
  * neighbour lists and computes the initial forces.  Synchronises.
  * Errors: EINVAL (null pointers, n_wires < 1, wires not packed back to back,
- * bad parameters), ENOMEM, ECUDA: *out is NULL.  EWIRE / EOVERFLOW (a wire
+ * bad parameters, non-finite positions, a wire centred 1e7 A or more from
+ * the coordinate origin), ENOMEM, ECUDA: *out is NULL.  EWIRE / EOVERFLOW (a wire
  * was flagged by the initial build): *out is a valid context that the
  * caller inspects (tbsma_get_wire_status) and destroys. */
 tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, int32_t n_wires,

@@ -23,7 +23,8 @@ constexpr double kMvv2e = kAmuKg * 1.0e10 / kElectronVoltJ;
 // ulp of a neighbour distance, so positions carry no coherent error.
 constexpr double kFixedScale = 67108864.0;                 // 2^26
 constexpr float kFixedInv = 1.4901161193847656e-08f;       // 2^-26
-constexpr double kFixedRange = 1.0e9;                      // |x - centre| sanity limit, A
+constexpr double kFixedRange = 1.0e7;                      // |x - centre| limit of fixed_coord, A
+constexpr double kFixedMagic = 6755399441055744.0;          // 1.5 * 2^52
 
 constexpr uint32_t kWireNonFinite = 1u;
 constexpr uint32_t kWireNbrOverflow = 2u;
@@ -41,8 +42,8 @@ struct WireDev {
   int64_t offset;
   int32_t n;
   int32_t n_mobile;
-  double origin[3];  // fixed-point origin = centre of the initial bounding box
-  double ofix[3];    // -origin * 2^26 (fixed-point offset, for one FMA per coordinate)
+  double origin[3];  // fixed-point origin: centre of the initial bounding box, a multiple of 2^-26
+  double ofixm[3];   // 1.5 * 2^52 - origin * 2^26 (exact): the fixed-point offset of fixed_coord
   double glo[3];     // cell-grid lower corner relative to the origin
   double einv[3];    // 1 / cell edge
   int32_t nc[3];     // cells per direction

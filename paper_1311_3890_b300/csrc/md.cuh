@@ -87,13 +87,25 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Modular fixed point: low 32 bits of round(rel * 2^26).
-__device__ __forceinline__ int to_fixed(double rel, uint32_t& bad) {
+// Modular fixed point: the low 32 bits of round((p - origin) * 2^26), read
+// from the mantissa of a single FMA.  With origin a multiple of 2^-26 the
+// offset 1.5 * 2^52 - origin * 2^26 is exact, so p * 2^26 + offset is rounded
+// once, to nearest even, onto the integer grid of [2^52, 2^53) -- the same
+// value a round-to-nearest conversion of the exact product would give, with
+// no conversion instruction.  Valid while |p - origin| < 2^25 A.
+__device__ __forceinline__ int fixed_coord(double p, double ofixm) {
+  return __double2loint(fma(p, kFixedScale, ofixm));
+}
+
+// fixed_coord with the range check of the packing kernels (a non-finite or
+// far-away coordinate flags the wire and packs a clamped value).
+__device__ __forceinline__ int to_fixed(double p, const WireDev& w, int d, uint32_t& bad) {
+  const double rel = p - w.origin[d];
   if (!(fabs(rel) < kFixedRange)) {
     bad = 1;
-    rel = rel != rel ? 0.0 : fmin(fmax(rel, -kFixedRange), kFixedRange);
+    p = rel != rel ? w.origin[d] : w.origin[d] + fmin(fmax(rel, -kFixedRange), kFixedRange);
   }
-  return (int)(unsigned)(unsigned long long)__double2ll_rn(rel * kFixedScale);
+  return fixed_coord(p, w.ofixm[d]);
 }
 
 template <int PREC>
@@ -106,8 +118,8 @@ __device__ __forceinline__ void pack_and_check(int64_t i, uint32_t m, const Wire
   bool moved = false;
   if (PREC == TBSMA_MIXED) {
     uint32_t bad = 0;
-    const int4 q = make_int4(to_fixed(px - w.origin[0], bad), to_fixed(py - w.origin[1], bad),
-                             to_fixed(pz - w.origin[2], bad), (int)m);
+    const int4 q = make_int4(to_fixed(px, w, 0, bad), to_fixed(py, w, 1, bad),
+                             to_fixed(pz, w, 2, bad), (int)m);
     if (bad) atomicOr(&wire_status[wi], kWireRange);
     xq[i] = q;
     if (check) {
@@ -149,8 +161,8 @@ __global__ void k_pack(int64_t N, const double* __restrict__ x, const uint32_t* 
     xd[i] = make_double4_32a(px, py, pz, __longlong_as_double((long long)m));
   } else {
     uint32_t bad = 0;
-    xq[i] = make_int4(to_fixed(px - w.origin[0], bad), to_fixed(py - w.origin[1], bad),
-                      to_fixed(pz - w.origin[2], bad), (int)m);
+    xq[i] = make_int4(to_fixed(px, w, 0, bad), to_fixed(py, w, 1, bad), to_fixed(pz, w, 2, bad),
+                      (int)m);
     if (bad) atomicOr(&wire_status[meta_wire(m)], kWireRange);
   }
 }
@@ -273,7 +285,7 @@ __device__ __forceinline__ float narrow(double d) {
 // so that v and x each take one FP64 add (v2 = v + (dv + D)); the FP32 value
 // of v1 is float(v) + dv.  Conversions run on the integer pipe (widen,
 // narrow); B300's FP64 pipe is ~1/64 of its FP32 rate.  The packed
-// fixed-point position is one FMA and a conversion per coordinate; the
+// fixed-point position is one FMA per coordinate (fixed_coord); the
 // displacement check is integer.
 template <int KICK>
 __global__ void __launch_bounds__(256)
@@ -329,11 +341,8 @@ __global__ void __launch_bounds__(256)
   if (!(finite_bits(px) & finite_bits(py) & finite_bits(pz) & finite_bits(vx) & finite_bits(vy) &
         finite_bits(vz)))
     atomicOr(&wire_status[wi], kWireNonFinite);
-  const double s = kFixedScale;
-  const int4 q = make_int4((int)(unsigned)(unsigned long long)__double2ll_rn(fma(px, s, w.ofix[0])),
-                           (int)(unsigned)(unsigned long long)__double2ll_rn(fma(py, s, w.ofix[1])),
-                           (int)(unsigned)(unsigned long long)__double2ll_rn(fma(pz, s, w.ofix[2])),
-                           (int)m);
+  const int4 q = make_int4(fixed_coord(px, w.ofixm[0]), fixed_coord(py, w.ofixm[1]),
+                           fixed_coord(pz, w.ofixm[2]), (int)m);
   xq[i] = q;
   const int4 b = xq_b[i];
   const float ex = fixed_diff(q.x, b.x), ey = fixed_diff(q.y, b.y), ez = fixed_diff(q.z, b.z);

@@ -449,8 +449,11 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
     for (int k = 0; k < 3; ++k) {
       const double lo = bbox[w * 7 + k], hi = bbox[w * 7 + 3 + k];
       if (!std::isfinite(lo) || !std::isfinite(hi)) return bail(fail(c, TBSMA_EINVAL, "non-finite positions"));
-      d.origin[k] = 0.5 * (lo + hi);
-      d.ofix[k] = -d.origin[k] * kFixedScale;
+      if (!(std::fabs(0.5 * (lo + hi)) < kFixedRange))
+        return bail(fail(c, TBSMA_EINVAL, "wire centre beyond 1e7 A of the coordinate origin"));
+      // origin on the 2^-26 grid, so that fixed_coord's offset is an exact integer
+      d.origin[k] = std::nearbyint(0.5 * (lo + hi) * kFixedScale) / kFixedScale;
+      d.ofixm[k] = kFixedMagic - d.origin[k] * kFixedScale;
       // along the axis leave room for strain up to 1.0 (each end +L/2)
       const double margin = (k == 0 ? 0.5 * (hi - lo) : 0.0) + rl;
       const double glo = lo - d.origin[k] - margin, ghi = hi - d.origin[k] + margin;
