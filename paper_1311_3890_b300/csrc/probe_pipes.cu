@@ -1,6 +1,6 @@
-// Throughput probe of the two pipes the pair passes use: MUFU ex2 results and
-// FP32 FFMA per SM per clock (8 independent chains per thread, 8 blocks of
-// 1024 threads per SM).  The measured MUFU rate is the denominator of the
+// Throughput probe of the pipes the pair passes use: MUFU ex2 results, FP32
+// FFMA and int32 -> FP32 conversions per SM per clock (8 independent chains
+// per thread, 8 blocks of 1024 threads per SM).  The measured MUFU rate is the denominator of the
 // MUFU side of the force pass's roofline.  Build and run: python -m
 // paper_1311_3890_b300.probe
 #include <cstdio>
@@ -23,6 +23,15 @@ __global__ void k_ffma(float* out, int iters, float seed) {
   float s = 0; for (int k = 0; k < 8; ++k) s += a[k];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+__global__ void k_i2f(float* out, int iters, int seed) {
+  int a[8];
+  for (int k = 0; k < 8; ++k) a[k] = seed + k + threadIdx.x;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) asm volatile("cvt.rn.f32.s32 %0, %0;" : "+r"(a[k]));
+  int s = 0; for (int k = 0; k < 8; ++k) s ^= a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+}
 int main() {
   int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   int clk; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
@@ -37,6 +46,9 @@ int main() {
     cudaEventRecord(a); k_ffma<<<blocks, threads>>>(out, iters, 0.5f); cudaEventRecord(b); cudaEventSynchronize(b);
     cudaEventElapsedTime(&ms, a, b);
     printf("ffma: %.3e ops/s = %.2f per SM per clock\n", ops / (ms * 1e-3), ops / (ms * 1e-3) / sms / (clk * 1e3));
+    cudaEventRecord(a); k_i2f<<<blocks, threads>>>(out, iters, 3); cudaEventRecord(b); cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    printf("i2f: %.3e ops/s = %.2f per SM per clock\n", ops / (ms * 1e-3), ops / (ms * 1e-3) / sms / (clk * 1e3));
   }
   printf("SMs %d\n", sms);
   return 0;
