@@ -220,14 +220,13 @@ __global__ void __launch_bounds__(256)
           if (nz < 0 || nz >= w.nc[2]) continue;
           const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
           const int cnt = min(cell_count[cn], kCellCap);
-          const int32_t* members = cell_atoms + cn * kCellCap;
-          for (int m = 0; m < cnt; ++m) {
-            const int32_t j = members[m];
-            const float d2 = build_d2(pi, pos[j]);
-            if (j == i || d2 > rlist2) continue;
+          const int4* members = reinterpret_cast<const int4*>(cell_atoms + cn * kCellCap);
+          auto visit = [&](int32_t j, const PosT& pj) {
+            const float d2 = build_d2(pi, pj);
+            if (j == i || d2 > rlist2) return;
             if (j - i > kMaxOffset || i - j > kMaxOffset) {
               far = true;  // not representable as an int16 offset: dropped, wire flagged
-              continue;
+              return;
             }
             // pairs inside r_cut fill the row from the front, skin pairs from the back
             if (d2 <= rcut2) {
@@ -239,6 +238,20 @@ __global__ void __launch_bounds__(256)
             }
             jmin = min(jmin, j);
             jmax = max(jmax, j);
+          };
+          // members four at a time (one 16-byte read, then four independent
+          // position reads), tested in member order; slots past the count
+          // are stale and stand in as atom i itself, which visit skips
+          for (int m = 0; m < cnt; m += 4) {
+            const int4 mj = members[m >> 2];
+            const int32_t ii = (int32_t)i;
+            const int32_t j1 = m + 1 < cnt ? mj.y : ii, j2 = m + 2 < cnt ? mj.z : ii,
+                          j3 = m + 3 < cnt ? mj.w : ii;
+            const PosT q0 = pos[mj.x], q1 = pos[j1], q2 = pos[j2], q3 = pos[j3];
+            visit(mj.x, q0);
+            visit(j1, q1);
+            visit(j2, q2);
+            visit(j3, q3);
           }
         }
       }
