@@ -174,96 +174,102 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
   return (float)(dx * dx + dy * dy + dz * dz);
 }
 
-// One thread per atom of a flagged wire; the list is stored at the atom's
-// slot (see k_slot_order).  The atom's own cell comes from the
-// binning pass; the 27 surrounding cells are visited in a fixed order and
-// their (sorted) members tested in turn, so the list order is deterministic.
-// Pairs inside r_cut at build time come first, skin pairs last, so that the
-// lanes of a warp mostly agree on which entries need the exponentials.
-// The 32 atoms of a warp are consecutive along the wire and share most of
-// their cells, so the cell and position reads hit L1.  Also records the range
-// [jmin, jmax] of the atom's neighbour indices (the pair passes stage the
-// union of a tile's ranges in shared memory) and copies the atom's packed
-// position to the build snapshot used by the displacement check.
+// Four threads per atom of a flagged wire (a quad of consecutive lanes);
+// thread q of the quad visits the cells c = 0..26 with c % 4 == q, c the
+// linear index of the offset (ox, oy, oz) in {-1, 0, 1}^3, each cell's
+// (sorted) members in order, four at a time (one 16-byte read of member
+// indices, then four independent position reads).  Accepted pairs go to
+// the thread's shared-memory buffer; the quad then exchanges its counts and
+// writes the row as the concatenation of the four buffers (q = 0 first), so
+// the list order is a fixed function of the cell contents.  Splitting the
+// 27 cells four ways shortens each thread's chain of dependent reads and
+// puts four times as many threads in flight; a rebuild touches only a few
+// wires, so the build is bound by that latency.  The list is stored at the
+// atom's slot (see k_slot_order).  Also records the range [jmin, jmax] of
+// the atom's neighbour indices (the pair passes stage the union of a tile's
+// ranges in shared memory) and copies the atom's packed position to the
+// build snapshot used by the displacement check.
+constexpr int kBuildQuad = 4;
 template <typename PosT>
 __global__ void __launch_bounds__(256)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
                const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
-               const int32_t* __restrict__ slot_of, float rlist2, float rcut2,
-               int16_t* __restrict__ nbr,
+               const int32_t* __restrict__ slot_of, float rlist2, int16_t* __restrict__ nbr,
                int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
                const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
                uint32_t* wire_status) {
+  extern __shared__ int16_t sbuf[];  // [cap][blockDim.x]: entry e of thread x at e * blockDim.x + x
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
-  const int64_t total = nw.wl_atom[nf];
+  const int64_t total = nw.wl_atom[nf] * kBuildQuad;
+  const int q = threadIdx.x & (kBuildQuad - 1);
+  const unsigned quad_mask = 0xfu << (threadIdx.x & 31 & ~(kBuildQuad - 1));
+  // the stride is a multiple of 4, so a quad is always entirely in or out
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int k = wl_find(nw.wl_atom, nf, idx);
+    const int64_t a = idx / kBuildQuad;
+    const int k = wl_find(nw.wl_atom, nf, a);
     const int wi = nw.wl_wire[k];
     const WireDev& w = wd[wi];
-    const int64_t i = w.offset + (idx - nw.wl_atom[k]);
-    const int64_t t = slot_of[i];
+    const int64_t i = w.offset + (a - nw.wl_atom[k]);
+    const int32_t ii = (int32_t)i;
     const int co = cell_of[i];
     const int cx = co >> 20, cy = (co >> 10) & 1023, cz = co & 1023;
     const PosT pi = pos[i];
-    int cin = 0, cskin = 0, jmin = INT_MAX, jmax = INT_MIN;
+    int cnt_mine = 0, jmin = INT_MAX, jmax = INT_MIN;
     bool far = false;
-    for (int ox = -1; ox <= 1; ++ox) {
-      const int nx = cx + ox;
-      if (nx < 0 || nx >= w.nc[0]) continue;
-      for (int oy = -1; oy <= 1; ++oy) {
-        const int ny = cy + oy;
-        if (ny < 0 || ny >= w.nc[1]) continue;
-        for (int oz = -1; oz <= 1; ++oz) {
-          const int nz = cz + oz;
-          if (nz < 0 || nz >= w.nc[2]) continue;
-          const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
-          const int cnt = min(cell_count[cn], kCellCap);
-          const int4* members = reinterpret_cast<const int4*>(cell_atoms + cn * kCellCap);
-          auto visit = [&](int32_t j, const PosT& pj) {
-            const float d2 = build_d2(pi, pj);
-            if (j == i || d2 > rlist2) return;
-            if (j - i > kMaxOffset || i - j > kMaxOffset) {
-              far = true;  // not representable as an int16 offset: dropped, wire flagged
-              return;
-            }
-            // pairs inside r_cut fill the row from the front, skin pairs from the back
-            if (d2 <= rcut2) {
-              if (cin + cskin < cap) nbr[nbr_slot(t, cin, cap)] = (int16_t)(j - i);
-              ++cin;
-            } else {
-              if (cin + cskin < cap) nbr[nbr_slot(t, cap - 1 - cskin, cap)] = (int16_t)(j - i);
-              ++cskin;
-            }
-            jmin = min(jmin, j);
-            jmax = max(jmax, j);
-          };
-          // members four at a time (one 16-byte read, then four independent
-          // position reads), tested in member order; slots past the count
-          // are stale and stand in as atom i itself, which visit skips
-          for (int m = 0; m < cnt; m += 4) {
-            const int4 mj = members[m >> 2];
-            const int32_t ii = (int32_t)i;
-            const int32_t j1 = m + 1 < cnt ? mj.y : ii, j2 = m + 2 < cnt ? mj.z : ii,
-                          j3 = m + 3 < cnt ? mj.w : ii;
-            const PosT q0 = pos[mj.x], q1 = pos[j1], q2 = pos[j2], q3 = pos[j3];
-            visit(mj.x, q0);
-            visit(j1, q1);
-            visit(j2, q2);
-            visit(j3, q3);
-          }
-        }
+    auto visit = [&](int32_t j, const PosT& pj) {
+      const float d2 = build_d2(pi, pj);
+      if (j == ii || d2 > rlist2) return;
+      if (j - ii > kMaxOffset || ii - j > kMaxOffset) {
+        far = true;  // not representable as an int16 offset: dropped, wire flagged
+        return;
+      }
+      if (cnt_mine < cap) sbuf[cnt_mine * blockDim.x + threadIdx.x] = (int16_t)(j - ii);
+      ++cnt_mine;
+      jmin = min(jmin, j);
+      jmax = max(jmax, j);
+    };
+    for (int c = q; c < 27; c += kBuildQuad) {
+      const int nx = cx + c / 9 - 1, ny = cy + (c / 3) % 3 - 1, nz = cz + c % 3 - 1;
+      if (nx < 0 || nx >= w.nc[0] || ny < 0 || ny >= w.nc[1] || nz < 0 || nz >= w.nc[2]) continue;
+      const int64_t cn = w.cell_base + ((int64_t)nx * w.nc[1] + ny) * w.nc[2] + nz;
+      const int cnt = min(cell_count[cn], kCellCap);
+      const int4* members = reinterpret_cast<const int4*>(cell_atoms + cn * kCellCap);
+      // slots past the count are stale and stand in as atom i itself, which visit skips
+      for (int m = 0; m < cnt; m += 4) {
+        const int4 mj = members[m >> 2];
+        const int32_t j1 = m + 1 < cnt ? mj.y : ii, j2 = m + 2 < cnt ? mj.z : ii,
+                      j3 = m + 3 < cnt ? mj.w : ii;
+        const PosT q0 = pos[mj.x], q1 = pos[j1], q2 = pos[j2], q3 = pos[j3];
+        visit(mj.x, q0);
+        visit(j1, q1);
+        visit(j2, q2);
+        visit(j3, q3);
       }
     }
-    const int count = cin + cskin;
-    if (count <= cap)  // move the skin block next to the in-cutoff block (source ahead of target)
-      for (int q = 0; q < cskin; ++q)
-        nbr[nbr_slot(t, cin + q, cap)] = nbr[nbr_slot(t, cap - cskin + q, cap)];
-    n_nbr[t] = min(count, cap);
-    jrange[t] = make_int2(jmin, jmax);
-    if (count > cap || far) atomicOr(&wire_status[wi], kWireNbrOverflow);
-    pos_build[i] = pi;
+    // quad: exclusive prefix of the counts, total, index range
+    int pre = 0, count = 0;
+#pragma unroll
+    for (int r = 0; r < kBuildQuad; ++r) {
+      const int cr = __shfl_sync(quad_mask, cnt_mine, r, kBuildQuad);
+      pre += r < q ? cr : 0;
+      count += cr;
+    }
+#pragma unroll
+    for (int o = 1; o < kBuildQuad; o <<= 1) {
+      jmin = min(jmin, __shfl_xor_sync(quad_mask, jmin, o, kBuildQuad));
+      jmax = max(jmax, __shfl_xor_sync(quad_mask, jmax, o, kBuildQuad));
+    }
+    const int64_t t = slot_of[i];
+    for (int e = 0; e < cnt_mine && e < cap && pre + e < cap; ++e)
+      nbr[nbr_slot(t, pre + e, cap)] = sbuf[e * blockDim.x + threadIdx.x];
+    if (far || (q == 0 && count > cap)) atomicOr(&wire_status[wi], kWireNbrOverflow);
+    if (q == 0) {
+      n_nbr[t] = min(count, cap);
+      jrange[t] = make_int2(jmin, jmax);
+      pos_build[i] = pi;
+    }
   }
 }
 

@@ -98,7 +98,6 @@ struct tbsma_ctx {
 
   PairConsts pc{};
   float rlist2 = 0.f;
-  float rcut2_build = 0.f;  // r_cut^2 in A^2 (list ordering only)
   double half_skin2 = 0.0;
   double inv_m = 0.0;
 
@@ -168,7 +167,6 @@ void fill_pair_consts(tbsma_ctx* c) {
   // displacement check can never drop a pair that reaches r_cut
   const double rl = P.r_cut + P.r_skin + 1e-3;
   c->rlist2 = (float)(rl * rl);
-  c->rcut2_build = (float)(P.r_cut * P.r_cut);
   c->half_skin2 = 0.25 * P.r_skin * P.r_skin;
   c->inv_m = 1.0 / (P.mass * kMvv2e);
 }
@@ -195,14 +193,15 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
                               c->cell_of, c->wire_status);
   k_nl_sort<<<gs * 2, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms);
   const unsigned gb = (unsigned)(c->sm_count * 8);
+  const size_t sbuf = (size_t)256 * c->cap * sizeof(int16_t);  // per-thread entry buffers
   if (c->prec == TBSMA_MIXED)
-    k_nl_build<int4><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
-                                        c->slot_of, c->rlist2, c->rcut2_build, c->nbr, c->n_nbr, c->cap, c->jrange, c->xq,
-                                        c->xq_b, c->wire_status);
+    k_nl_build<int4><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
+                                           c->slot_of, c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange,
+                                           c->xq, c->xq_b, c->wire_status);
   else
-    k_nl_build<double4_32a><<<gb, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
-                                               c->cell_of, c->slot_of, c->rlist2, c->rcut2_build, c->nbr, c->n_nbr, c->cap,
-                                               c->jrange, c->xd, c->xd_b, c->wire_status);
+    k_nl_build<double4_32a><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
+                                                  c->cell_of, c->slot_of, c->rlist2, c->nbr, c->n_nbr,
+                                                  c->cap, c->jrange, c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
