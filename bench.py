@@ -36,6 +36,8 @@ WORKLOAD = "batch256_d3_l40"
 LAUNCH = (256, 1024)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
 GRAPH_CHUNK = 50  # steps per captured graph (library constant)
 KERNELS_PER_STEP = 8  # integrate, plan, clear, bin, sort, build, density, force
+OBS_EVERY = 1000  # per-wire observables reported every OBS_EVERY steps inside the timed region
+KERNELS_PER_OBS = 9  # pack, plan, clear, bin, sort, build, density + force (with energies), reduce
 METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"
 UNIT = "atom-steps/s"
 
@@ -43,8 +45,9 @@ UNIT = "atom-steps/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
-    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--warmup", type=int, default=2000,
+                   help="untimed steps first, so that the rebuild cadence is in steady state")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--e2e-seg", type=int, default=100, help="MD steps per end-to-end segment")
@@ -149,46 +152,77 @@ def oracle_sample(batch, budget_s: float, steps: int | None = None):
     return N * steps / el, W, desc, N, steps
 
 
+def _oracle_run(batch, first_step: int, steps: int, state=None):
+    """Run the FP64 oracle on a batch (one wire per host thread); returns the state."""
+    import oracle
+
+    N = int(batch.n.sum())
+    W = len(batch.n)
+    a = (batch.kind[:N], batch.offset[:W], batch.n, batch.L0[:W], batch.strain_rate[:W],
+         batch.temperature[:W], batch.gamma[:W], batch.seed[:W])
+    if state is None:
+        x, v = batch.x[:N].copy(), np.zeros((N, 3))
+        for w in range(W):  # Gaussian velocities at T, as the GPU arm starts
+            s = slice(int(batch.offset[w]), int(batch.offset[w]) + int(batch.n[w]))
+            v[s] = oracle.init_velocities(batch.kind[s], int(batch.seed[w]),
+                                          float(batch.temperature[w]))
+        F, xb, dg, nr = oracle.md_batch(x, v, *a, 0, 0, 2.0, brute_max=0)
+        state = (x, v, F, xb, dg, nr)
+    x, v, F, xb, dg, nr = state
+    oracle.md_batch(x, v, *a, first_step, steps, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg,
+                    n_rebuild=nr)
+    return state
+
+
 def run_reference(args):
+    """The oracle as it stands, timed on the host on a bounded sample of the workload."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    from inputs import workload
-
-    batch = workload(args.workload)
-    # bound each step so that warmup + steps finish within ~2 minutes
     import oracle
+    from inputs.configs import WORKLOADS, WireSpec, build
 
     threads = oracle.max_threads()
-    per_step_budget = 120.0 / max(1, args.steps + args.warmup)
-    rate_guess = 1.8e5 * threads  # atom-steps/s of the oracle on this workload
-    n_w = int(max(1, min(threads, batch.n_wires, per_step_budget * rate_guess / batch.n[0])))
-    from inputs.wires import Batch
-
-    sub = Batch(x=batch.x[: int(batch.n[:n_w].sum())], kind=batch.kind, offset=batch.offset[:n_w],
-                n=batch.n[:n_w], L0=batch.L0, strain_rate=batch.strain_rate,
-                temperature=batch.temperature, gamma=batch.gamma, seed=batch.seed)
-    N = int(sub.n.sum())
-    x = sub.x.copy()
-    v = np.zeros_like(x)
-    a = (sub.kind[:N], sub.offset, sub.n, sub.L0[:n_w], sub.strain_rate[:n_w],
-         sub.temperature[:n_w], sub.gamma[:n_w], sub.seed[:n_w])
-    F, xb, dg, nr = oracle.md_batch(x, v, *a, 0, max(1, args.warmup), 2.0, brute_max=0)
+    specs = WORKLOADS[args.workload]()
+    total = args.steps + args.warmup
+    budget_s = 120.0
+    # one step of the first wire, alone, sizes the sample
+    one = build(specs[:1])
+    st = _oracle_run(one, 0, 1)
     t = time.perf_counter()
-    oracle.md_batch(x, v, *a, args.warmup, args.steps, 2.0, brute_max=0, F=F, x_build=xb,
-                    d_grip=dg, n_rebuild=nr)
+    _oracle_run(one, 1, 2, st)
+    t_wire = (time.perf_counter() - t) / 2
+    if total * t_wire <= budget_s:
+        sample_specs = specs[: min(threads, len(specs))]
+        sample = (f"{len(sample_specs)} of {len(specs)} wires of the workload, whole, one per "
+                  f"host thread")
+    else:
+        # the same wires shortened (same diameter, temperature, pull, seeds) so that
+        # warm-up + timed steps fit the budget: per-atom work of the oracle is that
+        # of the full wires (same cross-section and neighbourhoods)
+        frac = budget_s / (total * t_wire)
+        length = max(3.0, round(specs[0].length_nm * frac, 1))
+        sample_specs = [WireSpec(sp.diameter_nm, length, sp.temperature, sp.strain_rate, sp.seed,
+                                 sp.gamma) for sp in specs[: min(threads, len(specs))]]
+        sample = (f"{len(sample_specs)} wires D {specs[0].diameter_nm} nm x L {length} nm (the "
+                  f"workload's wires shortened from {specs[0].length_nm} nm so that {total} "
+                  f"steps fit ~{budget_s:.0f} s), one per host thread")
+    sub = build(sample_specs)
+    N = int(sub.n.sum())
+    st = _oracle_run(sub, 0, max(1, args.warmup))
+    t = time.perf_counter()
+    _oracle_run(sub, max(1, args.warmup), args.steps, st)
     el = time.perf_counter() - t
     value = N * args.steps / el
-    sample = f"{n_w} of {batch.n_wires} wires ({N} atoms, one wire per thread) per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "wires": int(batch.n_wires),
-                   "atoms": int(batch.n_atoms), "dt_fs": 2.0},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_w, "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": args.workload, "wires": len(specs), "dt_fs": 2.0,
+                   "temperature_K": specs[0].temperature, "strain_rate_per_s": specs[0].strain_rate},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(sample_specs),
+                         "kind": "oracle", "sample": f"{sample}; {N} atoms"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -196,11 +230,23 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- our path
+def _chunks(K: int):
+    """The timed call sequence: K steps in blocks of OBS_EVERY, observables after each."""
+    out = []
+    while K > 0:
+        out.append(min(OBS_EVERY, K))
+        K -= out[-1]
+    return out
+
+
 def launches_in(K: int) -> int:
-    full, rem = divmod(K, GRAPH_CHUNK) if K >= GRAPH_CHUNK else (0, K)
-    n = full * (KERNELS_PER_STEP * GRAPH_CHUNK + 1)
-    if rem:
-        n += KERNELS_PER_STEP * rem + 1
+    n = 0
+    for k in _chunks(K):
+        full, rem = divmod(k, GRAPH_CHUNK) if k >= GRAPH_CHUNK else (0, k)
+        n += full * (KERNELS_PER_STEP * GRAPH_CHUNK + 1)
+        if rem:
+            n += KERNELS_PER_STEP * rem + 1
+        n += KERNELS_PER_OBS
     return n
 
 
@@ -301,9 +347,9 @@ def run_ours(args):
 
         launch, _ = tune(eng)
     eng.set_launch(*launch)
-    # capture the step graph the timed call will replay (50-step chunks, or
+    # capture the step graph the timed calls will replay (50-step chunks, or
     # all K steps when K < 50) outside the timed region
-    eng.step(min(args.steps, GRAPH_CHUNK), 2.0)
+    eng.step(min(_chunks(args.steps)[0], GRAPH_CHUNK), 2.0)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -313,7 +359,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     ev0.record()
-    eng.step(args.steps, 2.0)
+    for k in _chunks(args.steps):  # the job: steps with per-wire observables every OBS_EVERY
+        eng.step(k, 2.0)
+        ob = eng.observables()
     ev1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -325,7 +373,6 @@ def run_ours(args):
 
     # force-error gate on the final state (same positions, same list)
     fc = eng.force_check()
-    ob = eng.observables()
 
     # dominant kernel (force pass) timed alone with CUDA events on the library's stream
     reps = 20
@@ -347,6 +394,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
+                   "observables_every": OBS_EVERY,
                    "tile_atoms": launch[0], "window_atoms": launch[1],
                    "launch": "autotuned" if args.autotune else "fixed",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
