@@ -264,6 +264,12 @@ def launches_in(K: int) -> int:
 # The roofline time is the slower of the ALU time (FP32 and MUFU pipes run
 # concurrently: the larger of the two) and the HBM time.
 FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 22, 7, 3
+# DRAM bytes (read + write) per atom of one force-pass launch, from an ncu
+# capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms:
+# 71.745 MB read + 1.685 MB written), scaled by the atom count (the traffic is
+# per atom); profiles/pair_integrate_batch32_d3_l40.md.  Set to None when the
+# kernel changes until it is captured again.
+FORCE_TRAFFIC_B_PER_ATOM = 131.6
 
 
 def _list_census(eng, r_cut=5.8, chunk=1 << 20):
@@ -314,7 +320,11 @@ def force_roofline(eng, ms, clocks):
         bound = {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s"}
     bound["frac"] = bound["achieved"] / bound["peak"]
     bound.update({
-        "kernel": "k_force_f32", "traffic": None, "ms_per_launch": ms,
+        "kernel": "k_force_f32",
+        "traffic": None if FORCE_TRAFFIC_B_PER_ATOM is None else FORCE_TRAFFIC_B_PER_ATOM * N,
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per atom, small-case "
+                          "capture scaled by atoms",
+        "ms_per_launch": ms,
         "roofline_ms": 1e3 * max(t_fp32, t_mufu, t_hbm),
         "t_fp32_ms": 1e3 * t_fp32, "t_mufu_ms": 1e3 * t_mufu, "t_hbm_ms": 1e3 * t_hbm,
         "hbm_frac": bytes_ / t / 1e9 / hbm, "hbm_peak_kind": kind,
