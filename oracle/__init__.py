@@ -65,6 +65,18 @@ class _Wire(ctypes.Structure):
     ]
 
 
+class _Protocol(ctypes.Structure):
+    _fields_ = [
+        ("thermostat", ctypes.c_int),
+        ("pull", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("pull_step", ctypes.c_double),
+        ("pull_interval", ctypes.c_int64),
+        ("t_start", ctypes.c_double),
+        ("ramp_steps", ctypes.c_int64),
+    ]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -91,6 +103,12 @@ def _declare(L):
     L.or_md_steps.argtypes = [_P, _P, _P, _I, _P, _P, _P, _P, _P, _I64, _I64, _D, _P, _P, _I]
     L.or_md_batch.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _I64, _D, _P, _P, _I]
     L.or_max_threads.restype = _I
+    L.or_target_temperature.argtypes = [_P, _D, _I64]
+    L.or_target_temperature.restype = _D
+    L.or_md_steps_protocol.argtypes = [_P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _I64, _I64, _D, _P,
+                                       _P, _P, _I]
+    L.or_md_batch_protocol.argtypes = [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _I64,
+                                       _D, _P, _P, _P, _I]
     L.or_observables.argtypes = [_P, _P, _P, _I, _P, _P, _P, _D, _I, _P]
 
 
@@ -311,6 +329,104 @@ def md_batch(x, v, kind, offset, count, L0, strain_rate, temperature, gamma, see
         brute_max,
     )
     return F, x_build, d_grip, n_rebuild
+
+
+@dataclasses.dataclass(frozen=True)
+class Protocol:
+    """Paper protocol mode (Methods, "Simulation details"); see or_md_steps_protocol.
+
+    thermostat: "langevin" (B A O A B) or "nose_hoover" (period tau, fs);
+    pull: "continuous" (strain rate) or "stepwise" (pull_step A per grip every
+    pull_interval steps); temperature ramp from t_start (K) over ramp_steps
+    (0: none).  The paper's values: Nosé–Hoover, 0.05 A every 10000 steps
+    (20 ps at 2 fs), ramp from 0.01 K over 200000 steps (400 ps).
+    """
+
+    thermostat: str = "nose_hoover"
+    pull: str = "stepwise"
+    tau: float = 1000.0
+    pull_step: float = 0.05
+    pull_interval: int = 10000
+    t_start: float = 0.01
+    ramp_steps: int = 0
+
+    def _c(self):
+        th = {"langevin": 0, "nose_hoover": 1}[self.thermostat]
+        pl = {"continuous": 0, "stepwise": 1}[self.pull]
+        return _Protocol(th, pl, self.tau, self.pull_step, int(self.pull_interval), self.t_start,
+                         int(self.ramp_steps))
+
+
+def target_temperature(proto: Protocol, T_w: float, step: int) -> float:
+    return lib().or_target_temperature(ctypes.byref(proto._c()), T_w, int(step))
+
+
+def md_steps_protocol(st: WireState, proto: Protocol, n_steps: int, dt: float,
+                      nh: np.ndarray | None = None, pot: Potential = AU, mass: float = MASS_AU,
+                      r_skin: float = R_SKIN, brute_max: int = 2000):
+    """Advance one wire by n_steps protocol-mode steps in place.
+
+    nh = [xi, eta] (the wire's Nosé–Hoover state, in/out; zeros if None).
+    Returns (st, nh)."""
+    st.x = _f64(st.x)
+    st.v = _f64(st.v)
+    kind = np.ascontiguousarray(st.kind, dtype=np.uint8)
+    if st.F is None:
+        st.F = tbsma(st.x, pot, brute_max).F
+    if st.x_build is None:
+        st.x_build = st.x.copy()
+    nh = np.zeros(2) if nh is None else np.ascontiguousarray(nh, dtype=np.float64)
+    p, m, r = pot._c(), _Md(mass, r_skin), proto._c()
+    w = _Wire(st.L0, st.strain_rate, st.temperature, st.gamma, st.seed)
+    dg = ctypes.c_double(st.d_grip)
+    nr = ctypes.c_int64(st.n_rebuild)
+    lib().or_md_steps_protocol(
+        ctypes.byref(p), ctypes.byref(m), ctypes.byref(w), ctypes.byref(r), st.x.shape[0],
+        _ptr(st.x), _ptr(st.v), _ptr(kind), _ptr(st.F), _ptr(st.x_build), st.step, n_steps, dt,
+        ctypes.byref(dg), ctypes.byref(nr), _ptr(nh), brute_max,
+    )
+    st.step += n_steps
+    st.d_grip = dg.value
+    st.n_rebuild = int(nr.value)
+    return st, nh
+
+
+def md_batch_protocol(proto: Protocol, x, v, kind, offset, count, L0, strain_rate, temperature,
+                      gamma, seed, step0: int, n_steps: int, dt: float, pot: Potential = AU,
+                      mass: float = MASS_AU, r_skin: float = R_SKIN, brute_max: int = 2000,
+                      F=None, x_build=None, d_grip=None, n_rebuild=None, nh=None):
+    """md_batch in protocol mode; nh is (W, 2) [xi, eta] per wire (in/out).
+
+    Returns (F, x_build, d_grip, n_rebuild, nh)."""
+    W = len(count)
+    offset = np.ascontiguousarray(offset, dtype=np.int64)
+    count = np.ascontiguousarray(count, dtype=np.int32)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    if F is None:
+        F = np.zeros_like(x)
+        for w in range(W):
+            s = slice(int(offset[w]), int(offset[w]) + int(count[w]))
+            F[s] = tbsma(x[s], pot, brute_max).F
+    if x_build is None:
+        x_build = x.copy()
+    if d_grip is None:
+        d_grip = np.zeros(W)
+    if n_rebuild is None:
+        n_rebuild = np.zeros(W, dtype=np.int64)
+    if nh is None:
+        nh = np.zeros((W, 2))
+    wires = (_Wire * W)(*[
+        _Wire(float(L0[w]), float(strain_rate[w]), float(temperature[w]), float(gamma[w]),
+              int(seed[w]))
+        for w in range(W)
+    ])
+    p, m, r = pot._c(), _Md(mass, r_skin), proto._c()
+    lib().or_md_batch_protocol(
+        ctypes.byref(p), ctypes.byref(m), ctypes.byref(r), W, wires, _ptr(offset), _ptr(count),
+        _ptr(x), _ptr(v), _ptr(kind), _ptr(F), _ptr(x_build), step0, n_steps, dt, _ptr(d_grip),
+        _ptr(n_rebuild), _ptr(nh), brute_max,
+    )
+    return F, x_build, d_grip, n_rebuild, nh
 
 
 def max_threads() -> int:

@@ -443,6 +443,161 @@ void or_md_batch(const or_pot* P, const or_md* M, int n_wires, const or_wire* W,
   }
 }
 
+/* ======================================================================
+ * Paper protocol mode (Methods, "Simulation details": Nosé–Hoover
+ * thermostat, velocity Verlet with dt = 2 fs, grips displaced by 0.05 A
+ * every 20 ps, temperature ramped from 0.01 K to the target).
+ *
+ * Thermostat (thermostat = 1).  One Nosé–Hoover variable xi per wire with
+ * g = 3 N_mobile degrees of freedom and mass Q = g k_B T_w tau^2 (T_w the
+ * wire's target temperature, tau the thermostat period).  Equations of
+ * motion for the mobile atoms:
+ *   dx/dt = v,  dv/dt = F/m - xi v,  dxi/dt = (2K - g k_B T)/Q,  deta/dt = xi
+ * with K = 1/2 m sum v^2.  A step of length dt is the symmetric splitting
+ *   NH(dt/2)  B(dt/2)  A(dt)  [forces]  B(dt/2)  NH(dt/2)
+ * where B: v += (dt/2) F/m, A: x += dt v, and NH(h) is
+ *   xi += (h/2) (2K - g k_B T)/Q;  v *= exp(-xi h);  eta += h xi;
+ *   xi += (h/2) (2K' - g k_B T)/Q   (K' the kinetic energy after scaling)
+ * (the single-thermostat case of the Martyna–Tuckerman–Klein factorisation).
+ * The extended energy E_pot + K + Q xi^2/2 + g k_B T eta is conserved when
+ * T is constant.  A wire with T_w = 0 or no mobile atom runs NVE (xi = 0).
+ * thermostat = 0 keeps the Langevin B A O A B step of or_md_steps.
+ *
+ * Target temperature at step index s (0-based): T(s) = t_start +
+ * (T_w - t_start) min(1, s / ramp_steps), or T_w when ramp_steps = 0.  The
+ * NH half step at the start of step s and the one at its end use T(s).
+ *
+ * Pull (pull = 1, stepwise): in step s each grip moves by -/+ pull_step
+ * (rigidly) when (s + 1) is a multiple of pull_interval, else not at all;
+ * pull = 0 keeps the continuous delta = strain_rate L0 dt / 2 per step.
+ * ==================================================================== */
+typedef struct {
+  int thermostat;        /* 0 Langevin (B A O A B), 1 Nosé–Hoover */
+  int pull;              /* 0 continuous, 1 stepwise */
+  double tau;            /* Nosé–Hoover period, fs */
+  double pull_step;      /* stepwise: displacement of each grip per event, A */
+  int64_t pull_interval; /* stepwise: steps per event */
+  double t_start;        /* ramp start temperature, K */
+  int64_t ramp_steps;    /* 0: no ramp */
+} or_protocol;
+
+double or_target_temperature(const or_protocol* R, double T_w, int64_t s) {
+  if (R->ramp_steps <= 0) return T_w;
+  double f = (double)s / (double)R->ramp_steps;
+  if (f > 1.0) f = 1.0;
+  return R->t_start + (T_w - R->t_start) * f;
+}
+
+static double kinetic(int n, const double* v, const uint8_t* kind, double m_e) {
+  double v2 = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (kind[i] == 0)
+      v2 += v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+  return 0.5 * m_e * v2;
+}
+
+/* One NH half step of length h on the mobile velocities (see above). */
+static void nh_half(int n, double* v, const uint8_t* kind, double m_e, double g, double kT,
+                    double Q, double h, double* xi, double* eta) {
+  double K = kinetic(n, v, kind, m_e);
+  *xi += 0.5 * h * (2.0 * K - g * kT) / Q;
+  double sc = exp(-*xi * h);
+  for (int i = 0; i < n; ++i)
+    if (kind[i] == 0)
+      for (int d = 0; d < 3; ++d) v[3 * i + d] *= sc;
+  *eta += h * *xi;
+  K = kinetic(n, v, kind, m_e);
+  *xi += 0.5 * h * (2.0 * K - g * kT) / Q;
+}
+
+/* Protocol-mode MD steps for one wire; arguments as or_md_steps, plus the
+ * protocol and the wire's thermostat state nh = {xi, eta} (in/out). */
+void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, const or_protocol* R,
+                          int n, double* x, double* v, const uint8_t* kind, double* F,
+                          double* x_build, int64_t step0, int64_t n_steps, double dt,
+                          double* d_grip, int64_t* n_rebuild, double nh[2], int brute_max) {
+  double m_e = M->mass * OR_MVV2E;
+  double inv_m = 1.0 / m_e;
+  double c1 = exp(-W->gamma * dt);
+  double c2 = sqrt(1.0 - c1 * c1);
+  double half_skin2 = 0.25 * M->r_skin * M->r_skin;
+  long nm = 0;
+  for (int i = 0; i < n; ++i) nm += kind[i] == 0;
+  double g = 3.0 * (double)nm;
+  double Q = g * OR_KB_EV_PER_K * W->temperature * R->tau * R->tau;
+  int nh_on = R->thermostat == 1 && Q > 0.0;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    int64_t step = step0 + s;
+    double T = or_target_temperature(R, W->temperature, step);
+    double kT = OR_KB_EV_PER_K * T;
+    double delta;
+    if (R->pull == 1)
+      delta = (R->pull_interval > 0 && (step + 1) % R->pull_interval == 0) ? R->pull_step : 0.0;
+    else
+      delta = W->strain_rate * 1.0e-15 * W->L0 * dt / 2.0;
+    if (R->thermostat == 1) {
+      if (nh_on) nh_half(n, v, kind, m_e, g, kT, Q, 0.5 * dt, &nh[0], &nh[1]);
+      for (int i = 0; i < n; ++i) {
+        if (kind[i] == 0) {
+          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
+          for (int d = 0; d < 3; ++d) x[3 * i + d] += dt * v[3 * i + d];               /* A */
+        } else {
+          x[3 * i + 0] += (kind[i] == 1) ? -delta : delta;
+          v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+        }
+      }
+    } else {
+      double sig = sqrt(kT * inv_m);
+      for (int i = 0; i < n; ++i) {
+        if (kind[i] == 0) {
+          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
+          for (int d = 0; d < 3; ++d) x[3 * i + d] += 0.5 * dt * v[3 * i + d];         /* A */
+          double gn[3];
+          or_normals3(W->seed, (uint32_t)i, (uint64_t)step, 0, gn);
+          for (int d = 0; d < 3; ++d) v[3 * i + d] = c1 * v[3 * i + d] + c2 * sig * gn[d]; /* O */
+          for (int d = 0; d < 3; ++d) x[3 * i + d] += 0.5 * dt * v[3 * i + d];               /* A */
+        } else {
+          x[3 * i + 0] += (kind[i] == 1) ? -delta : delta;
+          v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+        }
+      }
+    }
+    *d_grip += delta;
+    if (x_build) {
+      int need = 0;
+      for (int i = 0; i < n && !need; ++i) {
+        double dx = x[3 * i] - x_build[3 * i], dy = x[3 * i + 1] - x_build[3 * i + 1],
+               dz = x[3 * i + 2] - x_build[3 * i + 2];
+        if (dx * dx + dy * dy + dz * dz > half_skin2) need = 1;
+      }
+      if (need) {
+        memcpy(x_build, x, sizeof(double) * 3 * n);
+        if (n_rebuild) ++*n_rebuild;
+      }
+    }
+    or_energy_forces(P, n, x, brute_max, F, NULL, NULL, NULL, NULL, NULL, NULL);
+    for (int i = 0; i < n; ++i)
+      if (kind[i] == 0)
+        for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
+    if (nh_on) nh_half(n, v, kind, m_e, g, kT, Q, 0.5 * dt, &nh[0], &nh[1]);
+  }
+}
+
+/* Many wires in protocol mode; nh is [n_wires][2]. */
+void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R, int n_wires,
+                          const or_wire* W, const long* offset, const int* count, double* x,
+                          double* v, const uint8_t* kind, double* F, double* x_build,
+                          int64_t step0, int64_t n_steps, double dt, double* d_grip,
+                          int64_t* n_rebuild, double* nh, int brute_max) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int w = 0; w < n_wires; ++w) {
+    long o = offset[w];
+    or_md_steps_protocol(P, M, &W[w], R, count[w], x + 3 * o, v + 3 * o, kind + o, F + 3 * o,
+                         x_build ? x_build + 3 * o : NULL, step0, n_steps, dt, &d_grip[w],
+                         n_rebuild ? &n_rebuild[w] : NULL, nh + 2 * w, brute_max);
+  }
+}
+
 int or_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

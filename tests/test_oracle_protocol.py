@@ -1,0 +1,175 @@
+"""Pins of the oracle's paper protocol mode (Methods, "Simulation details":
+Nosé–Hoover thermostat, grips displaced by 0.05 A every 20 ps, temperature
+ramped from 0.01 K) against closed forms, conservation laws and physics."""
+
+import math
+
+import numpy as np
+import pytest
+
+from inputs import KIND_GRIP_LEFT, KIND_GRIP_RIGHT, fcc_ball, fcc_wire, jitter
+
+
+def _gas(n=64, spacing=20.0):
+    """n free atoms on a cubic grid 20 A apart: no pair within r_cut, F = 0."""
+    k = int(round(n ** (1 / 3)))
+    g = np.arange(k) * spacing
+    return np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:n].copy()
+
+
+def _kin(orc, v):
+    return 0.5 * orc.MASS_AU * orc.mvv2e() * float(np.sum(v * v))
+
+
+def _nh_run(orc, x, v, T, tau, dt, n_steps, pot=None, kind=None):
+    """Step-by-step NH run; returns per-step (K, xi, eta, E_pot) and the state."""
+    kind = np.zeros(x.shape[0], np.uint8) if kind is None else kind
+    pot = orc.AU if pot is None else pot
+    st = orc.WireState(x=x.copy(), v=v.copy(), kind=kind, L0=1.0, temperature=T)
+    proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=tau)
+    nh = np.zeros(2)
+    rows = []
+    for _ in range(n_steps):
+        st, nh = orc.md_steps_protocol(st, proto, 1, dt, nh=nh, pot=pot)
+        rows.append((_kin(orc, st.v), nh[0], nh[1], orc.energy(st.x, pot)))
+    return np.array(rows), st
+
+
+def test_nh_free_particles_scale_by_exp_minus_eta(orc):
+    """With F = 0 the equations give v(t) = v0 exp(-eta(t)): every NH half
+    step scales v by exp(-xi h) and advances eta by h xi with the same xi, so
+    the discrete scheme keeps this exactly."""
+    x = _gas()
+    rng = np.random.default_rng(1)
+    v0 = 0.002 * rng.standard_normal(x.shape)  # ~950 K against a 300 K target
+    rows, st = _nh_run(orc, x, v0, 300.0, 200.0, 2.0, 300)
+    eta = rows[-1, 2]
+    assert abs(eta) > 0.1  # the thermostat did act
+    np.testing.assert_allclose(st.v, v0 * math.exp(-eta), rtol=1e-12, atol=0)
+
+
+def test_nh_free_particles_invariant_second_order(orc):
+    """For F = 0: dK/dt = -2 xi K, dxi/dt = (2K - g kT)/Q, which conserve
+    H = Q xi^2/2 + K - (g kT/2) ln K.  The splitting keeps H to O(dt^2):
+    halving dt divides its excursion by ~4."""
+    x = _gas()
+    rng = np.random.default_rng(2)
+    v0 = 0.002 * rng.standard_normal(x.shape)  # ~950 K against a 300 K target
+    T, tau = 300.0, 200.0
+    g = 3.0 * x.shape[0]
+    kT = orc.kb() * T
+    Q = g * kT * tau * tau
+    dev = []
+    for dt, n in ((4.0, 250), (2.0, 500)):
+        rows, _ = _nh_run(orc, x, v0, T, tau, dt, n)
+        K, xi = rows[:, 0], rows[:, 1]
+        H = 0.5 * Q * xi**2 + K - 0.5 * g * kT * np.log(K)
+        K0 = _kin(orc, v0)
+        H0 = K0 - 0.5 * g * kT * math.log(K0)
+        dev.append(np.max(np.abs(H - H0)) / (g * kT))
+    assert dev[0] < 1e-3
+    assert 3.0 < dev[0] / dev[1] < 5.0
+
+
+def test_nh_extended_energy_second_order(orc):
+    """An interacting cluster (smooth enough with r_cut = 9 A that no pair
+    crosses the cutoff): E_pot + K + Q xi^2/2 + g kT eta is conserved to
+    O(dt^2)."""
+    P = orc.Potential(r_cut=9.0)
+    x = jitter(fcc_ball(5.0), 0.05, seed=3)
+    n = x.shape[0]
+    rng = np.random.default_rng(4)
+    v0 = 0.002 * rng.standard_normal(x.shape)
+    v0 -= v0.mean(0)
+    T, tau = 150.0, 100.0
+    g = 3.0 * n
+    kT = orc.kb() * T
+    Q = g * kT * tau * tau
+    dev = []
+    for dt, steps in ((2.0, 200), (1.0, 400)):
+        rows, _ = _nh_run(orc, x, v0, T, tau, dt, steps, pot=P)
+        K, xi, eta, E = rows.T
+        H = E + K + 0.5 * Q * xi**2 + g * kT * eta
+        H0 = orc.energy(x, P) + _kin(orc, v0)
+        dev.append(np.max(np.abs(H - H0)))
+    assert dev[0] < 1e-2 * n * kT  # measured 0.0027 eV for 43 atoms at dt = 2 fs
+    assert 3.5 < dev[0] / dev[1] < 4.5
+
+
+def test_nh_mean_temperature(orc):
+    """An fcc ball (135 atoms, Au potential) under NH at 300 K: the time
+    average of T over 10 ps after 2 ps settles within 3 % of the target."""
+    x = fcc_ball(6.5)
+    n = x.shape[0]
+    st = orc.WireState(x=x.copy(), v=orc.init_velocities(np.zeros(n, np.uint8), 5, 300.0),
+                       kind=np.zeros(n, np.uint8), L0=1.0, temperature=300.0)
+    proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=100.0)
+    nh = np.zeros(2)
+    st, nh = orc.md_steps_protocol(st, proto, 1000, 2.0, nh=nh)
+    temps = []
+    for _ in range(100):
+        st, nh = orc.md_steps_protocol(st, proto, 50, 2.0, nh=nh)
+        temps.append(2 * _kin(orc, st.v) / (3 * n * orc.kb()))
+    assert np.mean(temps) == pytest.approx(300.0, rel=0.03)
+
+
+def test_stepwise_pull_closed_form(orc):
+    """Stepwise pull: each grip moves rigidly by -/+ pull_step exactly in the
+    steps s with (s + 1) a multiple of the interval, and not otherwise."""
+    w = fcc_wire(2.0, 3.5)
+    kind = w.kind
+    st = orc.WireState(x=w.x.copy(), v=np.zeros_like(w.x), kind=kind, L0=w.L0, temperature=0.0,
+                       strain_rate=1e9)  # the strain rate must be ignored in stepwise mode
+    proto = orc.Protocol(thermostat="nose_hoover", pull="stepwise", pull_step=0.05,
+                         pull_interval=40)
+    left, right = kind == KIND_GRIP_LEFT, kind == KIND_GRIP_RIGHT
+    x0 = w.x.copy()
+    nh = np.zeros(2)
+    for s in range(130):
+        before = st.x.copy()
+        st, nh = orc.md_steps_protocol(st, proto, 1, 2.0, nh=nh)
+        jump = 0.05 if (s + 1) % 40 == 0 else 0.0
+        np.testing.assert_array_equal(st.x[left, 1:], before[left, 1:])
+        np.testing.assert_allclose(st.x[left, 0] - before[left, 0], -jump, atol=1e-12)
+        np.testing.assert_allclose(st.x[right, 0] - before[right, 0], jump, atol=1e-12)
+    assert st.d_grip == pytest.approx(0.05 * 3, abs=1e-12)
+    np.testing.assert_allclose(st.x[right, 0] - x0[right, 0], 0.15, atol=1e-12)
+
+
+def test_ramp_is_followed_by_a_strong_thermostat(orc):
+    """A strongly damped Langevin run (gamma = 0.05 1/fs) of a free gas
+    follows the ramp 0.01 K -> 200 K over 4000 steps: the temperature over
+    the last 500 ramp steps averages the ramp's own average there (within
+    sampling noise), and at step 2000 the target is halfway."""
+    x = _gas(216)
+    n = x.shape[0]
+    proto = orc.Protocol(thermostat="langevin", pull="continuous", t_start=0.01, ramp_steps=4000)
+    assert orc.target_temperature(proto, 200.0, 0) == pytest.approx(0.01)
+    assert orc.target_temperature(proto, 200.0, 2000) == pytest.approx(100.005)
+    assert orc.target_temperature(proto, 200.0, 9000) == pytest.approx(200.0)
+    st = orc.WireState(x=x.copy(), v=np.zeros_like(x), kind=np.zeros(n, np.uint8), L0=1.0,
+                       temperature=200.0, gamma=0.05, seed=9)
+    temps, targets = [], []
+    for s in range(4000):
+        st, _ = orc.md_steps_protocol(st, proto, 1, 2.0)
+        if s >= 3500:
+            temps.append(2 * _kin(orc, st.v) / (3 * n * orc.kb()))
+            targets.append(orc.target_temperature(proto, 200.0, s))
+    # mean over 500 correlated samples of a 648-dof gas: relative noise ~1 %
+    assert np.mean(temps) == pytest.approx(np.mean(targets), rel=0.04)
+
+
+def test_protocol_langevin_continuous_equals_md_steps(orc):
+    """With the Langevin thermostat, continuous pull and no ramp the protocol
+    integrator is the B A O A B integrator, bit for bit."""
+    w = fcc_wire(2.0, 3.5)
+    v = orc.init_velocities(w.kind, 3, 50.0)
+    a = orc.WireState(x=w.x.copy(), v=v.copy(), kind=w.kind, L0=w.L0, strain_rate=1e9,
+                      temperature=50.0, gamma=1e-3, seed=3)
+    b = orc.WireState(x=w.x.copy(), v=v.copy(), kind=w.kind, L0=w.L0, strain_rate=1e9,
+                      temperature=50.0, gamma=1e-3, seed=3)
+    orc.md_steps(a, 30, 2.0)
+    orc.md_steps_protocol(b, orc.Protocol(thermostat="langevin", pull="continuous"), 30, 2.0)
+    np.testing.assert_array_equal(a.x, b.x)
+    np.testing.assert_array_equal(a.v, b.v)
+    assert a.d_grip == b.d_grip and a.n_rebuild == b.n_rebuild
