@@ -162,11 +162,57 @@ tbsma_status tbsma_atom_energies(tbsma_ctx* ctx, double* e_out, double* w_out);
 
 /* Advance every wire by n_steps steps of dt_fs: B A O A (mobile atoms; grips
  * shifted rigidly), displacement check, list rebuild of flagged wires,
- * density pass, force pass, B.  Replays a captured CUDA graph; the first
+ * density pass, force pass, B (under the Nosé–Hoover protocol: NH B A,
+ * ..., B NH; see tbsma_set_protocol).  Replays a captured CUDA graph; the first
  * call with a new dt captures it.  Synchronises at the end to read the
  * wires' status words.  Errors: EINVAL (n_steps < 0, dt_fs <= 0), EWIRE,
  * EOVERFLOW, ECUDA. */
 tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
+
+/* Paper protocol mode (Methods, "Simulation details": Nosé–Hoover
+ * thermostat with velocity Verlet, dt = 2 fs; grips displaced by 0.05 A
+ * every 20 ps; temperature ramped from 0.01 K to the target).  Applies to
+ * every wire of the context from the next tbsma_step_nvt_pull on.
+ *   thermostat  TBSMA_THERMO_LANGEVIN (default; the wire's gamma, B A O A B)
+ *               or TBSMA_THERMO_NOSE_HOOVER: one thermostat per wire, g =
+ *               3 N_mobile degrees of freedom, mass Q = g k_B T_w tau^2 (T_w
+ *               the wire's temperature, tau = tau_fs), the step
+ *               NH(dt/2) B(dt/2) A(dt) [forces] B(dt/2) NH(dt/2) with
+ *               NH(h): xi += (h/2)(2K - g k_B T)/Q; v *= exp(-xi h);
+ *               eta += h xi; xi += (h/2)(2K' - g k_B T)/Q.  A wire with
+ *               T_w = 0 or no mobile atom runs NVE.
+ *   pull        TBSMA_PULL_CONTINUOUS (default; each grip moves by
+ *               strain_rate L0 dt / 2 per step) or TBSMA_PULL_STEPWISE:
+ *               in step s (0-based, counted from tbsma_init) each grip
+ *               moves by -/+ pull_step when (s + 1) is a multiple of
+ *               pull_interval, else not at all.
+ *   ramp        the thermostat's target at step s is t_start + (T_w -
+ *               t_start) min(1, s / ramp_steps); ramp_steps = 0: T_w.
+ * The paper's values: Nosé–Hoover (tau is not given; 1000 fs is this
+ * library's reading), pull_step 0.05 A, pull_interval 10000, t_start
+ * 0.01 K, ramp_steps 200000 (400 ps).  Resets every wire's thermostat
+ * state (xi = eta = 0) and drops captured graphs.  Errors: EINVAL (unknown
+ * thermostat or pull, tau_fs <= 0 under Nosé–Hoover, pull_interval < 1 or
+ * non-finite pull_step under stepwise pull, t_start < 0 or ramp_steps < 0). */
+typedef enum { TBSMA_THERMO_LANGEVIN = 0, TBSMA_THERMO_NOSE_HOOVER = 1 } tbsma_thermostat;
+typedef enum { TBSMA_PULL_CONTINUOUS = 0, TBSMA_PULL_STEPWISE = 1 } tbsma_pull;
+typedef struct {
+  int32_t thermostat;    /* tbsma_thermostat */
+  int32_t pull;          /* tbsma_pull */
+  double tau_fs;         /* Nosé–Hoover period, fs */
+  double pull_step;      /* stepwise: displacement of each grip per event, A */
+  int64_t pull_interval; /* stepwise: steps per event */
+  double t_start;        /* ramp start temperature, K */
+  int64_t ramp_steps;    /* ramp length in steps, 0 = no ramp */
+} tbsma_protocol;
+
+tbsma_status tbsma_set_protocol(tbsma_ctx* ctx, const tbsma_protocol* protocol);
+
+/* Each wire's Nosé–Hoover state into host arrays of n_wires doubles (either
+ * nullable): xi (1/fs) and its time integral eta, so that the extended
+ * energy E_pot + E_kin + Q xi^2/2 + g k_B T eta can be formed.  Zeros under
+ * the Langevin thermostat.  Synchronises. */
+tbsma_status tbsma_get_thermostat(tbsma_ctx* ctx, double* xi, double* eta);
 
 /* Per-wire observables at the current state into out[n_wires] (host).
  * Synchronises.  Returns EWIRE if any wire's status is non-zero (out is

@@ -62,6 +62,43 @@ struct WireDyn {
   float c2sigf;  // c2sig in FP32
 };
 
+// Paper protocol mode (Methods, "Simulation details"): the thermostat kind,
+// the pull mode and the temperature ramp, as set by tbsma_set_protocol.
+struct ProtoDev {
+  int thermo;          // 0 Langevin (B A O A B), 1 Nosé–Hoover
+  int pull;            // 0 continuous (strain rate), 1 stepwise
+  double tau;          // Nosé–Hoover period, fs
+  double pull_step;    // stepwise: displacement of each grip per event, A
+  long long interval;  // stepwise: steps per event
+  double t_start;      // ramp start temperature, K
+  long long ramp;      // ramp length in steps, 0 = none
+};
+
+// One wire's Nosé–Hoover state: xi (1/fs), its integral eta, and the
+// velocity scale factor s of the current step boundary (with s - 1 in FP32
+// for the mixed integrator's increment form).
+struct NhState {
+  double xi, eta, s;
+  float sm1f;
+};
+
+// Target temperature of step s (0-based): linear ramp from t_start to the
+// wire's temperature over `ramp` steps, then constant.
+__host__ __device__ inline double target_temperature(const ProtoDev& p, double T_w, long long s) {
+  if (p.ramp <= 0) return T_w;
+  double f = (double)s / (double)p.ramp;
+  if (f > 1.0) f = 1.0;
+  return p.t_start + (T_w - p.t_start) * f;
+}
+
+// Grip displacement in step s: a stepwise event when (s + 1) is a multiple
+// of the interval, else the continuous per-step displacement.
+__host__ __device__ inline double grip_delta(const ProtoDev& p, double delta_continuous,
+                                             long long s) {
+  if (p.pull == 1) return (p.interval > 0 && (s + 1) % p.interval == 0) ? p.pull_step : 0.0;
+  return delta_continuous;
+}
+
 // Constants of the pair kernels (Eq. 1-2 rewritten with exp2).
 struct PairConsts {
   // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-(p-2q) s} = 2^(-kh (r - r0))

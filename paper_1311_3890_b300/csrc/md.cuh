@@ -171,7 +171,12 @@ __global__ void k_pack(int64_t N, const double* __restrict__ x, const uint32_t* 
 // pack + displacement check.  KICK = 1: half kick dt/2 (first step of a
 // sequence); KICK = 2: the previous step's closing half kick merged with
 // this step's opening one (both use the same force).
-template <int PREC, int KICK>
+// Nosé–Hoover (proto.thermo = 1): closing half kick (KICK = 2), the scale s of
+// the step boundary's NH half steps (k_nh), opening half kick, drift dt.
+// The grips' displacement follows the pull mode and the Langevin noise the
+// ramped target temperature (see ProtoDev).  PROTO = false compiles the
+// default protocol (Langevin, continuous pull, no ramp) alone.
+template <int PREC, int KICK, bool PROTO>
 __global__ void __launch_bounds__(256)
     k_integrate(int64_t N, double* __restrict__ x, double* __restrict__ v,
                 const float* __restrict__ f32, const double* __restrict__ f64,
@@ -179,13 +184,16 @@ __global__ void __launch_bounds__(256)
                 const WireDyn* __restrict__ wdyn, double dt, double inv_m,
                 const int64_t* __restrict__ step_counter, int4* xq, double4_32a* xd,
                 const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
-                int32_t* flag, uint32_t* wire_status, double* d_grip) {
+                int32_t* flag, uint32_t* wire_status, double* d_grip, ProtoDev proto,
+                const NhState* __restrict__ nh) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t m = meta[i];
   const uint32_t wi = meta_wire(m), kind = meta_kind(m);
   const WireDev& w = wd[wi];
   const WireDyn dy = wdyn[wi];
+  const long long step = step_counter[0];
+  const double delta = PROTO ? grip_delta(proto, dy.delta, step) : dy.delta;
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
   double vx, vy, vz;
   if (kind == 0) {
@@ -202,39 +210,58 @@ __global__ void __launch_bounds__(256)
       fy = f64[N + i];
       fz = f64[2 * N + i];
     }
-    const double hk = 0.5 * KICK * dt * inv_m;
-    vx += hk * fx;
-    vy += hk * fy;
-    vz += hk * fz;
-    const double hd = 0.5 * dt;
-    px += hd * vx;
-    py += hd * vy;
-    pz += hd * vz;
-    if (dy.c2sig != 0.0 || dy.c1 != 1.0) {
-      double nx = 0.0, ny = 0.0, nz = 0.0;
-      if (dy.c2sig != 0.0) {
-        const uint4 b = thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step_counter[0], 0u);
-        if (PREC == TBSMA_MIXED) {
-          const float3 g = normals3_f32(b);
-          nx = g.x;
-          ny = g.y;
-          nz = g.z;
-        } else {
-          const double3 g = normals3_f64(b);
-          nx = g.x;
-          ny = g.y;
-          nz = g.z;
-        }
+    if (PROTO && proto.thermo == 1) {
+      const double hk = 0.5 * dt * inv_m;
+      if (KICK == 2) {
+        vx += hk * fx;
+        vy += hk * fy;
+        vz += hk * fz;
       }
-      vx = dy.c1 * vx + dy.c2sig * nx;
-      vy = dy.c1 * vy + dy.c2sig * ny;
-      vz = dy.c1 * vz + dy.c2sig * nz;
+      const double sc = nh[wi].s;
+      vx = sc * vx + hk * fx;
+      vy = sc * vy + hk * fy;
+      vz = sc * vz + hk * fz;
+      px += dt * vx;
+      py += dt * vy;
+      pz += dt * vz;
+    } else {
+      const double hk = 0.5 * KICK * dt * inv_m;
+      vx += hk * fx;
+      vy += hk * fy;
+      vz += hk * fz;
+      const double hd = 0.5 * dt;
+      px += hd * vx;
+      py += hd * vy;
+      pz += hd * vz;
+      double c2sig = dy.c2sig;
+      if (PROTO && proto.ramp > 0 && w.temperature > 0.0)
+        c2sig *= sqrt(target_temperature(proto, w.temperature, step) / w.temperature);
+      if (c2sig != 0.0 || dy.c1 != 1.0) {
+        double nx = 0.0, ny = 0.0, nz = 0.0;
+        if (c2sig != 0.0) {
+          const uint4 b = thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step, 0u);
+          if (PREC == TBSMA_MIXED) {
+            const float3 g = normals3_f32(b);
+            nx = g.x;
+            ny = g.y;
+            nz = g.z;
+          } else {
+            const double3 g = normals3_f64(b);
+            nx = g.x;
+            ny = g.y;
+            nz = g.z;
+          }
+        }
+        vx = dy.c1 * vx + c2sig * nx;
+        vy = dy.c1 * vy + c2sig * ny;
+        vz = dy.c1 * vz + c2sig * nz;
+      }
+      px += hd * vx;
+      py += hd * vy;
+      pz += hd * vz;
     }
-    px += hd * vx;
-    py += hd * vy;
-    pz += hd * vz;
   } else {
-    px += (kind == 1) ? -dy.delta : dy.delta;
+    px += (kind == 1) ? -delta : delta;
     vx = vy = vz = 0.0;
   }
   x[i] = px;
@@ -245,7 +272,7 @@ __global__ void __launch_bounds__(256)
   v[2 * N + i] = vz;
   if (!isfinite(px + py + pz + vx + vy + vz)) atomicOr(&wire_status[wi], kWireNonFinite);
   pack_and_check<PREC>(i, m, w, px, py, pz, xq, xd, xq_b, xd_b, half_skin2, 1, flag, wire_status);
-  if (i == w.offset) d_grip[wi] += dy.delta;
+  if (i == w.offset) d_grip[wi] += delta;
 }
 
 // Non-finite test on the exponent bits (integer ops, no FP64 pipe).
@@ -287,51 +314,73 @@ __device__ __forceinline__ float narrow(double d) {
 // narrow); B300's FP64 pipe is ~1/64 of its FP32 rate.  The packed
 // fixed-point position is one FMA per coordinate (fixed_coord); the
 // displacement check is integer.
-template <int KICK>
+template <int KICK, bool PROTO>
 __global__ void __launch_bounds__(256)
     k_integrate_mixed(int64_t N, double* __restrict__ x, double* __restrict__ v,
                       const float* __restrict__ f32, const uint32_t* __restrict__ meta,
                       const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk,
                       float hd, const int64_t* __restrict__ step_counter, int4* __restrict__ xq,
                       const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
-                      uint32_t* wire_status, double* d_grip) {
+                      uint32_t* wire_status, double* d_grip, ProtoDev proto,
+                      const NhState* __restrict__ nh) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t m = meta[i];
   const uint32_t wi = meta_wire(m), kind = meta_kind(m);
   const WireDev& w = wd[wi];
+  const long long step = step_counter[0];
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
   double vx = 0.0, vy = 0.0, vz = 0.0;
   if (kind == 0) {
-    const float c1m1 = wdyn[wi].c1m1f, c2sig = wdyn[wi].c2sigf;
     vx = v[i];
     vy = v[N + i];
     vz = v[2 * N + i];
-    const float dvx = hk * f32[i], dvy = hk * f32[N + i], dvz = hk * f32[2 * N + i];
-    const float v1x = narrow(vx) + dvx, v1y = narrow(vy) + dvy, v1z = narrow(vz) + dvz;
-    float Dx = 0.f, Dy = 0.f, Dz = 0.f;
-    if (c2sig != 0.f) {
-      const float3 g = normals3_f32(
-          thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step_counter[0], 0u));
-      Dx = fmaf(c1m1, v1x, c2sig * g.x);
-      Dy = fmaf(c1m1, v1y, c2sig * g.y);
-      Dz = fmaf(c1m1, v1z, c2sig * g.z);
-    } else if (c1m1 != 0.f) {
-      Dx = c1m1 * v1x;
-      Dy = c1m1 * v1y;
-      Dz = c1m1 * v1z;
+    if (PROTO && proto.thermo == 1) {
+      // Nosé–Hoover: v' = s (v + a) + b with a the closing half kick (KICK = 2)
+      // and b the opening one; increments (s - 1)(v + a) + a + b in FP32,
+      // drift dt v'.  hk is the half kick here.
+      const float bx = hk * f32[i], by = hk * f32[N + i], bz = hk * f32[2 * N + i];
+      const float ax = KICK == 2 ? bx : 0.f, ay = KICK == 2 ? by : 0.f, az = KICK == 2 ? bz : 0.f;
+      const float sm1 = nh[wi].sm1f;
+      const float cx = narrow(vx) + ax, cy = narrow(vy) + ay, cz = narrow(vz) + az;
+      const float Dx = sm1 * cx, Dy = sm1 * cy, Dz = sm1 * cz;
+      vx += widen(ax + Dx + bx);
+      vy += widen(ay + Dy + by);
+      vz += widen(az + Dz + bz);
+      px += widen(2.f * hd * (cx + Dx + bx));
+      py += widen(2.f * hd * (cy + Dy + by));
+      pz += widen(2.f * hd * (cz + Dz + bz));
+    } else {
+      const float c1m1 = wdyn[wi].c1m1f;
+      float c2sig = wdyn[wi].c2sigf;
+      if (PROTO && proto.ramp > 0 && w.temperature > 0.0)
+        c2sig *= sqrtf((float)(target_temperature(proto, w.temperature, step) / w.temperature));
+      const float dvx = hk * f32[i], dvy = hk * f32[N + i], dvz = hk * f32[2 * N + i];
+      const float v1x = narrow(vx) + dvx, v1y = narrow(vy) + dvy, v1z = narrow(vz) + dvz;
+      float Dx = 0.f, Dy = 0.f, Dz = 0.f;
+      if (c2sig != 0.f) {
+        const float3 g = normals3_f32(
+            thermostat_bits(w.seed, (uint32_t)(i - w.offset), (uint64_t)step, 0u));
+        Dx = fmaf(c1m1, v1x, c2sig * g.x);
+        Dy = fmaf(c1m1, v1y, c2sig * g.y);
+        Dz = fmaf(c1m1, v1z, c2sig * g.z);
+      } else if (c1m1 != 0.f) {
+        Dx = c1m1 * v1x;
+        Dy = c1m1 * v1y;
+        Dz = c1m1 * v1z;
+      }
+      vx += widen(dvx + Dx);
+      vy += widen(dvy + Dy);
+      vz += widen(dvz + Dz);
+      px += widen(hd * fmaf(2.f, v1x, Dx));
+      py += widen(hd * fmaf(2.f, v1y, Dy));
+      pz += widen(hd * fmaf(2.f, v1z, Dz));
     }
-    vx += widen(dvx + Dx);
-    vy += widen(dvy + Dy);
-    vz += widen(dvz + Dz);
-    px += widen(hd * fmaf(2.f, v1x, Dx));
-    py += widen(hd * fmaf(2.f, v1y, Dy));
-    pz += widen(hd * fmaf(2.f, v1z, Dz));
   } else {
-    const double delta = wdyn[wi].delta;
+    const double delta = PROTO ? grip_delta(proto, wdyn[wi].delta, step) : wdyn[wi].delta;
     px += (kind == 1) ? -delta : delta;
   }
-  if (i == w.offset) d_grip[wi] += wdyn[wi].delta;
+  if (i == w.offset) d_grip[wi] += PROTO ? grip_delta(proto, wdyn[wi].delta, step) : wdyn[wi].delta;
   x[i] = px;
   x[N + i] = py;
   x[2 * N + i] = pz;
@@ -347,6 +396,77 @@ __global__ void __launch_bounds__(256)
   const int4 b = xq_b[i];
   const float ex = fixed_diff(q.x, b.x), ey = fixed_diff(q.y, b.y), ez = fixed_diff(q.z, b.z);
   if (ex * ex + ey * ey + ez * ez > half_skin2) flag[wi] = 1;
+}
+
+// Block per wire: the Nosé–Hoover half steps at a step boundary (Methods,
+// "Simulation details": Nosé–Hoover thermostat with velocity Verlet).  K is
+// the mobile kinetic energy of v + kick F (kick = the closing half kick not
+// yet applied to v, or 0), reduced in a fixed order.  mode bit 1: the end
+// half step of step c - 1, bit 2: the begin half step of step c (c = the
+// step counter).  A half step of length h = dt/2 at target T is
+//   xi += (h/2)(2K - g k_B T)/Q;  scale exp(-xi h);  K *= scale^2;
+//   eta += h xi;  xi += (h/2)(2K - g k_B T)/Q
+// with g = 3 N_mobile and Q = g k_B T_w tau^2.  The product of the scales is
+// left in nh[w].s for the integrator (or k_nh_scale); a wire with Q = 0 gets
+// s = 1 (NVE).
+__global__ void __launch_bounds__(256)
+    k_nh(int W, const WireDev* __restrict__ wd, const uint32_t* __restrict__ meta, int64_t N,
+         const double* __restrict__ v, const float* __restrict__ f32,
+         const double* __restrict__ f64, int prec, double kick, int mode, double dt,
+         ProtoDev proto, double m_e, const int64_t* __restrict__ step_counter,
+         NhState* __restrict__ nh) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    double k2 = 0.0;
+    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
+      const int64_t i = wr.offset + a;
+      if (meta_kind(meta[i]) != 0) continue;
+      for (int d = 0; d < 3; ++d) {
+        const double f = prec == TBSMA_MIXED ? (double)f32[d * N + i] : f64[d * N + i];
+        const double u = v[d * N + i] + kick * f;
+        k2 += u * u;
+      }
+    }
+    const double K = 0.5 * m_e * block_sum(k2, sh);
+    if (threadIdx.x == 0) {
+      NhState st = nh[w];
+      const double g = 3.0 * (double)wr.n_mobile;
+      const double Q = g * kBoltzmann * wr.temperature * proto.tau * proto.tau;
+      double scale = 1.0;
+      if (Q > 0.0) {
+        const long long c = step_counter[0];
+        const double h = 0.5 * dt;
+        double Kc = K;
+        for (int half = 1; half <= 2; half <<= 1) {
+          if (!(mode & half)) continue;
+          const double T = target_temperature(proto, wr.temperature, half == 1 ? c - 1 : c);
+          const double gkT = g * kBoltzmann * T;
+          st.xi += 0.5 * h * (2.0 * Kc - gkT) / Q;
+          const double sc = exp(-st.xi * h);
+          Kc *= sc * sc;
+          st.eta += h * st.xi;
+          st.xi += 0.5 * h * (2.0 * Kc - gkT) / Q;
+          scale *= sc;
+        }
+      }
+      st.s = scale;
+      st.sm1f = (float)(scale - 1.0);
+      nh[w] = st;
+    }
+  }
+}
+
+// Mobile velocities times their wire's NH scale (the end half step of a
+// sequence, after the closing half kick).
+__global__ void k_nh_scale(int64_t N, double* __restrict__ v, const uint32_t* __restrict__ meta,
+                           const NhState* __restrict__ nh) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t m = meta[i];
+  if (meta_kind(m) != 0) return;
+  const double sc = nh[meta_wire(m)].s;
+  for (int d = 0; d < 3; ++d) v[d * N + i] *= sc;
 }
 
 // Closing half kick of the last step of a sequence.

@@ -87,6 +87,8 @@ struct tbsma_ctx {
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   uint32_t* wire_status = nullptr;
+  NhState* nh = nullptr;            // per-wire Nosé–Hoover state
+  tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
   double* d_grip = nullptr;
   int64_t* step_counter = nullptr;
   tbsma_obs* obs_d = nullptr;
@@ -249,35 +251,81 @@ tbsma_status launch_one_pass(tbsma_ctx* c, cudaStream_t s, int pass) {
   return TBSMA_OK;
 }
 
+ProtoDev proto_dev(const tbsma_ctx* c) {
+  ProtoDev p;
+  p.thermo = c->proto.thermostat;
+  p.pull = c->proto.pull;
+  p.tau = c->proto.tau_fs;
+  p.pull_step = c->proto.pull_step;
+  p.interval = c->proto.pull_interval;
+  p.t_start = c->proto.t_start;
+  p.ramp = c->proto.ramp_steps;
+  return p;
+}
+
+bool nose_hoover(const tbsma_ctx* c) { return c->proto.thermostat == TBSMA_THERMO_NOSE_HOOVER; }
+
+// A protocol other than the default (Langevin, continuous pull, no ramp).
+bool protocol_mode(const tbsma_ctx* c) {
+  return c->proto.thermostat != TBSMA_THERMO_LANGEVIN || c->proto.pull != TBSMA_PULL_CONTINUOUS ||
+         c->proto.ramp_steps > 0;
+}
+
+template <int KICK, bool PROTO>
+void integrate_as(tbsma_ctx* c, cudaStream_t s, double dt) {
+  const unsigned g = grid_for(c->N, 256);
+  // the mixed kernel takes the kick it applies at once: the merged full kick
+  // of B A O A B, or the half kick that Nosé–Hoover applies on either side of
+  // its scaling
+  const double kick = 0.5 * (nose_hoover(c) ? 1 : KICK) * dt * c->inv_m;
+  if (c->prec == TBSMA_MIXED)
+    k_integrate_mixed<KICK, PROTO><<<g, 256, 0, s>>>(
+        c->N, c->x, c->v, c->f32, c->meta, c->wd, c->wdyn, (float)kick, (float)(0.5 * dt),
+        c->step_counter, c->xq, c->xq_b, (float)c->half_skin2, c->flag, c->wire_status,
+        c->d_grip, proto_dev(c), c->nh);
+  else
+    k_integrate<TBSMA_FP64, KICK, PROTO><<<g, 256, 0, s>>>(
+        c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
+        c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip,
+        proto_dev(c), c->nh);
+}
+
 template <int KICK>
 void integrate(tbsma_ctx* c, cudaStream_t s, double dt) {
-  const unsigned g = grid_for(c->N, 256);
-  if (c->prec == TBSMA_MIXED)
-    k_integrate_mixed<KICK><<<g, 256, 0, s>>>(
-        c->N, c->x, c->v, c->f32, c->meta, c->wd, c->wdyn, (float)(0.5 * KICK * dt * c->inv_m),
-        (float)(0.5 * dt), c->step_counter, c->xq, c->xq_b, (float)c->half_skin2, c->flag,
-        c->wire_status, c->d_grip);
-  else
-    k_integrate<TBSMA_FP64, KICK><<<g, 256, 0, s>>>(
-        c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
-        c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip);
+  if (protocol_mode(c)) integrate_as<KICK, true>(c, s, dt);
+  else integrate_as<KICK, false>(c, s, dt);
+}
+
+// Nosé–Hoover half steps at a step boundary (mode 1 end, 2 begin, 3 both);
+// kick = the closing half kick still to be applied to v (0 if applied).
+void nh_boundary(tbsma_ctx* c, cudaStream_t s, double dt, double kick, int mode) {
+  k_nh<<<std::min(c->W, 65535), 256, 0, s>>>(c->W, c->wd, c->meta, c->N, c->v, c->f32, c->f64,
+                                               c->prec, kick, mode, dt, proto_dev(c),
+                                               c->P.mass * kMvv2e, c->step_counter, c->nh);
 }
 
 // n consecutive steps: first integrate with a half kick, the rest with a
 // merged full kick, and a closing half kick after the last force pass.
 tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
+  const double hk = 0.5 * dt * c->inv_m;
   for (int k = 0; k < n; ++k) {
+    // Nosé–Hoover: the begin half step (first step of the sequence) or the
+    // previous step's end half step followed by this step's begin half step
+    if (nose_hoover(c)) nh_boundary(c, s, dt, k == 0 ? 0.0 : hk, k == 0 ? 2 : 3);
     if (k == 0) integrate<1>(c, s, dt);
     else integrate<2>(c, s, dt);
     TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
     TB_TRY(launch_pair<false>(c, s, c->prec));
   }
   const unsigned g = grid_for(c->N, 256);
-  const double hk = 0.5 * dt * c->inv_m;
   if (c->prec == TBSMA_MIXED)
     k_half_kick<TBSMA_MIXED><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
   else
     k_half_kick<TBSMA_FP64><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+  if (nose_hoover(c)) {  // the last step's end half step
+    nh_boundary(c, s, dt, 0.0, 1);
+    k_nh_scale<<<g, 256, 0, s>>>(c->N, c->v, c->meta, c->nh);
+  }
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
@@ -496,6 +544,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->wire_status, W);
+  ALLOC(c->nh, W);
   ALLOC(c->d_grip, W);
   ALLOC(c->step_counter, 1);
   ALLOC(c->obs_d, W);
@@ -508,6 +557,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_grip, 0, sizeof(double) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->step_counter, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * N, st) == cudaSuccess;
@@ -670,6 +720,38 @@ tbsma_status tbsma_set_launch(tbsma_ctx* c, int32_t block_threads, int32_t windo
   c->block = block_threads;
   c->wcap = window_atoms;
   drop_graph(c);
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_set_protocol(tbsma_ctx* c, const tbsma_protocol* p) {
+  if (!c || !p) return TBSMA_EINVAL;
+  if (p->thermostat != TBSMA_THERMO_LANGEVIN && p->thermostat != TBSMA_THERMO_NOSE_HOOVER)
+    return fail(c, TBSMA_EINVAL, "unknown thermostat");
+  if (p->pull != TBSMA_PULL_CONTINUOUS && p->pull != TBSMA_PULL_STEPWISE)
+    return fail(c, TBSMA_EINVAL, "unknown pull mode");
+  if (p->thermostat == TBSMA_THERMO_NOSE_HOOVER && !(p->tau_fs > 0.0 && std::isfinite(p->tau_fs)))
+    return fail(c, TBSMA_EINVAL, "tau_fs must be positive");
+  if (p->pull == TBSMA_PULL_STEPWISE && (p->pull_interval < 1 || !std::isfinite(p->pull_step)))
+    return fail(c, TBSMA_EINVAL, "stepwise pull needs pull_interval >= 1 and a finite pull_step");
+  if (!(p->t_start >= 0.0 && std::isfinite(p->t_start)) || p->ramp_steps < 0)
+    return fail(c, TBSMA_EINVAL, "ramp needs t_start >= 0 and ramp_steps >= 0");
+  c->proto = *p;
+  drop_graph(c);
+  TB_CUDA(c, cudaMemsetAsync(c->nh, 0, sizeof(NhState) * c->W, c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_get_thermostat(tbsma_ctx* c, double* xi, double* eta) {
+  if (!c) return TBSMA_EINVAL;
+  std::vector<NhState> st(c->W);
+  TB_CUDA(c, cudaMemcpyAsync(st.data(), c->nh, sizeof(NhState) * c->W, cudaMemcpyDeviceToHost,
+                             c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  const bool on = nose_hoover(c);
+  for (int w = 0; w < c->W; ++w) {
+    if (xi) xi[w] = on ? st[w].xi : 0.0;
+    if (eta) eta[w] = on ? st[w].eta : 0.0;
+  }
   return TBSMA_OK;
 }
 

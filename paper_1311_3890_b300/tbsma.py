@@ -80,6 +80,23 @@ _P = ctypes.c_void_p
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/tbsma.h
+class ProtocolC(ctypes.Structure):
+    """tbsma_protocol (include/tbsma.h)."""
+
+    _fields_ = [
+        ("thermostat", ctypes.c_int32),
+        ("pull", ctypes.c_int32),
+        ("tau_fs", ctypes.c_double),
+        ("pull_step", ctypes.c_double),
+        ("pull_interval", ctypes.c_int64),
+        ("t_start", ctypes.c_double),
+        ("ramp_steps", ctypes.c_int64),
+    ]
+
+
+THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
+PULLS = {"continuous": 0, "stepwise": 1}
+
 SIGNATURES = [
     ("tbsma_init", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     ("tbsma_init_velocities", ctypes.c_int, [_P]),
@@ -96,6 +113,8 @@ SIGNATURES = [
     ("tbsma_get_neighbors", ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     ("tbsma_set_launch", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
+    ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     ("tbsma_normals", ctypes.c_int, [ctypes.c_uint64, _P, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_uint32, ctypes.c_int, _P, _P]),
@@ -267,6 +286,24 @@ class Engine:
     def set_launch(self, block_threads: int, window_atoms: int):
         """Pair-pass tile size (atoms per block) and shared-memory window (atoms)."""
         self._check(lib().tbsma_set_launch(self.ctx, block_threads, window_atoms), "tbsma_set_launch")
+
+    def set_protocol(self, thermostat: str = "nose_hoover", pull: str = "stepwise",
+                     tau_fs: float = 1000.0, pull_step: float = 0.05, pull_interval: int = 10000,
+                     t_start: float = 0.01, ramp_steps: int = 0):
+        """Paper protocol mode (tbsma_set_protocol); the defaults are the paper's
+        Nosé–Hoover thermostat and 0.05 A grip steps every 10000 steps, no ramp."""
+        p = ProtocolC(THERMOSTATS[thermostat], PULLS[pull], tau_fs, pull_step, int(pull_interval),
+                      t_start, int(ramp_steps))
+        self._check(lib().tbsma_set_protocol(self.ctx, ctypes.byref(p)), "tbsma_set_protocol")
+
+    def thermostat(self):
+        """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""
+        xi = np.zeros(self.W)
+        eta = np.zeros(self.W)
+        self._check(lib().tbsma_get_thermostat(self.ctx, xi.ctypes.data_as(ctypes.c_void_p),
+                                               eta.ctypes.data_as(ctypes.c_void_p)),
+                    "tbsma_get_thermostat")
+        return xi, eta
 
     def run_pass(self, which: int, reps: int = 1):
         """Enqueue `reps` launches of pass 1 (density) or 2 (force) alone."""
