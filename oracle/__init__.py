@@ -110,6 +110,8 @@ def _declare(L):
     L.or_md_batch_protocol.argtypes = [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _I64,
                                        _D, _P, _P, _P, _I]
     L.or_observables.argtypes = [_P, _P, _P, _I, _P, _P, _P, _D, _I, _P]
+    L.or_topology.argtypes = [_I, _P, _P, _D, _D, _L, _P, _P]
+    L.or_topology.restype = _L
 
 
 def _ptr(a: np.ndarray | None):
@@ -427,6 +429,39 @@ def md_batch_protocol(proto: Protocol, x, v, kind, offset, count, L0, strain_rat
         _ptr(n_rebuild), _ptr(nh), brute_max,
     )
     return F, x_build, d_grip, n_rebuild, nh
+
+
+A_LATTICE = 4.079  # A, the fcc lattice constant of the wires (Table 1 column)
+
+
+@dataclasses.dataclass
+class Topology:
+    connected: bool  # a left-grip and a right-grip atom share a cluster
+    n_clusters: int
+    neck: int  # smallest number of atoms in an axial slab between the grips
+    neck_slab: int
+    n_slabs: int
+    label: np.ndarray  # component label (smallest atom index) of every atom
+
+
+def topology(x: np.ndarray, kind: np.ndarray, pot: Potential = AU,
+             slab: float = 0.5 * A_LATTICE) -> Topology:
+    """Clusters of the interacting-pair graph and the neck (see or_topology)."""
+    x = _f64(x)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    n = x.shape[0]
+    label = np.zeros(n, dtype=np.int32)
+    out = np.zeros(5, dtype=np.int64)
+    cap = 64 * n + 64
+    while True:
+        r = lib().or_topology(n, _ptr(x), _ptr(kind), pot.r_cut, slab, cap, _ptr(label),
+                              _ptr(out))
+        if r == 0:
+            break
+        if cap > 1024 * n + 1024:
+            raise ValueError("a wire needs atoms of both grips")
+        cap *= 4
+    return Topology(bool(out[0]), int(out[1]), int(out[2]), int(out[3]), int(out[4]), label)
 
 
 def max_threads() -> int:

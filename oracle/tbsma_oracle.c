@@ -598,6 +598,91 @@ void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R,
   }
 }
 
+/* ======================================================================
+ * Wire topology: rupture and neck (Results, "Nanowire elongation": a wire
+ * fails when it separates into two pieces; the final neck is its thinnest
+ * cross-section before that; the paper gives no formal definition).
+ *
+ * Clusters: connected components of the graph whose edges are the pairs
+ * with r_ij <= r_cut (the interacting pairs), found by union-find; every
+ * component is labelled by its smallest atom index.  connected = 1 when a
+ * left-grip atom (kind 1) and a right-grip atom (kind 2) share a component.
+ * Neck: between the largest x of the left grip (x_lo) and the smallest x of
+ * the right grip (x_hi), slab k covers x_lo + (k + 1/2) w <= x < x_lo +
+ * (k + 3/2) w, k = 0 .. n_slabs - 1 with n_slabs = floor((x_hi - x_lo) / w
+ * - 1/2) and w = a/2, the spacing of the (100) planes, so that each (100) plane
+ * of the unstrained wire lies at the centre of one slab; the neck is the
+ * smallest count of atoms in a slab and its index (the first one on ties).
+ * out[0] connected, out[1] n_clusters, out[2] neck count, out[3] neck slab,
+ * out[4] n_slabs; label[n] (may be NULL) receives the component labels.
+ * Returns -1 if a grip is missing or the pair set does not fit in `cap`.
+ * ==================================================================== */
+static int uf_find(int* parent, int a) {
+  while (parent[a] != a) a = parent[a];
+  return a;
+}
+
+long or_topology(int n, const double* x, const uint8_t* kind, double rc, double w, long cap,
+                 int* label, long out[5]) {
+  int* start = (int*)malloc(sizeof(int) * (n + 1));
+  int* nbr = (int*)malloc(sizeof(int) * (cap > 0 ? cap : 1));
+  int* parent = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  long k = or_pairs_cells(n, x, rc, start, nbr, cap);
+  if (k < 0) {
+    free(start), free(nbr), free(parent);
+    return -1;
+  }
+  for (int i = 0; i < n; ++i) parent[i] = i;
+  for (int i = 0; i < n; ++i)
+    for (int e = start[i]; e < start[i + 1]; ++e) {
+      int ra = uf_find(parent, i), rb = uf_find(parent, nbr[e]);
+      if (ra == rb) continue;
+      if (ra < rb) parent[rb] = ra; /* the smaller index stays the root */
+      else parent[ra] = rb;
+    }
+  long n_clusters = 0;
+  int left = -1, right = -1;
+  double x_lo = -1e300, x_hi = 1e300;
+  for (int i = 0; i < n; ++i) {
+    int r = uf_find(parent, i);
+    if (label) label[i] = r;
+    if (r == i) ++n_clusters;
+    if (kind[i] == 1) {
+      if (left < 0) left = i;
+      if (x[3 * i] > x_lo) x_lo = x[3 * i];
+    } else if (kind[i] == 2) {
+      if (right < 0) right = i;
+      if (x[3 * i] < x_hi) x_hi = x[3 * i];
+    }
+  }
+  if (left < 0 || right < 0) {
+    free(start), free(nbr), free(parent);
+    return -1;
+  }
+  long n_slabs = (x_hi > x_lo) ? (long)floor((x_hi - x_lo) / w - 0.5) : 0;
+  if (n_slabs < 0) n_slabs = 0;
+  long neck = 0, neck_slab = -1;
+  if (n_slabs > 0) {
+    long* cnt = (long*)calloc((size_t)n_slabs, sizeof(long));
+    for (int i = 0; i < n; ++i) {
+      double u = (x[3 * i] - x_lo) / w - 0.5;
+      if (u >= 0.0 && u < (double)n_slabs) cnt[(long)floor(u)] += 1;
+    }
+    neck = cnt[0];
+    neck_slab = 0;
+    for (long s = 1; s < n_slabs; ++s)
+      if (cnt[s] < neck) neck = cnt[s], neck_slab = s;
+    free(cnt);
+  }
+  out[0] = uf_find(parent, left) == uf_find(parent, right);
+  out[1] = n_clusters;
+  out[2] = neck;
+  out[3] = neck_slab;
+  out[4] = n_slabs;
+  free(start), free(nbr), free(parent);
+  return 0;
+}
+
 int or_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
