@@ -214,6 +214,34 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* ctx, const tbsma_protocol* protocol);
  * the Langevin thermostat.  Synchronises. */
 tbsma_status tbsma_get_thermostat(tbsma_ctx* ctx, double* xi, double* eta);
 
+/* Wire topology: rupture and neck (Results, "Nanowire elongation"; the paper
+ * gives no formal definition).  Clusters are the connected components of
+ * the graph of interacting pairs (r_ij <= r_cut under the context's
+ * precision rule: the FP32 rule on fixed-point positions for MIXED, FP64
+ * distances for FP64), each labelled by its smallest atom index.  A wire is
+ * connected while a left-grip and a right-grip atom share a cluster (the
+ * failure strain is the strain of the first report at which it is not).
+ * Neck: with x_lo the largest x of the left grip and x_hi the smallest x of
+ * the right grip, slab k = 0 .. n_slabs - 1 covers x_lo + (k + 1/2) w <= x <
+ * x_lo + (k + 3/2) w, n_slabs = floor((x_hi - x_lo)/w - 1/2), w = a/2 =
+ * 2.0395 A (the (100) plane spacing), so each plane of the unstrained wire
+ * sits at a slab centre; neck = the fewest atoms in a slab, neck_slab its
+ * index (first on ties, -1 without slabs).  status: 0, 1 if the wire has
+ * more than 4096 slabs (neck not computed), 2 if a bounded union-find loop
+ * gave up.  Re-packs positions and rebuilds the lists of wires that moved
+ * past the skin first.  out[n_wires] host; labels (nullable) device, N int32.
+ * Synchronises.  Errors: EINVAL (null out), ETIMEOUT (a status 2), ECUDA. */
+typedef struct {
+  int32_t connected;  /* 1: the grips are in one cluster */
+  int32_t n_clusters; /* components of the interacting-pair graph */
+  int32_t neck;       /* fewest atoms in an axial slab between the grips */
+  int32_t neck_slab;  /* its index, -1 without slabs */
+  int32_t n_slabs;
+  int32_t status;
+} tbsma_topology;
+
+tbsma_status tbsma_wire_topology(tbsma_ctx* ctx, tbsma_topology* out, int32_t* labels);
+
 /* Per-wire observables at the current state into out[n_wires] (host).
  * Synchronises.  Returns EWIRE if any wire's status is non-zero (out is
  * still filled). */

@@ -64,8 +64,16 @@ def fcc_wire(
     strain_rate: float = 0.0,
     gamma: float = 1.0e-3,
     seed: int = 0,
+    notch_depth: float = 0.0,
+    notch_planes: int = 2,
 ) -> Wire:
-    """Cylindrical [100] fcc wire of diameter D and length L (nm)."""
+    """Cylindrical [100] fcc wire of diameter D and length L (nm).
+
+    notch_depth > 0 cuts a ring-shaped notch at the centre (Methods,
+    "Simulation details": a small ring notch fixes where the wire breaks; its
+    size is not given): the atoms farther than R_max - notch_depth from the
+    axis are removed from the `notch_planes` (100) planes nearest the middle,
+    R_max the largest radius of the wire's atoms."""
     R = 5.0 * diameter_nm  # radius in Angstrom
     L = 10.0 * length_nm
     nx = int(np.ceil(L / a)) + 1
@@ -82,6 +90,12 @@ def fcc_wire(
     x = sites[keep]
     x = x[_order_along_axis(x)]
     planes = np.unique(np.round(x[:, 0], 6))
+    if notch_depth > 0.0 and notch_planes > 0:
+        mid = 0.5 * (planes[0] + planes[-1])
+        centre = planes[np.argsort(np.abs(planes - mid), kind="stable")[:notch_planes]]
+        r = np.hypot(x[:, 1], x[:, 2])
+        cut = np.isin(np.round(x[:, 0], 6), centre) & (r > r.max() - notch_depth)
+        x = x[~cut]
     kind = np.zeros(x.shape[0], dtype=np.uint8)
     if grip_planes > 0:
         lo = planes[grip_planes - 1]

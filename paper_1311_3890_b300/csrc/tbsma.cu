@@ -19,6 +19,7 @@
 #include "md.cuh"
 #include "nlist.cuh"
 #include "pair.cuh"
+#include "topo.cuh"
 
 using namespace tbsma;
 
@@ -88,6 +89,9 @@ struct tbsma_ctx {
   int32_t* n_rebuilds = nullptr;
   uint32_t* wire_status = nullptr;
   NhState* nh = nullptr;            // per-wire Nosé–Hoover state
+  int* uf_parent = nullptr;         // union-find of the topology call (allocated on first use)
+  uint32_t* uf_err = nullptr;
+  tbsma_topology* topo_d = nullptr;
   tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
   double* d_grip = nullptr;
   int64_t* step_counter = nullptr;
@@ -751,6 +755,42 @@ tbsma_status tbsma_get_thermostat(tbsma_ctx* c, double* xi, double* eta) {
   for (int w = 0; w < c->W; ++w) {
     if (xi) xi[w] = on ? st[w].xi : 0.0;
     if (eta) eta[w] = on ? st[w].eta : 0.0;
+  }
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_wire_topology(tbsma_ctx* c, tbsma_topology* out, int32_t* labels) {
+  if (!c || !out) return TBSMA_EINVAL;
+  if (!c->uf_parent) {
+    if (alloc(c, &c->uf_parent, c->N) != TBSMA_OK || alloc(c, &c->uf_err, 1) != TBSMA_OK ||
+        alloc(c, &c->topo_d, c->W) != TBSMA_OK)
+      return fail(c, TBSMA_ENOMEM, "topology buffers");
+  }
+  TB_TRY(refresh(c, 0));
+  const unsigned g = grid_for(c->N, 256);
+  TB_CUDA(c, cudaMemsetAsync(c->uf_err, 0, sizeof(uint32_t), c->stream));
+  k_uf_init<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent);
+  if (c->prec == TBSMA_MIXED)
+    k_uf_link<TBSMA_MIXED><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
+                                                      c->cap, c->pc, c->uf_parent, c->uf_err);
+  else
+    k_uf_link<TBSMA_FP64><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
+                                                     c->cap, c->pc, c->uf_parent, c->uf_err);
+  k_uf_compress<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent, c->uf_err);
+  k_topology<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->meta, c->N, c->x,
+                                                           c->uf_parent, c->topo_d);
+  TB_CUDA(c, cudaGetLastError());
+  if (labels)
+    TB_CUDA(c, cudaMemcpyAsync(labels, c->uf_parent, sizeof(int32_t) * c->N,
+                               cudaMemcpyDeviceToDevice, c->stream));
+  uint32_t err = 0;
+  TB_CUDA(c, cudaMemcpyAsync(out, c->topo_d, sizeof(tbsma_topology) * c->W, cudaMemcpyDeviceToHost,
+                             c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(&err, c->uf_err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (err) {
+    for (int w = 0; w < c->W; ++w) out[w].status = 2;
+    return fail(c, TBSMA_ETIMEOUT, "a bounded union-find loop gave up");
   }
   return TBSMA_OK;
 }

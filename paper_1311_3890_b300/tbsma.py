@@ -94,6 +94,13 @@ class ProtocolC(ctypes.Structure):
     ]
 
 
+class TopologyC(ctypes.Structure):
+    """tbsma_topology (include/tbsma.h)."""
+
+    _fields_ = [(k, ctypes.c_int32) for k in ("connected", "n_clusters", "neck", "neck_slab",
+                                                 "n_slabs", "status")]
+
+
 THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
 PULLS = {"continuous": 0, "stepwise": 1}
 
@@ -115,6 +122,7 @@ SIGNATURES = [
     ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     ("tbsma_normals", ctypes.c_int, [ctypes.c_uint64, _P, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_uint32, ctypes.c_int, _P, _P]),
@@ -304,6 +312,21 @@ class Engine:
                                                eta.ctypes.data_as(ctypes.c_void_p)),
                     "tbsma_get_thermostat")
         return xi, eta
+
+    def topology(self, labels: bool = False):
+        """Per-wire rupture and neck (tbsma_wire_topology): dict of numpy arrays
+        connected, n_clusters, neck, neck_slab, n_slabs, status; with
+        labels=True also the per-atom cluster labels (cuda int32 tensor)."""
+        out = (TopologyC * self.W)()
+        lab = self.torch.empty(self.N, dtype=self.torch.int32, device=self.device) if labels else None
+        self._check(lib().tbsma_wire_topology(self.ctx, out, _ptr(lab) if labels else None),
+                    "tbsma_wire_topology")
+        res = {k: np.array([getattr(o, k) for o in out], dtype=np.int32)
+               for k, _ in TopologyC._fields_}
+        res["connected"] = res["connected"].astype(bool)
+        if labels:
+            res["labels"] = lab
+        return res
 
     def run_pass(self, which: int, reps: int = 1):
         """Enqueue `reps` launches of pass 1 (density) or 2 (force) alone."""
