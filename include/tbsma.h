@@ -226,7 +226,7 @@ tbsma_status tbsma_get_thermostat(tbsma_ctx* ctx, double* xi, double* eta);
  * x_lo + (k + 3/2) w, n_slabs = floor((x_hi - x_lo)/w - 1/2), w = a/2 =
  * 2.0395 A (the (100) plane spacing), so each plane of the unstrained wire
  * sits at a slab centre; neck = the fewest atoms in a slab, neck_slab its
- * index (first on ties, -1 without slabs).  status: 0, 1 if the wire has
+ * index (first on ties; without slabs neck = 0 and neck_slab = -1).  status: 0, 1 if the wire has
  * more than 4096 slabs (neck not computed), 2 if a bounded union-find loop
  * gave up.  Re-packs positions and rebuilds the lists of wires that moved
  * past the skin first.  out[n_wires] host; labels (nullable) device, N int32.
@@ -241,6 +241,34 @@ typedef struct {
 } tbsma_topology;
 
 tbsma_status tbsma_wire_topology(tbsma_ctx* ctx, tbsma_topology* out, int32_t* labels);
+
+/* Test hook for failure detection: the bound of every union-find walk of
+ * tbsma_wire_topology (default 1048576 steps).  A bound too small for the
+ * graph makes the call give up: status 2 and TBSMA_ETIMEOUT, with the
+ * context still usable.  Errors: EINVAL (steps < 1). */
+tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
+
+/* Checkpoint / resume.  A wire's counters: grip displacement (A), the
+ * Nosé–Hoover state, the number of list rebuilds and its status word. */
+typedef struct {
+  double d_grip;
+  double xi, eta;
+  int32_t n_rebuilds;
+  uint32_t status;
+} tbsma_wire_state;
+
+/* Save: rebuild every wire's list from the current positions and recompute
+ * the forces (so that the state is a function of what is saved), then copy
+ * x, v (host, 3*N doubles SoA each), the wires' counters (host, n_wires) and
+ * the step count.  Restore into a context made by tbsma_init on the same
+ * batch layout and parameters (and the same tbsma_set_protocol, which must
+ * come first): the continuation of the restored context equals the
+ * continuation of the saved one bit for bit.  Both synchronise.  Errors:
+ * EINVAL (null pointers, step < 0), ESTATE (the counts disagree), ECUDA. */
+tbsma_status tbsma_save_state(tbsma_ctx* ctx, double* x_host, double* v_host,
+                              tbsma_wire_state* wires, int64_t* step);
+tbsma_status tbsma_restore_state(tbsma_ctx* ctx, const double* x_host, const double* v_host,
+                                 const tbsma_wire_state* wires, int64_t step);
 
 /* Per-wire observables at the current state into out[n_wires] (host).
  * Synchronises.  Returns EWIRE if any wire's status is non-zero (out is

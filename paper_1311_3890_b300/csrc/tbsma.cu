@@ -92,6 +92,7 @@ struct tbsma_ctx {
   int* uf_parent = nullptr;         // union-find of the topology call (allocated on first use)
   uint32_t* uf_err = nullptr;
   tbsma_topology* topo_d = nullptr;
+  int wait_limit = kUfSteps;        // bound of the topology's union-find walks
   tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
   double* d_grip = nullptr;
   int64_t* step_counter = nullptr;
@@ -772,11 +773,13 @@ tbsma_status tbsma_wire_topology(tbsma_ctx* c, tbsma_topology* out, int32_t* lab
   k_uf_init<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent);
   if (c->prec == TBSMA_MIXED)
     k_uf_link<TBSMA_MIXED><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
-                                                      c->cap, c->pc, c->uf_parent, c->uf_err);
+                                                      c->cap, c->pc, c->uf_parent, c->wait_limit,
+                                                      c->uf_err);
   else
     k_uf_link<TBSMA_FP64><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
-                                                     c->cap, c->pc, c->uf_parent, c->uf_err);
-  k_uf_compress<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent, c->uf_err);
+                                                     c->cap, c->pc, c->uf_parent, c->wait_limit,
+                                                     c->uf_err);
+  k_uf_compress<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent, c->wait_limit, c->uf_err);
   k_topology<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->meta, c->N, c->x,
                                                            c->uf_parent, c->topo_d);
   TB_CUDA(c, cudaGetLastError());
@@ -792,6 +795,78 @@ tbsma_status tbsma_wire_topology(tbsma_ctx* c, tbsma_topology* out, int32_t* lab
     for (int w = 0; w < c->W; ++w) out[w].status = 2;
     return fail(c, TBSMA_ETIMEOUT, "a bounded union-find loop gave up");
   }
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_set_wait_limit(tbsma_ctx* c, int32_t steps) {
+  if (!c) return TBSMA_EINVAL;
+  if (steps < 1) return fail(c, TBSMA_EINVAL, "the wait limit must be >= 1");
+  c->wait_limit = steps;
+  return TBSMA_OK;
+}
+
+// Rebuild every wire's list from the current positions and recompute the
+// forces: the state after this is a function of (x, v, counters) alone.
+tbsma_status rebuild_all(tbsma_ctx* c) {
+  TB_TRY(refresh(c, 1));
+  TB_TRY(launch_pair<false>(c, c->stream, c->prec));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_save_state(tbsma_ctx* c, double* x_host, double* v_host,
+                              tbsma_wire_state* wires, int64_t* step) {
+  if (!c || !x_host || !v_host || !wires || !step) return TBSMA_EINVAL;
+  TB_TRY(rebuild_all(c));
+  const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+  std::vector<double> dg(c->W);
+  std::vector<int32_t> nr(c->W);
+  std::vector<uint32_t> ws(c->W);
+  std::vector<NhState> nh(c->W);
+  int64_t sc = 0;
+  TB_CUDA(c, cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(v_host, c->v, bytes, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(dg.data(), c->d_grip, sizeof(double) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(nr.data(), c->n_rebuilds, sizeof(int32_t) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(ws.data(), c->wire_status, sizeof(uint32_t) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(nh.data(), c->nh, sizeof(NhState) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(&sc, c->step_counter, sizeof sc, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int w = 0; w < c->W; ++w) {
+    wires[w].d_grip = dg[w];
+    wires[w].xi = nh[w].xi;
+    wires[w].eta = nh[w].eta;
+    wires[w].n_rebuilds = nr[w];
+    wires[w].status = ws[w];
+  }
+  *step = sc;
+  if (sc != c->steps_done) return fail(c, TBSMA_ESTATE, "device and host step counts disagree");
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_restore_state(tbsma_ctx* c, const double* x_host, const double* v_host,
+                                 const tbsma_wire_state* wires, int64_t step) {
+  if (!c || !x_host || !v_host || !wires || step < 0) return TBSMA_EINVAL;
+  const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+  std::vector<double> dg(c->W);
+  std::vector<int32_t> nr(c->W);
+  std::vector<uint32_t> ws(c->W);
+  std::vector<NhState> nh(c->W);
+  for (int w = 0; w < c->W; ++w) {
+    dg[w] = wires[w].d_grip;
+    nr[w] = wires[w].n_rebuilds;
+    ws[w] = wires[w].status;
+    nh[w] = NhState{wires[w].xi, wires[w].eta, 1.0, 0.f};
+  }
+  TB_CUDA(c, cudaMemcpyAsync(c->x, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->v, v_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->d_grip, dg.data(), sizeof(double) * c->W, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->n_rebuilds, nr.data(), sizeof(int32_t) * c->W, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->wire_status, ws.data(), sizeof(uint32_t) * c->W, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->nh, nh.data(), sizeof(NhState) * c->W, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->step_counter, &step, sizeof step, cudaMemcpyHostToDevice, c->stream));
+  c->steps_done = step;
+  TB_TRY(rebuild_all(c));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));  // the host buffers may be released on return
   return TBSMA_OK;
 }
 

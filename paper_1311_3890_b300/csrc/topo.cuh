@@ -17,14 +17,14 @@
 
 namespace tbsma {
 
-constexpr int kUfSteps = 1 << 20;    // bound of one root walk
+constexpr int kUfSteps = 1 << 20;    // default bound of one root walk (tbsma_set_wait_limit)
 constexpr int kUfRetries = 1 << 16;  // bound of one link's retries
 constexpr int kMaxSlabs = 4096;      // slabs per wire in the neck histogram
 constexpr double kSlabWidth = 0.5 * 4.079;  // a/2, the (100) plane spacing of the wires, A
 constexpr uint32_t kUfGaveUp = 2u;
 
-__device__ __forceinline__ int uf_find(int* parent, int a, uint32_t* err) {
-  for (int s = 0; s < kUfSteps; ++s) {
+__device__ __forceinline__ int uf_find(int* parent, int a, int limit, uint32_t* err) {
+  for (int s = 0; s < limit; ++s) {
     const int p = __ldcg(parent + a);
     if (p == a) return a;
     const int gp = __ldcg(parent + p);
@@ -35,9 +35,9 @@ __device__ __forceinline__ int uf_find(int* parent, int a, uint32_t* err) {
   return a;
 }
 
-__device__ __forceinline__ void uf_union(int* parent, int a, int b, uint32_t* err) {
+__device__ __forceinline__ void uf_union(int* parent, int a, int b, int limit, uint32_t* err) {
   for (int r = 0; r < kUfRetries; ++r) {
-    int ra = uf_find(parent, a, err), rb = uf_find(parent, b, err);
+    int ra = uf_find(parent, a, limit, err), rb = uf_find(parent, b, limit, err);
     if (ra == rb) return;
     if (ra > rb) {
       const int tmp = ra;
@@ -60,7 +60,7 @@ template <int PREC>
 __global__ void k_uf_link(int64_t N, const int4* __restrict__ xq, const double4_32a* __restrict__ xd,
                           const int16_t* __restrict__ nbr, const int32_t* __restrict__ n_nbr,
                           const int32_t* __restrict__ perm, int cap, PairConsts pc, int* parent,
-                          uint32_t* err) {
+                          int limit, uint32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = perm[t];
@@ -76,13 +76,13 @@ __global__ void k_uf_link(int64_t N, const int4* __restrict__ xq, const double4_
       const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
       in = dx * dx + dy * dy + dz * dz <= pc.rc2;
     }
-    if (in) uf_union(parent, i, j, err);
+    if (in) uf_union(parent, i, j, limit, err);
   }
 }
 
-__global__ void k_uf_compress(int64_t N, int* parent, uint32_t* err) {
+__global__ void k_uf_compress(int64_t N, int* parent, int limit, uint32_t* err) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) parent[i] = uf_find(parent, (int)i, err);
+  if (i < N) parent[i] = uf_find(parent, (int)i, limit, err);
 }
 
 // Block per wire: grip connectivity, cluster count and the neck histogram
@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256)
         best = min(best, ((long long)cnt[k] << 32) | k);
       best = -block_max(-best, shl);
       o.n_slabs = (int32_t)ns;
+      o.neck = 0;  // no slab between the grips: no section to count
       if (ns > 0) {
         o.neck = (int32_t)(best >> 32);
         o.neck_slab = (int32_t)(best & 0xffffffffLL);

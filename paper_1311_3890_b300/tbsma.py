@@ -101,6 +101,13 @@ class TopologyC(ctypes.Structure):
                                                  "n_slabs", "status")]
 
 
+class WireStateC(ctypes.Structure):
+    """tbsma_wire_state (include/tbsma.h)."""
+
+    _fields_ = [("d_grip", ctypes.c_double), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
+                ("n_rebuilds", ctypes.c_int32), ("status", ctypes.c_uint32)]
+
+
 THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
 PULLS = {"continuous": 0, "stepwise": 1}
 
@@ -123,6 +130,9 @@ SIGNATURES = [
     ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("tbsma_restore_state", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     ("tbsma_normals", ctypes.c_int, [ctypes.c_uint64, _P, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_uint32, ctypes.c_int, _P, _P]),
@@ -303,6 +313,9 @@ class Engine:
         p = ProtocolC(THERMOSTATS[thermostat], PULLS[pull], tau_fs, pull_step, int(pull_interval),
                       t_start, int(ramp_steps))
         self._check(lib().tbsma_set_protocol(self.ctx, ctypes.byref(p)), "tbsma_set_protocol")
+        self.protocol = dict(thermostat=thermostat, pull=pull, tau_fs=tau_fs, pull_step=pull_step,
+                             pull_interval=int(pull_interval), t_start=t_start,
+                             ramp_steps=int(ramp_steps))
 
     def thermostat(self):
         """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""
@@ -327,6 +340,59 @@ class Engine:
         if labels:
             res["labels"] = lab
         return res
+
+    def set_wait_limit(self, steps: int):
+        """Bound of the topology's union-find walks (a failure-detection test hook)."""
+        self._check(lib().tbsma_set_wait_limit(self.ctx, int(steps)), "tbsma_set_wait_limit")
+
+    def save(self, path: str):
+        """Checkpoint into directory `path` (tbsma_save_state): header.json and
+        raw little-endian float64 SoA arrays x.f64, v.f64 (3N each)."""
+        import json
+        import os
+
+        os.makedirs(path, exist_ok=True)
+        x = np.empty(3 * self.N)
+        v = np.empty(3 * self.N)
+        ws = (WireStateC * self.W)()
+        step = ctypes.c_int64(0)
+        self._check(lib().tbsma_save_state(self.ctx, x.ctypes.data_as(ctypes.c_void_p),
+                                           v.ctypes.data_as(ctypes.c_void_p), ws,
+                                           ctypes.byref(step)), "tbsma_save_state")
+        x.astype("<f8").tofile(os.path.join(path, "x.f64"))
+        v.astype("<f8").tofile(os.path.join(path, "v.f64"))
+        header = {
+            "format": "tbsma-checkpoint-1", "n_atoms": self.N, "n_wires": self.W,
+            "precision": "mixed" if self.precision == MIXED else "fp64", "step": int(step.value),
+            "protocol": getattr(self, "protocol", None),
+            "wires": [{k: getattr(w, k) for k, _ in WireStateC._fields_} for w in ws],
+        }
+        with open(os.path.join(path, "header.json"), "w") as f:
+            json.dump(header, f, indent=1)
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by save() for the same batch layout
+        (re-applies its protocol first, then tbsma_restore_state)."""
+        import json
+        import os
+
+        with open(os.path.join(path, "header.json")) as f:
+            header = json.load(f)
+        if header.get("format") != "tbsma-checkpoint-1":
+            raise ValueError("not a tbsma checkpoint")
+        if header["n_atoms"] != self.N or header["n_wires"] != self.W:
+            raise ValueError("checkpoint of a different batch layout")
+        if header.get("protocol"):
+            self.set_protocol(**header["protocol"])
+        x = np.fromfile(os.path.join(path, "x.f64"), dtype="<f8").astype(np.float64)
+        v = np.fromfile(os.path.join(path, "v.f64"), dtype="<f8").astype(np.float64)
+        ws = (WireStateC * self.W)()
+        for w, d in zip(ws, header["wires"]):
+            for k, _ in WireStateC._fields_:
+                setattr(w, k, d[k])
+        self._check(lib().tbsma_restore_state(self.ctx, x.ctypes.data_as(ctypes.c_void_p),
+                                              v.ctypes.data_as(ctypes.c_void_p), ws,
+                                              int(header["step"])), "tbsma_restore_state")
 
     def run_pass(self, which: int, reps: int = 1):
         """Enqueue `reps` launches of pass 1 (density) or 2 (force) alone."""

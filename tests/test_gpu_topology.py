@@ -156,3 +156,24 @@ def test_pull_to_rupture_batch(tb):
         assert r.final_neck >= 0 and r.neck[0] > 0
         assert (r.strain[-1] - r.eps_f) * w.L0 >= 2.0
     eng.close()
+
+
+def test_wait_limit_gives_up_and_context_recovers(tb, orc):
+    """Failure detection without a fault: a walk bound of one step is too
+    small for the union-find of a whole wire, so the call gives up with
+    TBSMA_ETIMEOUT and status 2; with the default bound restored the same
+    context answers correctly."""
+    w = fcc_wire(2.0, 6.0)
+    eng = tb.Engine(pack([_wire(w.x, w.kind)]), precision="mixed")
+    eng.set_wait_limit(1)
+    with pytest.raises(tb.TbsmaError) as e:
+        eng.topology()
+    assert e.value.status == 5  # TBSMA_ETIMEOUT
+    eng.set_wait_limit(1 << 20)
+    got = eng.topology()
+    ref = orc.topology(w.x, w.kind)
+    assert got["status"][0] == 0 and bool(got["connected"][0]) == ref.connected
+    assert got["neck"][0] == ref.neck and got["n_clusters"][0] == ref.n_clusters
+    with pytest.raises(tb.TbsmaError):
+        eng.set_wait_limit(0)
+    eng.close()
