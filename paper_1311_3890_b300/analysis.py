@@ -14,6 +14,15 @@ tbsma_wire_topology every `report_every` steps):
   end       a run stops when every wire has failed and been pulled 2 A past
             its failure (Methods: the runs continue 2 A beyond failure), or
             after `max_steps`.
+  mode      the post-yield strain eps_f - eps_y separates brittle failure
+            (the wire fails right after yielding) from ductile failure; the
+            paper shows the bimodal distributions (Figures 4-8) without a
+            numeric cut, so the cut is a parameter (default 0.1);
+  L_C       Eq. 6, L_C = (D0 / eps_y) cot(alpha) with cot(alpha) from 1
+            (perfect dislocations) to sqrt(2) (partial dislocations) for
+            [100] wires; the observed L_C is the midpoint between the
+            longest L0 with predominantly ductile failure and the shortest
+            L0 with predominantly brittle failure.
 This module only reads what the library reports; it does no MD arithmetic.
 """
 
@@ -70,6 +79,48 @@ class WireResult:
 
 
 EV_PER_A3_IN_GPA = 160.21766208  # 1 eV/A^3 in GPa
+
+
+def critical_length(d0_nm: float, eps_y: float) -> tuple[float, float]:
+    """Eq. 6 range (nm): (D0/eps_y) cot(alpha) for cot(alpha) = 1 and sqrt(2)."""
+    base = d0_nm / eps_y
+    return base, base * math.sqrt(2.0)
+
+
+def post_yield_strain(eps_f, eps_y) -> np.ndarray:
+    return np.asarray(eps_f, dtype=np.float64) - np.asarray(eps_y, dtype=np.float64)
+
+
+def brittle(eps_f, eps_y, cut: float = 0.1) -> np.ndarray:
+    """True where the wire failed within `cut` of strain after yielding."""
+    return post_yield_strain(eps_f, eps_y) < cut
+
+
+def observed_critical_length(lengths, eps_f, eps_y, cut: float = 0.1) -> float:
+    """Midpoint between the longest initial length whose wires fail mostly
+    (>= half) ductile and the shortest one whose wires fail mostly brittle,
+    over groups of wires by initial length (nan if no such pair)."""
+    lengths = np.asarray(lengths, dtype=np.float64)
+    b = brittle(eps_f, eps_y, cut)
+    groups = sorted(set(lengths.tolist()))
+    frac = {L: float(np.mean(b[lengths == L])) for L in groups}
+    ductile = [L for L in groups if frac[L] < 0.5]
+    brit = [L for L in groups if frac[L] >= 0.5]
+    if not ductile or not brit:
+        return math.nan
+    lo = max(L for L in ductile if L < min(brit)) if any(L < min(brit) for L in ductile) else None
+    if lo is None:
+        return math.nan
+    return 0.5 * (lo + min(L for L in brit if L > lo))
+
+
+def failure_map(lengths, eps_f, eps_y, length_edges, strain_edges) -> np.ndarray:
+    """Counts of wires per (initial length, post-yield strain) bin: the
+    histograms behind the paper's failure heat maps."""
+    h, _, _ = np.histogram2d(np.asarray(lengths, dtype=np.float64),
+                             post_yield_strain(eps_f, eps_y),
+                             bins=[np.asarray(length_edges), np.asarray(strain_edges)])
+    return h
 
 
 def pull_to_rupture(eng, report_every: int, max_steps: int, dt: float = 2.0,

@@ -35,3 +35,35 @@ def test_failure_strain_and_final_neck():
     assert ef == eps[4] and fn == 9
     ef, fn = failure(eps, np.ones(10, bool), neck)
     assert math.isnan(ef) and fn == -1
+
+
+def test_critical_length_worked_example():
+    """Eq. 6's worked example as printed (golden fixture): D0 = 3.1 nm and
+    eps_y = 0.076 give L_C between 40.8 and 57.7 nm."""
+    import json
+    import os
+
+    from paper_1311_3890_b300.analysis import critical_length
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "critical_length_eq6.json")) as f:
+        g = json.load(f)
+    lo, hi = critical_length(g["D0_nm"], g["eps_y"])
+    tol = g["printed_precision_nm"]
+    assert abs(lo - g["L_C_range_nm_printed"][0]) <= tol
+    assert abs(hi - g["L_C_range_nm_printed"][1]) <= tol
+
+
+def test_observed_critical_length_and_failure_map():
+    from paper_1311_3890_b300.analysis import failure_map, observed_critical_length
+
+    # 20 and 40 nm wires fail ductile (post-yield strain 0.3), 60 and 80 nm brittle (0.02)
+    L = np.repeat([20.0, 40.0, 60.0, 80.0], 10)
+    eps_y = np.full(L.size, 0.08)
+    eps_f = eps_y + np.where(L < 50, 0.3, 0.02)
+    assert observed_critical_length(L, eps_f, eps_y) == 50.0
+    # one brittle outlier among ductile wires does not move it
+    eps_f[0] = eps_y[0] + 0.01
+    assert observed_critical_length(L, eps_f, eps_y) == 50.0
+    h = failure_map(L, eps_f, eps_y, [0, 30, 50, 70, 90], [0.0, 0.1, 1.0])
+    np.testing.assert_array_equal(h, [[1, 9], [0, 10], [10, 0], [10, 0]])
+    assert np.isnan(observed_critical_length(L[:20], eps_f[:20], eps_y[:20]))
