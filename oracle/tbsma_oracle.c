@@ -470,6 +470,19 @@ void or_md_batch(const or_pot* P, const or_md* M, int n_wires, const or_wire* W,
  * Pull (pull = 1, stepwise): in step s each grip moves by -/+ pull_step
  * (rigidly) when (s + 1) is a multiple of pull_interval, else not at all;
  * pull = 0 keeps the continuous delta = strain_rate L0 dt / 2 per step.
+ *
+ * Axial barostat (baro_tau > 0; Methods: the wire is first equilibrated at
+ * zero pressure along [100]): at the start of every step, with sigma_xx the
+ * wire's axial stress at the current state (Eq. 5, the pair virial of the
+ * current positions and the mobile kinetic term), every atom's x moves about
+ * the centre c of the grips (the mean x of the grip atoms) by the factor
+ *   mu = exp(-dt (sigma_xx - baro_pressure) / (baro_modulus baro_tau)),
+ * and lambda += log(mu) accumulates the wire's axial log-stretch.  A wire
+ * under more tension than the target (sigma_xx, tension positive, above it)
+ * shortens and one under less lengthens until sigma_xx reaches the target,
+ * relaxing with the time baro_tau baro_modulus / E (E the wire's axial
+ * modulus).  The step's first kick uses the forces of the
+ * unscaled positions.  The grips' pull displacement d_grip is not changed.
  * ==================================================================== */
 typedef struct {
   int thermostat;        /* 0 Langevin (B A O A B), 1 Nosé–Hoover */
@@ -479,6 +492,9 @@ typedef struct {
   int64_t pull_interval; /* stepwise: steps per event */
   double t_start;        /* ramp start temperature, K */
   int64_t ramp_steps;    /* 0: no ramp */
+  double baro_tau;       /* axial barostat time, fs; 0: off */
+  double baro_modulus;   /* its reference modulus, eV/A^3 */
+  double baro_pressure;  /* its target sigma_xx, eV/A^3 */
 } or_protocol;
 
 double or_target_temperature(const or_protocol* R, double T_w, int64_t s) {
@@ -510,8 +526,26 @@ static void nh_half(int n, double* v, const uint8_t* kind, double m_e, double g,
   *xi += 0.5 * h * (2.0 * K - g * kT) / Q;
 }
 
+/* Axial stress of a wire (Eq. 5 with D7's hard-sphere volume). */
+static double axial_stress(const or_pot* P, const or_md* M, int n, const double* x,
+                           const double* v, const uint8_t* kind, int brute_max) {
+  double* w = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  or_energy_forces(P, n, x, brute_max, NULL, NULL, NULL, NULL, w, NULL, NULL);
+  double vir = 0.0, mv2x = 0.0;
+  for (int i = 0; i < n; ++i) {
+    vir += w[i];
+    if (kind[i] == 0) mv2x += v[3 * i] * v[3 * i];
+  }
+  free(w);
+  const double pi = 3.141592653589793238462643383279;
+  double rhs = 0.5 * P->r0;
+  double V = (double)n * (4.0 / 3.0) * pi * rhs * rhs * rhs;
+  return (vir - M->mass * OR_MVV2E * mv2x) / V;
+}
+
 /* Protocol-mode MD steps for one wire; arguments as or_md_steps, plus the
- * protocol and the wire's thermostat state nh = {xi, eta} (in/out). */
+ * protocol and the wire's state nh = {xi, eta, lambda} (in/out: the
+ * Nosé–Hoover variable, its integral and the barostat's log-stretch). */
 void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, const or_protocol* R,
                           int n, double* x, double* v, const uint8_t* kind, double* F,
                           double* x_build, int64_t step0, int64_t n_steps, double dt,
@@ -528,6 +562,20 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
   int nh_on = R->thermostat == 1 && Q > 0.0;
   for (int64_t s = 0; s < n_steps; ++s) {
     int64_t step = step0 + s;
+    if (R->baro_tau > 0.0) {
+      double sig = axial_stress(P, M, n, x, v, kind, brute_max);
+      double dl = -dt * (sig - R->baro_pressure) / (R->baro_modulus * R->baro_tau);
+      double mu = exp(dl);
+      double c = 0.0;
+      long ng = 0;
+      for (int i = 0; i < n; ++i)
+        if (kind[i] != 0) c += x[3 * i], ++ng;
+      if (ng > 0) {
+        c /= (double)ng;
+        for (int i = 0; i < n; ++i) x[3 * i] = c + (x[3 * i] - c) * mu;
+      }
+      nh[2] += dl;
+    }
     double T = or_target_temperature(R, W->temperature, step);
     double kT = OR_KB_EV_PER_K * T;
     double delta;
@@ -583,7 +631,7 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
   }
 }
 
-/* Many wires in protocol mode; nh is [n_wires][2]. */
+/* Many wires in protocol mode; nh is [n_wires][3]. */
 void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R, int n_wires,
                           const or_wire* W, const long* offset, const int* count, double* x,
                           double* v, const uint8_t* kind, double* F, double* x_build,
@@ -594,7 +642,7 @@ void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R,
     long o = offset[w];
     or_md_steps_protocol(P, M, &W[w], R, count[w], x + 3 * o, v + 3 * o, kind + o, F + 3 * o,
                          x_build ? x_build + 3 * o : NULL, step0, n_steps, dt, &d_grip[w],
-                         n_rebuild ? &n_rebuild[w] : NULL, nh + 2 * w, brute_max);
+                         n_rebuild ? &n_rebuild[w] : NULL, nh + 3 * w, brute_max);
   }
 }
 

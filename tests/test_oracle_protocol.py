@@ -27,7 +27,7 @@ def _nh_run(orc, x, v, T, tau, dt, n_steps, pot=None, kind=None):
     pot = orc.AU if pot is None else pot
     st = orc.WireState(x=x.copy(), v=v.copy(), kind=kind, L0=1.0, temperature=T)
     proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=tau)
-    nh = np.zeros(2)
+    nh = np.zeros(3)
     rows = []
     for _ in range(n_steps):
         st, nh = orc.md_steps_protocol(st, proto, 1, dt, nh=nh, pot=pot)
@@ -104,7 +104,7 @@ def test_nh_mean_temperature(orc):
     st = orc.WireState(x=x.copy(), v=orc.init_velocities(np.zeros(n, np.uint8), 5, 300.0),
                        kind=np.zeros(n, np.uint8), L0=1.0, temperature=300.0)
     proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=100.0)
-    nh = np.zeros(2)
+    nh = np.zeros(3)
     st, nh = orc.md_steps_protocol(st, proto, 1000, 2.0, nh=nh)
     temps = []
     for _ in range(100):
@@ -124,7 +124,7 @@ def test_stepwise_pull_closed_form(orc):
                          pull_interval=40)
     left, right = kind == KIND_GRIP_LEFT, kind == KIND_GRIP_RIGHT
     x0 = w.x.copy()
-    nh = np.zeros(2)
+    nh = np.zeros(3)
     for s in range(130):
         before = st.x.copy()
         st, nh = orc.md_steps_protocol(st, proto, 1, 2.0, nh=nh)
@@ -173,3 +173,72 @@ def test_protocol_langevin_continuous_equals_md_steps(orc):
     np.testing.assert_array_equal(a.x, b.x)
     np.testing.assert_array_equal(a.v, b.v)
     assert a.d_grip == b.d_grip and a.n_rebuild == b.n_rebuild
+
+
+def _baro_run(orc, w, x0, steps, P=0.0, tau_p=100.0):
+    st = orc.WireState(x=x0.copy(), v=np.zeros_like(x0), kind=w.kind, L0=w.L0, temperature=0.01)
+    proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=200.0,
+                         baro_tau=tau_p, baro_pressure=P)
+    nh = np.zeros(3)
+    sig, lam = [], []
+    for _ in range(steps // 50):
+        st, nh = orc.md_steps_protocol(st, proto, 50, 2.0, nh=nh)
+        sig.append(orc.observables(st).sigma_xx)
+        lam.append(nh[2])
+    return np.array(sig), np.array(lam), st
+
+
+def test_barostat_direction(orc):
+    """A wire stretched by 2 % (affinely, about its centre) is under tension
+    and the barostat shortens it (lambda < 0); one compressed by 8 % is under
+    compression (the unrelaxed 2 nm wire's surface stress puts its zero near
+    -4 %) and is lengthened (lambda > 0)."""
+    w = fcc_wire(2.0, 3.0)
+    c = 0.5 * (w.x[:, 0].min() + w.x[:, 0].max())
+    for f, sign in ((1.02, -1.0), (0.92, 1.0)):
+        x = w.x.copy()
+        x[:, 0] = c + (x[:, 0] - c) * f
+        assert np.sign(orc.observables(orc.WireState(x=x, v=np.zeros_like(x), kind=w.kind,
+                                                     L0=w.L0)).sigma_xx) == -sign
+        _, lam, _ = _baro_run(orc, w, x, 200)
+        assert np.sign(lam[-1]) == sign
+
+
+@pytest.mark.parametrize("P", [0.0, 0.0025])
+def test_barostat_reaches_the_target_stress(orc, P):
+    """Near 0 K the barostat drives the wire to sigma_xx = P (0 and 0.4 GPa):
+    the stress averaged over the last 0.4 ps is within 1e-4 eV/A^3 (16 MPa)
+    of the target, and the stretch has stopped moving."""
+    w = fcc_wire(2.0, 3.0)
+    sig, lam, _ = _baro_run(orc, w, w.x, 2000, P=P)
+    assert abs(sig[-4:].mean() - P) < 1e-4
+    assert abs(lam[-1] - lam[-5]) < 2e-4
+
+
+def test_barostat_zero_stress_length_matches_a_strain_scan(orc):
+    """Independent check of the relaxed length: hold the wire at fixed
+    affine axial strains (grips rigid, no barostat), relax it near 0 K and
+    interpolate the strain at which sigma_xx crosses zero; the barostat's
+    final log-stretch equals it within 1e-3."""
+    w = fcc_wire(2.0, 3.0)
+    c = 0.5 * (w.x[:, 0].min() + w.x[:, 0].max())
+    proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=200.0)
+
+    def relaxed_stress(lam):
+        x = w.x.copy()
+        x[:, 0] = c + (x[:, 0] - c) * np.exp(lam)
+        st = orc.WireState(x=x, v=np.zeros_like(x), kind=w.kind, L0=w.L0, temperature=0.01)
+        nh = np.zeros(3)
+        st, nh = orc.md_steps_protocol(st, proto, 1500, 2.0, nh=nh)
+        s = []
+        for _ in range(8):
+            st, nh = orc.md_steps_protocol(st, proto, 50, 2.0, nh=nh)
+            s.append(orc.observables(st).sigma_xx)
+        return float(np.mean(s))
+
+    grid = [-0.06, -0.045, -0.03, -0.015]
+    sig = np.array([relaxed_stress(l) for l in grid])
+    k = int(np.flatnonzero(np.sign(sig[:-1]) != np.sign(sig[1:]))[0])  # bracketing pair
+    lam_scan = grid[k] + (grid[k + 1] - grid[k]) * sig[k] / (sig[k] - sig[k + 1])
+    _, lam, _ = _baro_run(orc, w, w.x, 2000)
+    assert abs(lam[-1] - lam_scan) < 1e-3
