@@ -77,6 +77,7 @@ class _Protocol(ctypes.Structure):
         ("baro_tau", ctypes.c_double),
         ("baro_modulus", ctypes.c_double),
         ("baro_pressure", ctypes.c_double),
+        ("baro_drag", ctypes.c_double),
     ]
 
 
@@ -354,15 +355,17 @@ class Protocol:
     pull_interval: int = 10000
     t_start: float = 0.01
     ramp_steps: int = 0
-    baro_tau: float = 0.0  # fs, 0 = no barostat
+    baro_tau: float = 0.0  # fs, barostat period / 2 pi at modulus baro_modulus; 0 = off
     baro_modulus: float = 100.0 / 160.21766208  # 100 GPa in eV/A^3
     baro_pressure: float = 0.0  # target sigma_xx, eV/A^3
+    baro_drag: float = 1.0  # barostat drag in units of 1/baro_tau
 
     def _c(self):
         th = {"langevin": 0, "nose_hoover": 1}[self.thermostat]
         pl = {"continuous": 0, "stepwise": 1}[self.pull]
         return _Protocol(th, pl, self.tau, self.pull_step, int(self.pull_interval), self.t_start,
-                         int(self.ramp_steps), self.baro_tau, self.baro_modulus, self.baro_pressure)
+                         int(self.ramp_steps), self.baro_tau, self.baro_modulus, self.baro_pressure,
+                         self.baro_drag)
 
 
 def target_temperature(proto: Protocol, T_w: float, step: int) -> float:
@@ -374,8 +377,9 @@ def md_steps_protocol(st: WireState, proto: Protocol, n_steps: int, dt: float,
                       r_skin: float = R_SKIN, brute_max: int = 2000):
     """Advance one wire by n_steps protocol-mode steps in place.
 
-    nh = [xi, eta, lambda] (the wire's Nosé–Hoover variable, its integral and
-    the barostat's log-stretch, in/out; zeros if None).  Returns (st, nh)."""
+    nh = [xi, eta, lambda, zeta] (the wire's Nosé–Hoover variable, its
+    integral, the barostat's log-stretch and strain rate, in/out; zeros if
+    None).  Returns (st, nh)."""
     st.x = _f64(st.x)
     st.v = _f64(st.v)
     kind = np.ascontiguousarray(st.kind, dtype=np.uint8)
@@ -383,7 +387,7 @@ def md_steps_protocol(st: WireState, proto: Protocol, n_steps: int, dt: float,
         st.F = tbsma(st.x, pot, brute_max).F
     if st.x_build is None:
         st.x_build = st.x.copy()
-    nh = np.zeros(3) if nh is None else np.ascontiguousarray(nh, dtype=np.float64)
+    nh = np.zeros(4) if nh is None else np.ascontiguousarray(nh, dtype=np.float64)
     p, m, r = pot._c(), _Md(mass, r_skin), proto._c()
     w = _Wire(st.L0, st.strain_rate, st.temperature, st.gamma, st.seed)
     dg = ctypes.c_double(st.d_grip)
@@ -403,7 +407,7 @@ def md_batch_protocol(proto: Protocol, x, v, kind, offset, count, L0, strain_rat
                       gamma, seed, step0: int, n_steps: int, dt: float, pot: Potential = AU,
                       mass: float = MASS_AU, r_skin: float = R_SKIN, brute_max: int = 2000,
                       F=None, x_build=None, d_grip=None, n_rebuild=None, nh=None):
-    """md_batch in protocol mode; nh is (W, 3) [xi, eta, lambda] per wire (in/out).
+    """md_batch in protocol mode; nh is (W, 4) [xi, eta, lambda, zeta] per wire (in/out).
 
     Returns (F, x_build, d_grip, n_rebuild, nh)."""
     W = len(count)
@@ -422,7 +426,7 @@ def md_batch_protocol(proto: Protocol, x, v, kind, offset, count, L0, strain_rat
     if n_rebuild is None:
         n_rebuild = np.zeros(W, dtype=np.int64)
     if nh is None:
-        nh = np.zeros((W, 3))
+        nh = np.zeros((W, 4))
     wires = (_Wire * W)(*[
         _Wire(float(L0[w]), float(strain_rate[w]), float(temperature[w]), float(gamma[w]),
               int(seed[w]))

@@ -471,18 +471,31 @@ void or_md_batch(const or_pot* P, const or_md* M, int n_wires, const or_wire* W,
  * (rigidly) when (s + 1) is a multiple of pull_interval, else not at all;
  * pull = 0 keeps the continuous delta = strain_rate L0 dt / 2 per step.
  *
- * Axial barostat (baro_tau > 0; Methods: the wire is first equilibrated at
- * zero pressure along [100]): at the start of every step, with sigma_xx the
- * wire's axial stress at the current state (Eq. 5, the pair virial of the
- * current positions and the mobile kinetic term), every atom's x moves about
- * the centre c of the grips (the mean x of the grip atoms) by the factor
- *   mu = exp(-dt (sigma_xx - baro_pressure) / (baro_modulus baro_tau)),
- * and lambda += log(mu) accumulates the wire's axial log-stretch.  A wire
- * under more tension than the target (sigma_xx, tension positive, above it)
- * shortens and one under less lengthens until sigma_xx reaches the target,
- * relaxing with the time baro_tau baro_modulus / E (E the wire's axial
- * modulus).  The step's first kick uses the forces of the
- * unscaled positions.  The grips' pull displacement d_grip is not changed.
+ * Axial Nosé–Hoover barostat (baro_tau > 0; Methods: the wire is first
+ * equilibrated for 100 ps at zero pressure along [100] with a Nosé–Hoover
+ * barostat).  One strain-rate variable zeta (1/fs) per wire, the wire's
+ * axial log-stretch lambda, and Hoover's constant-stress equations along x
+ * about the centre c of the grips (the mean x of the grip atoms):
+ *   dx/dt = v_x + zeta (x - c)            (every atom; grips have v = 0)
+ *   dv_x/dt = F_x/m - zeta v_x            (mobile atoms)
+ *   dzeta/dt = -V (sigma_xx - P) / W_b - gamma_b zeta,  dlambda/dt = zeta,
+ * sigma_xx the wire's axial stress (Eq. 5, tension positive, V = N (4/3)
+ * pi (r0/2)^3), P = baro_pressure and barostat mass W_b = V B tau_b^2
+ * (B = baro_modulus, tau_b = baro_tau: a wire of axial modulus B oscillates
+ * with angular frequency 1/tau_b) and drag gamma_b = baro_drag / tau_b.
+ * Because V sigma_xx = -sum_i F_x,i (x_i - c) - m sum v_x^2, these conserve
+ * (with the grips held, no thermostat and no drag) H = E_pot + K +
+ * W_b zeta^2/2 - P V lambda.  At the paper's 0.01 K nothing else damps the
+ * barostat's oscillation, so the drag (a reading: the paper names the
+ * barostat only) is what lets the length settle.  A step is the symmetric
+ * splitting (h = dt/2)
+ *   Z(h) C(h) [NH(h)] B(h) S(h) A(dt) S(h) [forces] B(h) [NH(h)] C(h) Z(h)
+ * with Z(h): zeta *= exp(-gamma_b h), then zeta -= h V (sigma_xx - P)/W_b
+ * at the current state (at the step's end: the kick, then the drag), C(h):
+ * mobile v_x *= exp(-zeta h), S(h): x = c + (x - c) exp(zeta h) for every
+ * atom and lambda += zeta h; A(dt) is the thermostat's drift (A, or A O A
+ * under Langevin) with the grip displacement, and c is taken once per step,
+ * at its start (the scaling and the symmetric grip moves leave it fixed).
  * ==================================================================== */
 typedef struct {
   int thermostat;        /* 0 Langevin (B A O A B), 1 Nosé–Hoover */
@@ -492,9 +505,10 @@ typedef struct {
   int64_t pull_interval; /* stepwise: steps per event */
   double t_start;        /* ramp start temperature, K */
   int64_t ramp_steps;    /* 0: no ramp */
-  double baro_tau;       /* axial barostat time, fs; 0: off */
-  double baro_modulus;   /* its reference modulus, eV/A^3 */
+  double baro_tau;       /* axial barostat time tau_b, fs; 0: off */
+  double baro_modulus;   /* its reference modulus B, eV/A^3 */
   double baro_pressure;  /* its target sigma_xx, eV/A^3 */
+  double baro_drag;      /* its drag gamma_b in units of 1/tau_b */
 } or_protocol;
 
 double or_target_temperature(const or_protocol* R, double T_w, int64_t s) {
@@ -543,13 +557,41 @@ static double axial_stress(const or_pot* P, const or_md* M, int n, const double*
   return (vir - M->mass * OR_MVV2E * mv2x) / V;
 }
 
+/* Z(h): the drag zeta *= exp(-gamma_b h) and the kick zeta -= h V (sigma_xx
+ * - P) / W_b = h (sigma_xx - P) / (B tau_b^2); drag first at a step's start
+ * (end = 0), kick first at its end (end = 1). */
+static void baro_z(const or_pot* P, const or_md* M, const or_protocol* R, int n, const double* x,
+                   const double* v, const uint8_t* kind, int brute_max, double h, int end,
+                   double* zeta) {
+  double drag = exp(-R->baro_drag / R->baro_tau * h);
+  if (!end) *zeta *= drag;
+  double sig = axial_stress(P, M, n, x, v, kind, brute_max);
+  *zeta -= h * (sig - R->baro_pressure) / (R->baro_modulus * R->baro_tau * R->baro_tau);
+  if (end) *zeta *= drag;
+}
+
+/* C(h): mobile v_x *= exp(-zeta h). */
+static void baro_c(int n, double* v, const uint8_t* kind, double zeta, double h) {
+  double sc = exp(-zeta * h);
+  for (int i = 0; i < n; ++i)
+    if (kind[i] == 0) v[3 * i] *= sc;
+}
+
+/* S(h): every atom's x = c + (x - c) exp(zeta h); lambda += zeta h. */
+static void baro_s(int n, double* x, double c, double zeta, double h, double* lambda) {
+  double mu = exp(zeta * h);
+  for (int i = 0; i < n; ++i) x[3 * i] = c + (x[3 * i] - c) * mu;
+  *lambda += zeta * h;
+}
+
 /* Protocol-mode MD steps for one wire; arguments as or_md_steps, plus the
- * protocol and the wire's state nh = {xi, eta, lambda} (in/out: the
- * Nosé–Hoover variable, its integral and the barostat's log-stretch). */
+ * protocol and the wire's state nh = {xi, eta, lambda, zeta} (in/out: the
+ * Nosé–Hoover variable, its integral, the barostat's log-stretch and its
+ * strain rate). */
 void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, const or_protocol* R,
                           int n, double* x, double* v, const uint8_t* kind, double* F,
                           double* x_build, int64_t step0, int64_t n_steps, double dt,
-                          double* d_grip, int64_t* n_rebuild, double nh[2], int brute_max) {
+                          double* d_grip, int64_t* n_rebuild, double nh[4], int brute_max) {
   double m_e = M->mass * OR_MVV2E;
   double inv_m = 1.0 / m_e;
   double c1 = exp(-W->gamma * dt);
@@ -560,21 +602,17 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
   double g = 3.0 * (double)nm;
   double Q = g * OR_KB_EV_PER_K * W->temperature * R->tau * R->tau;
   int nh_on = R->thermostat == 1 && Q > 0.0;
+  int baro_on = R->baro_tau > 0.0;
   for (int64_t s = 0; s < n_steps; ++s) {
     int64_t step = step0 + s;
-    if (R->baro_tau > 0.0) {
-      double sig = axial_stress(P, M, n, x, v, kind, brute_max);
-      double dl = -dt * (sig - R->baro_pressure) / (R->baro_modulus * R->baro_tau);
-      double mu = exp(dl);
-      double c = 0.0;
+    double c = 0.0;
+    if (baro_on) {
       long ng = 0;
       for (int i = 0; i < n; ++i)
         if (kind[i] != 0) c += x[3 * i], ++ng;
-      if (ng > 0) {
-        c /= (double)ng;
-        for (int i = 0; i < n; ++i) x[3 * i] = c + (x[3 * i] - c) * mu;
-      }
-      nh[2] += dl;
+      c = ng > 0 ? c / (double)ng : 0.0;
+      baro_z(P, M, R, n, x, v, kind, brute_max, 0.5 * dt, 0, &nh[3]); /* Z(h) */
+      baro_c(n, v, kind, nh[3], 0.5 * dt);                             /* C(h) */
     }
     double T = or_target_temperature(R, W->temperature, step);
     double kT = OR_KB_EV_PER_K * T;
@@ -585,10 +623,13 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
       delta = W->strain_rate * 1.0e-15 * W->L0 * dt / 2.0;
     if (R->thermostat == 1) {
       if (nh_on) nh_half(n, v, kind, m_e, g, kT, Q, 0.5 * dt, &nh[0], &nh[1]);
+      for (int i = 0; i < n; ++i)
+        if (kind[i] == 0)
+          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
+      if (baro_on) baro_s(n, x, c, nh[3], 0.5 * dt, &nh[2]);                       /* S(h) */
       for (int i = 0; i < n; ++i) {
         if (kind[i] == 0) {
-          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
-          for (int d = 0; d < 3; ++d) x[3 * i + d] += dt * v[3 * i + d];               /* A */
+          for (int d = 0; d < 3; ++d) x[3 * i + d] += dt * v[3 * i + d]; /* A */
         } else {
           x[3 * i + 0] += (kind[i] == 1) ? -delta : delta;
           v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
@@ -596,9 +637,12 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
       }
     } else {
       double sig = sqrt(kT * inv_m);
+      for (int i = 0; i < n; ++i)
+        if (kind[i] == 0)
+          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
+      if (baro_on) baro_s(n, x, c, nh[3], 0.5 * dt, &nh[2]);                       /* S(h) */
       for (int i = 0; i < n; ++i) {
         if (kind[i] == 0) {
-          for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
           for (int d = 0; d < 3; ++d) x[3 * i + d] += 0.5 * dt * v[3 * i + d];         /* A */
           double gn[3];
           or_normals3(W->seed, (uint32_t)i, (uint64_t)step, 0, gn);
@@ -610,6 +654,7 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
         }
       }
     }
+    if (baro_on) baro_s(n, x, c, nh[3], 0.5 * dt, &nh[2]); /* S(h) */
     *d_grip += delta;
     if (x_build) {
       int need = 0;
@@ -628,10 +673,14 @@ void or_md_steps_protocol(const or_pot* P, const or_md* M, const or_wire* W, con
       if (kind[i] == 0)
         for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * dt * F[3 * i + d] * inv_m; /* B */
     if (nh_on) nh_half(n, v, kind, m_e, g, kT, Q, 0.5 * dt, &nh[0], &nh[1]);
+    if (baro_on) {
+      baro_c(n, v, kind, nh[3], 0.5 * dt);                             /* C(h) */
+      baro_z(P, M, R, n, x, v, kind, brute_max, 0.5 * dt, 1, &nh[3]); /* Z(h) */
+    }
   }
 }
 
-/* Many wires in protocol mode; nh is [n_wires][3]. */
+/* Many wires in protocol mode; nh is [n_wires][4]. */
 void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R, int n_wires,
                           const or_wire* W, const long* offset, const int* count, double* x,
                           double* v, const uint8_t* kind, double* F, double* x_build,
@@ -642,7 +691,7 @@ void or_md_batch_protocol(const or_pot* P, const or_md* M, const or_protocol* R,
     long o = offset[w];
     or_md_steps_protocol(P, M, &W[w], R, count[w], x + 3 * o, v + 3 * o, kind + o, F + 3 * o,
                          x_build ? x_build + 3 * o : NULL, step0, n_steps, dt, &d_grip[w],
-                         n_rebuild ? &n_rebuild[w] : NULL, nh + 3 * w, brute_max);
+                         n_rebuild ? &n_rebuild[w] : NULL, nh + 4 * w, brute_max);
   }
 }
 

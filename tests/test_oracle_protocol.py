@@ -175,51 +175,96 @@ def test_protocol_langevin_continuous_equals_md_steps(orc):
     assert a.d_grip == b.d_grip and a.n_rebuild == b.n_rebuild
 
 
-def _baro_run(orc, w, x0, steps, P=0.0, tau_p=100.0):
+def _baro_run(orc, w, x0, steps, P=0.0, tau_b=100.0, drag=1.0):
+    """Barostat run near 0 K (NH at 0.01 K); (sigma, lambda, zeta) every 50 steps."""
     st = orc.WireState(x=x0.copy(), v=np.zeros_like(x0), kind=w.kind, L0=w.L0, temperature=0.01)
     proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=200.0,
-                         baro_tau=tau_p, baro_pressure=P)
-    nh = np.zeros(3)
-    sig, lam = [], []
+                         baro_tau=tau_b, baro_pressure=P, baro_drag=drag)
+    nh = np.zeros(4)
+    sig, lam, zeta = [], [], []
     for _ in range(steps // 50):
         st, nh = orc.md_steps_protocol(st, proto, 50, 2.0, nh=nh)
         sig.append(orc.observables(st).sigma_xx)
         lam.append(nh[2])
-    return np.array(sig), np.array(lam), st
+        zeta.append(nh[3])
+    return np.array(sig), np.array(lam), np.array(zeta)
+
+
+def _v_atom(orc):
+    return 4.0 / 3.0 * math.pi * (0.5 * orc.AU.r0) ** 3
+
+
+def test_barostat_extended_energy_second_order(orc):
+    """Without drag or thermostat the barostat's equations conserve
+    H = E_pot + K + W_b zeta^2/2 - P V lambda (W_b = V B tau_b^2); the
+    symmetric splitting keeps H to O(dt^2): over 1 ps of a D1.5 x L2.5 wire
+    at 5 K driven by a 0.48 GPa target (it contracts by ~9 %), halving dt
+    divides the excursion of H by 4 (within 15 %), and H moves 300 times
+    less than E_pot + K.  The cutoff is 40 A, beyond the whole wire, so that
+    no pair crosses it while the wire changes length (a pair crossing a hard
+    cutoff makes the energy jump, whatever the integrator)."""
+    import dataclasses
+
+    pot = dataclasses.replace(orc.AU, r_cut=40.0)
+    w = fcc_wire(1.5, 2.5)
+    T, P, tau_b, B = 5.0, 0.003, 150.0, 100.0 / 160.21766208
+    v0 = orc.init_velocities(w.kind, 5, T)
+    V = w.n * _v_atom(orc)
+    Wb = V * B * tau_b ** 2
+    excursion = []
+    for dt in (2.0, 1.0):
+        st = orc.WireState(x=w.x.copy(), v=v0.copy(), kind=w.kind, L0=w.L0, temperature=T,
+                           gamma=0.0)
+        proto = orc.Protocol(thermostat="langevin", pull="continuous", baro_tau=tau_b,
+                             baro_modulus=B, baro_pressure=P, baro_drag=0.0)
+        nh = np.zeros(4)
+        H, E = [], []
+        every = int(round(20.0 / dt))
+        for _ in range(50):
+            e = orc.energy(st.x, pot) + _kin(orc, st.v)
+            E.append(e)
+            H.append(e + 0.5 * Wb * nh[3] ** 2 - P * V * nh[2])
+            st, nh = orc.md_steps_protocol(st, proto, every, dt, nh=nh, pot=pot)
+        assert nh[2] < -0.03  # the wire did change length
+        H, E = np.array(H), np.array(E)
+        excursion.append(np.max(np.abs(H - H[0])))
+        assert np.max(np.abs(E - E[0])) > 300 * excursion[-1]
+    assert 3.4 < excursion[0] / excursion[1] < 4.6
 
 
 def test_barostat_direction(orc):
     """A wire stretched by 2 % (affinely, about its centre) is under tension
-    and the barostat shortens it (lambda < 0); one compressed by 8 % is under
-    compression (the unrelaxed 2 nm wire's surface stress puts its zero near
-    -4 %) and is lengthened (lambda > 0)."""
+    and the barostat's first step makes its strain rate negative; one
+    compressed by 8 % is under compression (the unrelaxed 2 nm wire's surface
+    stress puts its zero near -4 %) and gets a positive strain rate."""
     w = fcc_wire(2.0, 3.0)
     c = 0.5 * (w.x[:, 0].min() + w.x[:, 0].max())
+    proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=200.0, baro_tau=100.0)
     for f, sign in ((1.02, -1.0), (0.92, 1.0)):
         x = w.x.copy()
         x[:, 0] = c + (x[:, 0] - c) * f
-        assert np.sign(orc.observables(orc.WireState(x=x, v=np.zeros_like(x), kind=w.kind,
-                                                     L0=w.L0)).sigma_xx) == -sign
-        _, lam, _ = _baro_run(orc, w, x, 200)
-        assert np.sign(lam[-1]) == sign
+        st = orc.WireState(x=x, v=np.zeros_like(x), kind=w.kind, L0=w.L0, temperature=0.01)
+        assert np.sign(orc.observables(st).sigma_xx) == -sign
+        st, nh = orc.md_steps_protocol(st, proto, 1, 2.0)
+        assert np.sign(nh[3]) == sign and np.sign(nh[2]) == sign
 
 
 @pytest.mark.parametrize("P", [0.0, 0.0025])
 def test_barostat_reaches_the_target_stress(orc, P):
-    """Near 0 K the barostat drives the wire to sigma_xx = P (0 and 0.4 GPa):
-    the stress averaged over the last 0.4 ps is within 1e-4 eV/A^3 (16 MPa)
-    of the target, and the stretch has stopped moving."""
+    """Near 0 K the damped barostat drives the wire to sigma_xx = P (0 and
+    0.4 GPa): the stress of the last 0.4 ps is within 1e-4 eV/A^3 (16 MPa) of
+    the target and the strain rate has fallen below 1e-6 per fs."""
     w = fcc_wire(2.0, 3.0)
-    sig, lam, _ = _baro_run(orc, w, w.x, 2000, P=P)
+    sig, lam, zeta = _baro_run(orc, w, w.x, 2000, P=P)
     assert abs(sig[-4:].mean() - P) < 1e-4
-    assert abs(lam[-1] - lam[-5]) < 2e-4
+    assert np.max(np.abs(zeta[-4:])) < 1e-6
 
 
 def test_barostat_zero_stress_length_matches_a_strain_scan(orc):
     """Independent check of the relaxed length: hold the wire at fixed
     affine axial strains (grips rigid, no barostat), relax it near 0 K and
     interpolate the strain at which sigma_xx crosses zero; the barostat's
-    final log-stretch equals it within 1e-3."""
+    log-stretch after 4 ps equals it within 2e-3."""
     w = fcc_wire(2.0, 3.0)
     c = 0.5 * (w.x[:, 0].min() + w.x[:, 0].max())
     proto = orc.Protocol(thermostat="nose_hoover", pull="continuous", tau=200.0)
@@ -228,7 +273,7 @@ def test_barostat_zero_stress_length_matches_a_strain_scan(orc):
         x = w.x.copy()
         x[:, 0] = c + (x[:, 0] - c) * np.exp(lam)
         st = orc.WireState(x=x, v=np.zeros_like(x), kind=w.kind, L0=w.L0, temperature=0.01)
-        nh = np.zeros(3)
+        nh = np.zeros(4)
         st, nh = orc.md_steps_protocol(st, proto, 1500, 2.0, nh=nh)
         s = []
         for _ in range(8):
@@ -241,4 +286,5 @@ def test_barostat_zero_stress_length_matches_a_strain_scan(orc):
     k = int(np.flatnonzero(np.sign(sig[:-1]) != np.sign(sig[1:]))[0])  # bracketing pair
     lam_scan = grid[k] + (grid[k + 1] - grid[k]) * sig[k] / (sig[k] - sig[k + 1])
     _, lam, _ = _baro_run(orc, w, w.x, 2000)
-    assert abs(lam[-1] - lam_scan) < 1e-3
+    print(f"lambda scan {lam_scan:.5f}, barostat {lam[-1]:.5f}")
+    assert abs(lam[-1] - lam_scan) < 2e-3
