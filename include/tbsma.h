@@ -188,12 +188,35 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
  *               pull_interval, else not at all.
  *   ramp        the thermostat's target at step s is t_start + (T_w -
  *               t_start) min(1, s / ramp_steps); ramp_steps = 0: T_w.
+ *   barostat    (baro_tau_fs > 0; Methods: 100 ps at zero pressure along
+ *               [100] with a Nosé–Hoover barostat before the pull) Hoover's
+ *               constant-stress equations along x about the mean x, c, of
+ *               the wire's grip atoms: dx/dt = v_x + zeta (x - c) (every
+ *               atom), dv_x/dt = F_x/m - zeta v_x (mobile atoms), dzeta/dt =
+ *               -(sigma_xx - P)/(B tau_b^2) - gamma_b zeta, dlambda/dt =
+ *               zeta, with sigma_xx the wire's axial stress (Eq. 5, as
+ *               tbsma_reduce_observables), P = baro_pressure, B =
+ *               baro_modulus, tau_b = baro_tau_fs (barostat mass V B
+ *               tau_b^2: a wire of axial modulus B oscillates with angular
+ *               frequency 1/tau_b) and drag gamma_b = baro_drag / tau_b.
+ *               Without drag and thermostat E_pot + K + V B tau_b^2 zeta^2/2
+ *               - P V lambda is conserved.  Step (h = dt/2): Z C [NH] B S
+ *               A S [forces] B [NH] C Z, with Z the drag and stress kick of
+ *               zeta (kick first at the step's end), C: v_x *= exp(-zeta h),
+ *               S: x = c + (x - c) exp(zeta h), lambda += zeta h; c is
+ *               taken at the step's start.  The default sequence's merged
+ *               kicks are not used and every force pass also forms the
+ *               per-atom virial; the grips keep their pull (d_grip is not
+ *               changed by the scaling).
  * The paper's values: Nosé–Hoover (tau is not given; 1000 fs is this
  * library's reading), pull_step 0.05 A, pull_interval 10000, t_start
  * 0.01 K, ramp_steps 200000 (400 ps).  Resets every wire's thermostat
- * state (xi = eta = 0) and drops captured graphs.  Errors: EINVAL (unknown
- * thermostat or pull, tau_fs <= 0 under Nosé–Hoover, pull_interval < 1 or
- * non-finite pull_step under stepwise pull, t_start < 0 or ramp_steps < 0). */
+ * state (xi = eta = 0; lambda is kept) and drops captured graphs.  Errors:
+ * EINVAL (unknown thermostat or pull, tau_fs <= 0 under Nosé–Hoover,
+ * pull_interval < 1 or non-finite pull_step under stepwise pull, t_start < 0
+ * or ramp_steps < 0, baro_tau_fs < 0 or non-finite, and with the barostat on
+ * baro_modulus <= 0, baro_drag < 0, or any of them or baro_pressure
+ * non-finite). */
 typedef enum { TBSMA_THERMO_LANGEVIN = 0, TBSMA_THERMO_NOSE_HOOVER = 1 } tbsma_thermostat;
 typedef enum { TBSMA_PULL_CONTINUOUS = 0, TBSMA_PULL_STEPWISE = 1 } tbsma_pull;
 typedef struct {
@@ -204,6 +227,10 @@ typedef struct {
   int64_t pull_interval; /* stepwise: steps per event */
   double t_start;        /* ramp start temperature, K */
   int64_t ramp_steps;    /* ramp length in steps, 0 = no ramp */
+  double baro_tau_fs;    /* axial barostat time, fs; 0 = no barostat */
+  double baro_modulus;   /* its reference modulus, eV/A^3 */
+  double baro_pressure;  /* its target sigma_xx (tension positive), eV/A^3 */
+  double baro_drag;      /* its drag gamma_b in units of 1/baro_tau_fs */
 } tbsma_protocol;
 
 tbsma_status tbsma_set_protocol(tbsma_ctx* ctx, const tbsma_protocol* protocol);
@@ -213,6 +240,13 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* ctx, const tbsma_protocol* protocol);
  * energy E_pot + E_kin + Q xi^2/2 + g k_B T eta can be formed.  Zeros under
  * the Langevin thermostat.  Synchronises. */
 tbsma_status tbsma_get_thermostat(tbsma_ctx* ctx, double* xi, double* eta);
+
+/* Each wire's barostat state into host arrays of n_wires doubles (either
+ * nullable): the axial log-stretch lambda (the integral of zeta since
+ * tbsma_init or tbsma_restore_state: a wire of length L then has length
+ * L e^lambda, less its grips' pull) and the strain rate zeta (1/fs).  Kept
+ * across tbsma_set_protocol.  Synchronises. */
+tbsma_status tbsma_get_barostat(tbsma_ctx* ctx, double* lambda, double* zeta);
 
 /* Wire topology: rupture and neck (Results, "Nanowire elongation"; the paper
  * gives no formal definition).  Clusters are the connected components of
@@ -249,10 +283,12 @@ tbsma_status tbsma_wire_topology(tbsma_ctx* ctx, tbsma_topology* out, int32_t* l
 tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
 
 /* Checkpoint / resume.  A wire's counters: grip displacement (A), the
- * Nosé–Hoover state, the number of list rebuilds and its status word. */
+ * Nosé–Hoover state, the barostat's log-stretch and strain rate, the number
+ * of list rebuilds and its status word. */
 typedef struct {
   double d_grip;
   double xi, eta;
+  double log_stretch, stretch_rate; /* barostat lambda and zeta */
   int32_t n_rebuilds;
   uint32_t status;
 } tbsma_wire_state;

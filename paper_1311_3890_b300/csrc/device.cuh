@@ -72,6 +72,15 @@ struct ProtoDev {
   long long interval;  // stepwise: steps per event
   double t_start;      // ramp start temperature, K
   long long ramp;      // ramp length in steps, 0 = none
+  int baro;            // 1: the axial barostat scales x about BaroState::c
+};
+
+// One wire's axial Nosé–Hoover barostat: strain rate zeta (1/fs), the
+// log-stretch lambda, and for the current step the grips' centre c and the
+// half-step scale factor mu = exp(zeta dt/2) that the integrator applies
+// to x before and after its drift.
+struct BaroState {
+  double zeta, lam, c, mu;
 };
 
 // One wire's Nosé–Hoover state: xi (1/fs), its integral eta, and the

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256)
                 const int64_t* __restrict__ step_counter, int4* xq, double4_32a* xd,
                 const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
                 int32_t* flag, uint32_t* wire_status, double* d_grip, ProtoDev proto,
-                const NhState* __restrict__ nh) {
+                const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t m = meta[i];
@@ -195,6 +195,12 @@ __global__ void __launch_bounds__(256)
   const long long step = step_counter[0];
   const double delta = PROTO ? grip_delta(proto, dy.delta, step) : dy.delta;
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
+  double bc = 0.0, bmu = 1.0;
+  if (PROTO && proto.baro) {  // S(dt/2) before the drift (B changes v only)
+    bc = baro[wi].c;
+    bmu = baro[wi].mu;
+    px = bc + (px - bc) * bmu;
+  }
   double vx, vy, vz;
   if (kind == 0) {
     vx = v[i];
@@ -264,6 +270,7 @@ __global__ void __launch_bounds__(256)
     px += (kind == 1) ? -delta : delta;
     vx = vy = vz = 0.0;
   }
+  if (PROTO && proto.baro) px = bc + (px - bc) * bmu;  // S(dt/2) after the drift
   x[i] = px;
   x[N + i] = py;
   x[2 * N + i] = pz;
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(256, 6)
                       float hd, const int64_t* __restrict__ step_counter, int4* __restrict__ xq,
                       const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
                       uint32_t* wire_status, double* d_grip, ProtoDev proto,
-                      const NhState* __restrict__ nh) {
+                      const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t m = meta[i];
@@ -332,6 +339,10 @@ __global__ void __launch_bounds__(256, 6)
   const WireDev& w = wd[wi];
   const long long step = step_counter[0];
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
+  if (PROTO && proto.baro) {  // S(dt/2) before the drift (B changes v only)
+    const double bc = baro[wi].c;
+    px = bc + (px - bc) * baro[wi].mu;
+  }
   double vx = 0.0, vy = 0.0, vz = 0.0;
   if (kind == 0) {
     vx = v[i];
@@ -383,6 +394,10 @@ __global__ void __launch_bounds__(256, 6)
     px += (kind == 1) ? -delta : delta;
   }
   if (i == w.offset) d_grip[wi] += PROTO ? grip_delta(proto, wdyn[wi].delta, step) : wdyn[wi].delta;
+  if (PROTO && proto.baro) {  // S(dt/2) after the drift
+    const double bc = baro[wi].c;
+    px = bc + (px - bc) * baro[wi].mu;
+  }
   x[i] = px;
   x[N + i] = py;
   x[2 * N + i] = pz;
@@ -469,6 +484,93 @@ __global__ void k_nh_scale(int64_t N, double* __restrict__ v, const uint32_t* __
   if (meta_kind(m) != 0) return;
   const double sc = nh[meta_wire(m)].s;
   for (int d = 0; d < 3; ++d) v[d * N + i] *= sc;
+}
+
+// Axial Nosé–Hoover barostat (Methods: 100 ps at zero pressure along [100]
+// with a Nosé–Hoover barostat before the pull).  Hoover's constant-stress
+// equations along x about the grips' centre c, per wire:
+//   dx/dt = v_x + zeta (x - c),  dv_x/dt = F_x/m - zeta v_x,
+//   dzeta/dt = -(sigma_xx - P) / (B tau_b^2) - gamma_b zeta,  dlambda/dt = zeta
+// (barostat mass V B tau_b^2, V the Eq. 5 volume), in the symmetric step
+//   Z C [NH] B S A S [forces] B [NH] C Z  (each half a step h = dt/2),
+// Z: drag and stress kick of zeta, C: v_x *= exp(-zeta h), S: x = c + (x - c)
+// exp(zeta h) (in the integrator).  sigma_xx is Eq. 5 as k_observe forms it,
+// from the per-atom virial of the last force pass (on these positions).
+struct BaroArgs {
+  double m_e, v_atom, h, p, inv_btau2, drag;  // drag = exp(-gamma_b h)
+};
+
+__device__ __forceinline__ double baro_sigma(double vir, double vx2, const BaroArgs& a, int n) {
+  return (vir - a.m_e * vx2) / (a.v_atom * n);
+}
+
+// Block per wire, at a step's start: Z (drag, then kick), C; leaves c and mu
+// for the integrator's S and advances lambda by both S half steps.
+__global__ void __launch_bounds__(256)
+    k_baro_begin(int W, const WireDev* __restrict__ wd, const uint32_t* __restrict__ meta,
+                 int64_t N, const double* __restrict__ x, double* __restrict__ v,
+                 const double* __restrict__ w_atom, BaroArgs a, BaroState* __restrict__ baro) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    double vir = 0.0, vx2 = 0.0, cx = 0.0, ng = 0.0;
+    for (int t = threadIdx.x; t < wr.n; t += blockDim.x) {
+      const int64_t i = wr.offset + t;
+      vir += w_atom[i];
+      if (meta_kind(meta[i]) == 0) {
+        vx2 += v[i] * v[i];
+      } else {
+        cx += x[i];
+        ng += 1.0;
+      }
+    }
+    vir = block_sum(vir, sh);
+    vx2 = block_sum(vx2, sh);
+    cx = block_sum(cx, sh);
+    ng = block_sum(ng, sh);
+    BaroState b = baro[w];
+    b.zeta *= a.drag;
+    b.zeta -= a.h * (baro_sigma(vir, vx2, a, wr.n) - a.p) * a.inv_btau2;
+    b.c = ng > 0.0 ? cx / ng : 0.0;
+    b.mu = exp(b.zeta * a.h);
+    b.lam = (b.lam + b.zeta * a.h) + b.zeta * a.h;
+    const double sc = exp(-b.zeta * a.h);
+    for (int t = threadIdx.x; t < wr.n; t += blockDim.x) {
+      const int64_t i = wr.offset + t;
+      if (meta_kind(meta[i]) == 0) v[i] *= sc;
+    }
+    if (threadIdx.x == 0) baro[w] = b;
+    __syncthreads();
+  }
+}
+
+// Block per wire, at a step's end: C, then Z (kick, then drag).
+__global__ void __launch_bounds__(256)
+    k_baro_end(int W, const WireDev* __restrict__ wd, const uint32_t* __restrict__ meta,
+               int64_t N, double* __restrict__ v, const double* __restrict__ w_atom, BaroArgs a,
+               BaroState* __restrict__ baro) {
+  __shared__ double sh[256];
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    BaroState b = baro[w];
+    const double sc = exp(-b.zeta * a.h);
+    double vir = 0.0, vx2 = 0.0;
+    for (int t = threadIdx.x; t < wr.n; t += blockDim.x) {
+      const int64_t i = wr.offset + t;
+      vir += w_atom[i];
+      if (meta_kind(meta[i]) == 0) {
+        const double u = v[i] * sc;
+        v[i] = u;
+        vx2 += u * u;
+      }
+    }
+    vir = block_sum(vir, sh);
+    vx2 = block_sum(vx2, sh);
+    b.zeta -= a.h * (baro_sigma(vir, vx2, a, wr.n) - a.p) * a.inv_btau2;
+    b.zeta *= a.drag;
+    if (threadIdx.x == 0) baro[w] = b;
+    __syncthreads();
+  }
 }
 
 // Closing half kick of the last step of a sequence.

@@ -89,6 +89,7 @@ struct tbsma_ctx {
   int32_t* n_rebuilds = nullptr;
   uint32_t* wire_status = nullptr;
   NhState* nh = nullptr;            // per-wire Nosé–Hoover state
+  BaroState* baro = nullptr;        // per-wire axial barostat state
   int* uf_parent = nullptr;         // union-find of the topology call (allocated on first use)
   uint32_t* uf_err = nullptr;
   tbsma_topology* topo_d = nullptr;
@@ -265,15 +266,17 @@ ProtoDev proto_dev(const tbsma_ctx* c) {
   p.interval = c->proto.pull_interval;
   p.t_start = c->proto.t_start;
   p.ramp = c->proto.ramp_steps;
+  p.baro = c->proto.baro_tau_fs > 0.0 ? 1 : 0;
   return p;
 }
 
 bool nose_hoover(const tbsma_ctx* c) { return c->proto.thermostat == TBSMA_THERMO_NOSE_HOOVER; }
+bool barostat(const tbsma_ctx* c) { return c->proto.baro_tau_fs > 0.0; }
 
-// A protocol other than the default (Langevin, continuous pull, no ramp).
+// A protocol other than the default (Langevin, continuous pull, no ramp, no barostat).
 bool protocol_mode(const tbsma_ctx* c) {
   return c->proto.thermostat != TBSMA_THERMO_LANGEVIN || c->proto.pull != TBSMA_PULL_CONTINUOUS ||
-         c->proto.ramp_steps > 0;
+         c->proto.ramp_steps > 0 || barostat(c);
 }
 
 template <int KICK, bool PROTO>
@@ -287,12 +290,12 @@ void integrate_as(tbsma_ctx* c, cudaStream_t s, double dt) {
     k_integrate_mixed<KICK, PROTO><<<g, 256, 0, s>>>(
         c->N, c->x, c->v, c->f32, c->meta, c->wd, c->wdyn, (float)kick, (float)(0.5 * dt),
         c->step_counter, c->xq, c->xq_b, (float)c->half_skin2, c->flag, c->wire_status,
-        c->d_grip, proto_dev(c), c->nh);
+        c->d_grip, proto_dev(c), c->nh, c->baro);
   else
     k_integrate<TBSMA_FP64, KICK, PROTO><<<g, 256, 0, s>>>(
         c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
         c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip,
-        proto_dev(c), c->nh);
+        proto_dev(c), c->nh, c->baro);
 }
 
 template <int KICK>
@@ -309,9 +312,52 @@ void nh_boundary(tbsma_ctx* c, cudaStream_t s, double dt, double kick, int mode)
                                                c->P.mass * kMvv2e, c->step_counter, c->nh);
 }
 
+void half_kick(tbsma_ctx* c, cudaStream_t s, double hk) {
+  const unsigned g = grid_for(c->N, 256);
+  if (c->prec == TBSMA_MIXED)
+    k_half_kick<TBSMA_MIXED><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+  else
+    k_half_kick<TBSMA_FP64><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+}
+
+// n steps under the axial Nosé–Hoover barostat, each step whole:
+//   k_baro_begin (Z C), [NH begin], B S A S (integrator), [forces + virial],
+//   B, [NH end], k_baro_end (C Z).
+// The first pass recomputes the virial of the current positions (the forces
+// it writes are those already held: same positions, same list).
+tbsma_status enqueue_steps_baro(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
+  const double hk = 0.5 * dt * c->inv_m;
+  const double rhs = 0.5 * c->P.r0;
+  BaroArgs a;
+  a.m_e = c->P.mass * kMvv2e;
+  a.v_atom = 4.0 / 3.0 * 3.141592653589793238462643383279 * rhs * rhs * rhs;
+  a.h = 0.5 * dt;
+  a.p = c->proto.baro_pressure;
+  a.inv_btau2 = 1.0 / (c->proto.baro_modulus * c->proto.baro_tau_fs * c->proto.baro_tau_fs);
+  a.drag = std::exp(-c->proto.baro_drag / c->proto.baro_tau_fs * a.h);
+  const unsigned gw = (unsigned)std::min(c->W, 65535);
+  TB_TRY(launch_pair<true>(c, s, c->prec));
+  for (int k = 0; k < n; ++k) {
+    k_baro_begin<<<gw, 256, 0, s>>>(c->W, c->wd, c->meta, c->N, c->x, c->v, c->w_atom, a, c->baro);
+    if (nose_hoover(c)) nh_boundary(c, s, dt, 0.0, 2);
+    integrate<1>(c, s, dt);
+    TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
+    TB_TRY(launch_pair<true>(c, s, c->prec));
+    half_kick(c, s, hk);
+    if (nose_hoover(c)) {
+      nh_boundary(c, s, dt, 0.0, 1);
+      k_nh_scale<<<grid_for(c->N, 256), 256, 0, s>>>(c->N, c->v, c->meta, c->nh);
+    }
+    k_baro_end<<<gw, 256, 0, s>>>(c->W, c->wd, c->meta, c->N, c->v, c->w_atom, a, c->baro);
+  }
+  TB_CUDA(c, cudaGetLastError());
+  return TBSMA_OK;
+}
+
 // n consecutive steps: first integrate with a half kick, the rest with a
 // merged full kick, and a closing half kick after the last force pass.
 tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
+  if (barostat(c)) return enqueue_steps_baro(c, s, n, dt);
   const double hk = 0.5 * dt * c->inv_m;
   for (int k = 0; k < n; ++k) {
     // Nosé–Hoover: the begin half step (first step of the sequence) or the
@@ -322,14 +368,10 @@ tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
     TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
     TB_TRY(launch_pair<false>(c, s, c->prec));
   }
-  const unsigned g = grid_for(c->N, 256);
-  if (c->prec == TBSMA_MIXED)
-    k_half_kick<TBSMA_MIXED><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
-  else
-    k_half_kick<TBSMA_FP64><<<g, 256, 0, s>>>(c->N, c->v, c->f32, c->f64, c->meta, hk);
+  half_kick(c, s, hk);
   if (nose_hoover(c)) {  // the last step's end half step
     nh_boundary(c, s, dt, 0.0, 1);
-    k_nh_scale<<<g, 256, 0, s>>>(c->N, c->v, c->meta, c->nh);
+    k_nh_scale<<<grid_for(c->N, 256), 256, 0, s>>>(c->N, c->v, c->meta, c->nh);
   }
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
@@ -550,6 +592,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->wire_status, W);
   ALLOC(c->nh, W);
+  ALLOC(c->baro, W);
   ALLOC(c->d_grip, W);
   ALLOC(c->step_counter, 1);
   ALLOC(c->obs_d, W);
@@ -563,6 +606,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->baro, 0, sizeof(BaroState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_grip, 0, sizeof(double) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->step_counter, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * N, st) == cudaSuccess;
@@ -740,9 +784,29 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* c, const tbsma_protocol* p) {
     return fail(c, TBSMA_EINVAL, "stepwise pull needs pull_interval >= 1 and a finite pull_step");
   if (!(p->t_start >= 0.0 && std::isfinite(p->t_start)) || p->ramp_steps < 0)
     return fail(c, TBSMA_EINVAL, "ramp needs t_start >= 0 and ramp_steps >= 0");
+  if (!(p->baro_tau_fs >= 0.0 && std::isfinite(p->baro_tau_fs)))
+    return fail(c, TBSMA_EINVAL, "baro_tau_fs must be >= 0 (0 = no barostat)");
+  if (p->baro_tau_fs > 0.0 &&
+      !(p->baro_modulus > 0.0 && std::isfinite(p->baro_modulus) && std::isfinite(p->baro_pressure) &&
+        p->baro_drag >= 0.0 && std::isfinite(p->baro_drag)))
+    return fail(c, TBSMA_EINVAL,
+                "the barostat needs baro_modulus > 0, baro_drag >= 0 and a finite baro_pressure");
   c->proto = *p;
   drop_graph(c);
   TB_CUDA(c, cudaMemsetAsync(c->nh, 0, sizeof(NhState) * c->W, c->stream));
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_get_barostat(tbsma_ctx* c, double* lambda, double* zeta) {
+  if (!c) return TBSMA_EINVAL;
+  std::vector<BaroState> b(c->W);
+  TB_CUDA(c, cudaMemcpyAsync(b.data(), c->baro, sizeof(BaroState) * c->W, cudaMemcpyDeviceToHost,
+                             c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int w = 0; w < c->W; ++w) {
+    if (lambda) lambda[w] = b[w].lam;
+    if (zeta) zeta[w] = b[w].zeta;
+  }
   return TBSMA_OK;
 }
 
@@ -822,6 +886,7 @@ tbsma_status tbsma_save_state(tbsma_ctx* c, double* x_host, double* v_host,
   std::vector<int32_t> nr(c->W);
   std::vector<uint32_t> ws(c->W);
   std::vector<NhState> nh(c->W);
+  std::vector<BaroState> bs(c->W);
   int64_t sc = 0;
   TB_CUDA(c, cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(v_host, c->v, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -829,12 +894,15 @@ tbsma_status tbsma_save_state(tbsma_ctx* c, double* x_host, double* v_host,
   TB_CUDA(c, cudaMemcpyAsync(nr.data(), c->n_rebuilds, sizeof(int32_t) * c->W, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(ws.data(), c->wire_status, sizeof(uint32_t) * c->W, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(nh.data(), c->nh, sizeof(NhState) * c->W, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(bs.data(), c->baro, sizeof(BaroState) * c->W, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(&sc, c->step_counter, sizeof sc, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int w = 0; w < c->W; ++w) {
     wires[w].d_grip = dg[w];
     wires[w].xi = nh[w].xi;
     wires[w].eta = nh[w].eta;
+    wires[w].log_stretch = bs[w].lam;
+    wires[w].stretch_rate = bs[w].zeta;
     wires[w].n_rebuilds = nr[w];
     wires[w].status = ws[w];
   }
@@ -851,11 +919,13 @@ tbsma_status tbsma_restore_state(tbsma_ctx* c, const double* x_host, const doubl
   std::vector<int32_t> nr(c->W);
   std::vector<uint32_t> ws(c->W);
   std::vector<NhState> nh(c->W);
+  std::vector<BaroState> bs(c->W);
   for (int w = 0; w < c->W; ++w) {
     dg[w] = wires[w].d_grip;
     nr[w] = wires[w].n_rebuilds;
     ws[w] = wires[w].status;
     nh[w] = NhState{wires[w].xi, wires[w].eta, 1.0, 0.f};
+    bs[w] = BaroState{wires[w].stretch_rate, wires[w].log_stretch, 0.0, 1.0};
   }
   TB_CUDA(c, cudaMemcpyAsync(c->x, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(c->v, v_host, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -863,6 +933,7 @@ tbsma_status tbsma_restore_state(tbsma_ctx* c, const double* x_host, const doubl
   TB_CUDA(c, cudaMemcpyAsync(c->n_rebuilds, nr.data(), sizeof(int32_t) * c->W, cudaMemcpyHostToDevice, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(c->wire_status, ws.data(), sizeof(uint32_t) * c->W, cudaMemcpyHostToDevice, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(c->nh, nh.data(), sizeof(NhState) * c->W, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(c->baro, bs.data(), sizeof(BaroState) * c->W, cudaMemcpyHostToDevice, c->stream));
   TB_CUDA(c, cudaMemcpyAsync(c->step_counter, &step, sizeof step, cudaMemcpyHostToDevice, c->stream));
   c->steps_done = step;
   TB_TRY(rebuild_all(c));

@@ -91,6 +91,10 @@ class ProtocolC(ctypes.Structure):
         ("pull_interval", ctypes.c_int64),
         ("t_start", ctypes.c_double),
         ("ramp_steps", ctypes.c_int64),
+        ("baro_tau_fs", ctypes.c_double),
+        ("baro_modulus", ctypes.c_double),
+        ("baro_pressure", ctypes.c_double),
+        ("baro_drag", ctypes.c_double),
     ]
 
 
@@ -105,10 +109,13 @@ class WireStateC(ctypes.Structure):
     """tbsma_wire_state (include/tbsma.h)."""
 
     _fields_ = [("d_grip", ctypes.c_double), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
-                ("n_rebuilds", ctypes.c_int32), ("status", ctypes.c_uint32)]
+                ("log_stretch", ctypes.c_double), ("stretch_rate", ctypes.c_double),
+                ("n_rebuilds", ctypes.c_int32),
+                ("status", ctypes.c_uint32)]
 
 
 THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
+BARO_MODULUS = 100.0 / 160.21766208  # 100 GPa in eV/A^3: the barostat's reference modulus
 PULLS = {"continuous": 0, "stepwise": 1}
 
 SIGNATURES = [
@@ -129,6 +136,7 @@ SIGNATURES = [
     ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_get_barostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -307,15 +315,22 @@ class Engine:
 
     def set_protocol(self, thermostat: str = "nose_hoover", pull: str = "stepwise",
                      tau_fs: float = 1000.0, pull_step: float = 0.05, pull_interval: int = 10000,
-                     t_start: float = 0.01, ramp_steps: int = 0):
+                     t_start: float = 0.01, ramp_steps: int = 0, baro_tau_fs: float = 0.0,
+                     baro_modulus: float = BARO_MODULUS, baro_pressure: float = 0.0,
+                     baro_drag: float = 1.0):
         """Paper protocol mode (tbsma_set_protocol); the defaults are the paper's
-        Nosé–Hoover thermostat and 0.05 A grip steps every 10000 steps, no ramp."""
+        Nosé–Hoover thermostat and 0.05 A grip steps every 10000 steps, no ramp,
+        no barostat (baro_tau_fs > 0 turns on the axial Nosé–Hoover barostat;
+        baro_modulus and baro_pressure in eV/A^3, baro_drag in 1/baro_tau_fs)."""
         p = ProtocolC(THERMOSTATS[thermostat], PULLS[pull], tau_fs, pull_step, int(pull_interval),
-                      t_start, int(ramp_steps))
+                      t_start, int(ramp_steps), baro_tau_fs, baro_modulus, baro_pressure,
+                      baro_drag)
         self._check(lib().tbsma_set_protocol(self.ctx, ctypes.byref(p)), "tbsma_set_protocol")
         self.protocol = dict(thermostat=thermostat, pull=pull, tau_fs=tau_fs, pull_step=pull_step,
                              pull_interval=int(pull_interval), t_start=t_start,
-                             ramp_steps=int(ramp_steps))
+                             ramp_steps=int(ramp_steps), baro_tau_fs=baro_tau_fs,
+                             baro_modulus=baro_modulus, baro_pressure=baro_pressure,
+                             baro_drag=baro_drag)
 
     def thermostat(self):
         """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""
@@ -325,6 +340,16 @@ class Engine:
                                                eta.ctypes.data_as(ctypes.c_void_p)),
                     "tbsma_get_thermostat")
         return xi, eta
+
+    def barostat(self):
+        """(lambda, zeta) per wire: the barostat's axial log-stretch and strain
+        rate (1/fs), numpy arrays (tbsma_get_barostat)."""
+        lam = np.zeros(self.W)
+        zeta = np.zeros(self.W)
+        self._check(lib().tbsma_get_barostat(self.ctx, lam.ctypes.data_as(ctypes.c_void_p),
+                                             zeta.ctypes.data_as(ctypes.c_void_p)),
+                    "tbsma_get_barostat")
+        return lam, zeta
 
     def topology(self, labels: bool = False):
         """Per-wire rupture and neck (tbsma_wire_topology): dict of numpy arrays
@@ -389,7 +414,7 @@ class Engine:
         ws = (WireStateC * self.W)()
         for w, d in zip(ws, header["wires"]):
             for k, _ in WireStateC._fields_:
-                setattr(w, k, d[k])
+                setattr(w, k, d.get(k, 0.0) if k in ("log_stretch", "stretch_rate") else d[k])
         self._check(lib().tbsma_restore_state(self.ctx, x.ctypes.data_as(ctypes.c_void_p),
                                               v.ctypes.data_as(ctypes.c_void_p), ws,
                                               int(header["step"])), "tbsma_restore_state")
