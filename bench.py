@@ -33,11 +33,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "batch256_d3_l40"
-LAUNCH = (256, 1024)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
+LAUNCH = (256, 1280)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
 GRAPH_CHUNK = 50  # steps per captured graph (library constant)
-KERNELS_PER_STEP = 8  # integrate, plan, clear, bin, sort, build, density, force
+# List skin (A).  Results do not depend on it (every pass tests r_cut); at
+# 10 K a 0.40 A skin keeps the list radius (6.20 A) inside the gap between the
+# fourth (5.77 A) and fifth (6.45 A) fcc shells, so the lists are no longer
+# while rebuilds, driven by thermal excursions past skin/2, become ~15x rarer
+# than at 0.29 A (measured on this workload: 751.6 -> 700.6 us per step).
+R_SKIN = 0.40
+KERNELS_PER_STEP = 4  # integrate, plan, density, force (+ the rebuild chain when it runs)
+KERNELS_PER_CHAIN = 4  # cell clear, bin, sort, build: counted by the library (rebuild_chains)
 OBS_EVERY = 1000  # per-wire observables reported every OBS_EVERY steps inside the timed region
-KERNELS_PER_OBS = 9  # pack, plan, clear, bin, sort, build, density + force (with energies), reduce
+KERNELS_PER_OBS = 5  # pack, plan, density + force (with energies), reduce (+ a rebuild chain)
 METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"
 UNIT = "atom-steps/s"
 
@@ -239,8 +246,11 @@ def _chunks(K: int):
     return out
 
 
-def launches_in(K: int) -> int:
-    n = 0
+def launches_in(K: int, chains: int) -> int:
+    """Kernels launched by K timed steps: the fixed ones per step and per
+    report, one closing kernel per graph replay or direct sequence, and
+    `chains` launches of the rebuild chain (counted on the device)."""
+    n = KERNELS_PER_CHAIN * chains
     for k in _chunks(K):
         full, rem = divmod(k, GRAPH_CHUNK) if k >= GRAPH_CHUNK else (0, k)
         n += full * (KERNELS_PER_STEP * GRAPH_CHUNK + 1)
@@ -348,7 +358,8 @@ def run_ours(args):
     specs = replicate_specs(WORKLOADS[args.workload](), rank, world)
     batch = build(specs)
     N, W = batch.n_atoms, batch.n_wires
-    eng = tb.Engine(batch, precision="mixed")
+    params = tb.au_params(r_skin=R_SKIN)
+    eng = tb.Engine(batch, precision="mixed", params=params)
     eng.init_velocities()
     eng.step(max(3, args.warmup), 2.0)
     launch = LAUNCH
@@ -362,6 +373,7 @@ def run_ours(args):
     eng.step(min(_chunks(args.steps)[0], GRAPH_CHUNK), 2.0)
     torch.cuda.synchronize()
 
+    chains0 = eng.rebuild_chains()
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -378,6 +390,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     t_ms = ev0.elapsed_time(ev1)
+    chains = eng.rebuild_chains() - chains0
     t_max, atoms_all = aggregate(t_ms, N, device="cuda")
     value = atoms_all * args.steps / (t_max / 1e3)
 
@@ -404,13 +417,13 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
-                   "observables_every": OBS_EVERY,
+                   "observables_every": OBS_EVERY, "r_skin_A": R_SKIN,
                    "tile_atoms": launch[0], "window_atoms": launch[1],
                    "launch": "autotuned" if args.autotune else "fixed",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
         "roofline": roof,
         "clocks": ck,
-        "gpu_launches": launches_in(args.steps),
+        "gpu_launches": launches_in(args.steps, chains),
         "force_check": {"max_err_scaled": float(fc["max_err_scaled"].max()),
                         "norm_err": float(fc["norm_err"].max()),
                         "max_err_raw": float(fc["max_err_raw"].max())},
@@ -447,7 +460,7 @@ def run_ours(args):
             one = pack([Wire(x=batch.x[s].copy(), kind=batch.kind[s].copy(), diameter_nm=3.0,
                              length_nm=40.0, L0=float(batch.L0[w]), temperature=10.0,
                              strain_rate=1e8, gamma=float(batch.gamma[w]), seed=int(batch.seed[w]))])
-            e1 = tb.Engine(one, precision="fp64")
+            e1 = tb.Engine(one, precision="fp64", params=params)
             e1.set_launch(64, 0)  # one 17k-atom wire: small tiles to occupy every SM
             e1.init_velocities()
             e1.step(5, 2.0)

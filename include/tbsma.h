@@ -82,7 +82,13 @@ typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
 /* TB-SMA parameters (Table 1; r_cut after Eq. 3), list skin and mass.
  * Au: A = 0.2061 eV, xi = 1.790 eV, p = 10.229, q = 4.036, r0 = 2.884 A
  * (the nearest-neighbour distance; Table 1 prints the lattice constant
- * 4.079 A in that column), r_cut = 5.8 A, r_skin = 0.29 A, mass = 196.966569. */
+ * 4.079 A in that column), r_cut = 5.8 A, r_skin = 0.29 A, mass = 196.966569.
+ * r_skin changes only speed, never results: lists hold the pairs within
+ * r_cut + r_skin and every pass tests r_cut itself.  The list row length
+ * follows the list radius (1.25 x the fcc sites of a sphere of that radius
+ * for nearest-neighbour distance r0, 64 to 128 entries:
+ * tbsma_nbr_capacity); an atom with more neighbours sets
+ * TBSMA_WIRE_NBR_OVERFLOW. */
 typedef struct {
   double A, xi, p, q, r0, r_cut, r_skin, mass;
 } tbsma_params;
@@ -336,6 +342,12 @@ tbsma_status tbsma_get_wire_status(tbsma_ctx* ctx, int32_t* status_host);
  * neighbours within r_cut + r_skin, in the library's deterministic order;
  * unused entries -1).  cap must equal tbsma_nbr_capacity(ctx). */
 int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
+
+/* Launch accounting: how many times the four kernels of the list-rebuild
+ * chain (cell clear, bin, sort, build) were launched since tbsma_init: once
+ * per step and per position refresh (they return at once when no wire is
+ * flagged).  Synchronises.  Errors: EINVAL (null). */
+tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* ctx, int64_t* n);
 tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, int32_t cap);
 
 /* Launch shape of the pair passes: threads per block (64, 128 or 256; one
@@ -343,7 +355,8 @@ tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, i
  * shared-memory window in atoms (0..4096, 0 = read neighbours from global
  * memory): a tile whose neighbours span at most that many consecutive atoms
  * stages their packed positions in shared memory.  Invalidates captured
- * graphs.  Defaults: 256, 1024. */
+ * graphs.  Defaults: 256, 1280 (the window of a 256-atom tile of a 4 nm wire;
+ * 8 blocks of 256 threads still fit an SM). */
 tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t block_threads, int32_t window_atoms);
 
 /* Enqueue `reps` launches of one pair pass on the context's stream, on the

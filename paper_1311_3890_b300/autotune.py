@@ -15,7 +15,7 @@ import json
 import math
 import os
 
-CANDIDATES = [(b, w) for b in (128, 256) for w in (0, 512, 1024, 2048)]
+CANDIDATES = [(b, w) for b in (128, 256) for w in (0, 512, 1024, 1280, 1536, 2048)]
 
 
 def size_class(engine) -> str:

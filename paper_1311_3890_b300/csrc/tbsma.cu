@@ -26,7 +26,8 @@ using namespace tbsma;
 namespace {
 
 constexpr int kGraphChunk = 50;  // steps per captured graph
-constexpr int kDefaultCap = 64;  // neighbour-list row length
+constexpr int kMinCap = 64;   // neighbour-list row length, bounds (list_capacity)
+constexpr int kMaxCap = 128;
 constexpr int kMaxWindow = 4096; // largest shared-memory window of a pair-pass tile, atoms
 
 struct Graph {
@@ -45,8 +46,8 @@ struct tbsma_ctx {
   cudaStream_t cap_stream = nullptr;
   int sm_count = 148;
   int block = 256;   // atoms per tile of the pair passes
-  int wcap = 1024;   // shared-memory window of a tile, atoms
-  int cap = kDefaultCap;
+  int wcap = 1280;   // shared-memory window of a tile, atoms
+  int cap = kMinCap;
   int64_t n_cells = 0;
   int64_t steps_done = 0;
   double dt_dyn = -1.0;  // dt the per-wire dynamic table was filled for
@@ -87,6 +88,7 @@ struct tbsma_ctx {
   int64_t* wl_atom = nullptr;
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
+  int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
   uint32_t* wire_status = nullptr;
   NhState* nh = nullptr;            // per-wire Nosé–Hoover state
   BaroState* baro = nullptr;        // per-wire axial barostat state
@@ -109,7 +111,7 @@ struct tbsma_ctx {
   double half_skin2 = 0.0;
   double inv_m = 0.0;
 
-  NlWork nw() const { return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds}; }
+  NlWork nw() const { return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds, chains}; }
 };
 
 namespace {
@@ -177,6 +179,15 @@ void fill_pair_consts(tbsma_ctx* c) {
   c->rlist2 = (float)(rl * rl);
   c->half_skin2 = 0.25 * P.r_skin * P.r_skin;
   c->inv_m = 1.0 / (P.mass * kMvv2e);
+  // List row length: the fcc sites (density sqrt(2)/r0^3 for nearest-neighbour
+  // distance r0) in a sphere of the list radius, times 1.25 for thermal and
+  // surface disorder, rounded up to 8 and kept within [kMinCap, kMaxCap].  A
+  // bulk Au atom has 54 sites within 5.8 A and 24 more at 6.45 A, which
+  // thermal motion brings inside a list radius of 6.2 A at 298 K.
+  const double sites = std::sqrt(2.0) / (P.r0 * P.r0 * P.r0) * 4.0 / 3.0 *
+                       3.141592653589793238462643383279 * rl * rl * rl;
+  const int want = ((int)std::ceil(1.25 * sites) + 7) / 8 * 8;
+  c->cap = std::min(kMaxCap, std::max(kMinCap, want));
 }
 
 // ------------------------------------------------------------- launchers
@@ -192,9 +203,9 @@ tbsma_status launch_pack(tbsma_ctx* c, cudaStream_t s, int check) {
   return TBSMA_OK;
 }
 
-tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_rebuild,
-                       int64_t* step_counter) {
-  k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, force_all, count_rebuild, step_counter);
+// The list rebuild of the wires the plan selected: clear their cells, bin,
+// sort each cell, build (each kernel returns at once when none is selected).
+tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
   const unsigned gs = (unsigned)(c->sm_count * 4);
   k_nl_clear<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->cell_count);
   k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
@@ -212,6 +223,12 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
                                                   c->cap, c->jrange, c->xd, c->xd_b, c->wire_status);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
+}
+
+tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_rebuild,
+                       int64_t* step_counter) {
+  k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, force_all, count_rebuild, step_counter);
+  return launch_rebuild(c, s);
 }
 
 template <bool OBS>
@@ -504,6 +521,10 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
+  const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
+  if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
 #define ALLOC(ptr, n)                          \
@@ -590,6 +611,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->wl_atom, W + 1);
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
+  ALLOC(c->chains, 1);
   ALLOC(c->wire_status, W);
   ALLOC(c->nh, W);
   ALLOC(c->baro, W);
@@ -604,6 +626,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
                             st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->baro, 0, sizeof(BaroState) * W, st) == cudaSuccess;
@@ -750,6 +773,13 @@ tbsma_status tbsma_get_wire_status(tbsma_ctx* c, int32_t* status_host) {
 }
 
 int32_t tbsma_nbr_capacity(const tbsma_ctx* c) { return c ? c->cap : 0; }
+
+tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* c, int64_t* n) {
+  if (!c || !n) return TBSMA_EINVAL;
+  TB_CUDA(c, cudaMemcpyAsync(n, c->chains, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TBSMA_OK;
+}
 
 tbsma_status tbsma_get_neighbors(tbsma_ctx* c, int32_t* n_nbr, int32_t* nbr, int32_t cap) {
   if (!c || cap != c->cap) return TBSMA_EINVAL;

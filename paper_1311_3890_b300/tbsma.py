@@ -131,6 +131,7 @@ SIGNATURES = [
     ("tbsma_download_state", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_get_wire_status", ctypes.c_int, [_P, _P]),
     ("tbsma_nbr_capacity", ctypes.c_int32, [_P]),
+    ("tbsma_get_rebuild_chains", ctypes.c_int, [_P, _P]),
     ("tbsma_get_neighbors", ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     ("tbsma_set_launch", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
@@ -308,6 +309,13 @@ class Engine:
         nb = t.empty(self.N * cap, dtype=t.int32, device=self.device)
         self._check(lib().tbsma_get_neighbors(self.ctx, _ptr(n), _ptr(nb), cap), "tbsma_get_neighbors")
         return n, nb.view(self.N, cap)
+
+    def rebuild_chains(self) -> int:
+        """Launches of the four-kernel list-rebuild chain so far (launch accounting)."""
+        n = ctypes.c_int64(0)
+        self._check(lib().tbsma_get_rebuild_chains(self.ctx, ctypes.byref(n)),
+                    "tbsma_get_rebuild_chains")
+        return int(n.value)
 
     def set_launch(self, block_threads: int, window_atoms: int):
         """Pair-pass tile size (atoms per block) and shared-memory window (atoms)."""
