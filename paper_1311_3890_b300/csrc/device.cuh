@@ -49,6 +49,7 @@ struct WireDev {
   int32_t nc[3];     // cells per direction
   int32_t pad;
   int64_t cell_base;  // index of the wire's first cell
+  int64_t slot_base;  // first slot of the wire's tiles (a multiple of kSlotTile; see k_slot_order)
   uint64_t seed;
   double L0, strain_rate, temperature, gamma;
 };

@@ -28,7 +28,13 @@ struct NlWork {
   int32_t* n_flagged;   // [1]
   int32_t* n_rebuilds;  // [W]
   int64_t* chains;      // [1] launches of the rebuild chain (clear, bin, sort, build)
+  int64_t* last_build;  // [W] step of the wire's last list build
+  uint8_t* banked;      // [W] the wire's rows in bank-group order (k_nl_build) at this build
 };
+
+// Shortest life (steps) of a wire's previous list for which its rebuilt
+// rows are put in bank-group order (see k_nl_build).
+constexpr int64_t kBankedInterval = 128;
 
 // Binary search: largest k < nf with pre[k] <= idx.
 __device__ __forceinline__ int wl_find(const int64_t* pre, int nf, int64_t idx) {
@@ -90,7 +96,8 @@ __device__ __forceinline__ void block_scan3(int64_t& a, int64_t& b, int64_t& c, 
 // which return at once.)
 __global__ void __launch_bounds__(1024)
     k_nl_plan(int W, NlWork nw, const WireDev* __restrict__ wd, int force_all, int count_rebuild,
-              int64_t* step_counter) {
+              int64_t* step_counter, const int64_t* __restrict__ steps_now) {
+  const int64_t steps = steps_now[0];
   __shared__ int64_t tot[3];
   const int t = threadIdx.x;
   const int chunk = (W + 1023) / 1024;
@@ -115,6 +122,10 @@ __global__ void __launch_bounds__(1024)
       ++k;
       nw.flag[w] = 0;
       if (count_rebuild) nw.n_rebuilds[w] += 1;
+      // bank-group row order when the previous list lived long enough to
+      // repay it (always on a full rebuild: init, checkpoint save / restore)
+      nw.banked[w] = force_all || steps - nw.last_build[w] >= kBankedInterval;
+      nw.last_build[w] = steps;
     }
   }
   if (t == 0) {
@@ -201,6 +212,9 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
   return (float)(dx * dx + dy * dy + dz * dz);
 }
 
+// Byte g of a packed vector of eight 8-bit counters.
+__device__ __forceinline__ int byte_of(uint64_t v, int g) { return (int)((v >> (8 * g)) & 0xffu); }
+
 // Four threads per atom of a flagged wire (a quad of consecutive lanes);
 // thread q of the quad visits the cells c = 0..26 with c % 4 == q, c the
 // linear index of the offset (ox, oy, oz) in {-1, 0, 1}^3, each cell's
@@ -216,6 +230,27 @@ __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
 // the atom's neighbour indices (the pair passes stage the union of a tile's
 // ranges in shared memory) and copies the atom's packed position to the
 // build snapshot used by the displacement check.
+//
+// Row order: the pair passes gather neighbour positions from a shared-memory
+// window whose base is a multiple of 8 rows, so row j lies in bank group
+// j mod 8 of the 128-bit gathers, and the 8 lanes of a quarter-warp that
+// load at the same list position conflict when their rows share a group.
+// Each row is therefore emitted so that at position k the atom in lane l
+// (its slot mod 8) takes an entry of group (k + l) mod 8 when it has one
+// left, else one of the group with the most entries left (nearest to the
+// preferred one on ties).  Groups are counted from the wire's first atom
+// ((j - offset) mod 8) and a wire's slots start on a tile boundary, so the
+// order is a function of the wire alone; within a tile the groups differ
+// from the bank groups by one rotation, which keeps the lanes apart.  In a
+// CPU replay of thermalised D3-wire lists this brings 8 random rows per
+// quarter-warp load (2.6 deep in one bank group) down to ~1.6.  All four
+// threads of the quad run the same schedule on packed per-group counters;
+// each writes the positions that fall on its own entries.  The schedule
+// costs ~1.3 ns per rebuilt atom and the ordered rows save ~10 ps per atom
+// and step in the passes, so a wire takes it only when its previous list
+// lived at least kBankedInterval steps (k_nl_plan decides from the wire's
+// own counters, so the order stays a function of its trajectory); a wire
+// that rebuilds more often (298 K) keeps the rows in quad order.
 constexpr int kBuildQuad = 4;
 template <typename PosT>
 __global__ void __launch_bounds__(256)
@@ -275,13 +310,12 @@ __global__ void __launch_bounds__(256)
         visit(j3, q3);
       }
     }
-    // quad: exclusive prefix of the counts, total, index range
-    int pre = 0, count = 0;
+    // quad: the four counts, total, index range
+    int c4[kBuildQuad], count = 0;
 #pragma unroll
     for (int r = 0; r < kBuildQuad; ++r) {
-      const int cr = __shfl_sync(quad_mask, cnt_mine, r, kBuildQuad);
-      pre += r < q ? cr : 0;
-      count += cr;
+      c4[r] = __shfl_sync(quad_mask, cnt_mine, r, kBuildQuad);
+      count += c4[r];
     }
 #pragma unroll
     for (int o = 1; o < kBuildQuad; o <<= 1) {
@@ -289,8 +323,53 @@ __global__ void __launch_bounds__(256)
       jmax = max(jmax, __shfl_xor_sync(quad_mask, jmax, o, kBuildQuad));
     }
     const int64_t t = slot_of[i];
-    for (int e = 0; e < cnt_mine && e < cap && pre + e < cap; ++e)
-      nbr[nbr_slot(t, pre + e, cap)] = sbuf[e * blockDim.x + threadIdx.x];
+    {
+      // the row keeps its first n entries in quad order; this thread holds
+      // entries [pre, pre + mine) of them, in its own buffer
+      const int n = min(count, cap);
+      int pre = 0;
+#pragma unroll
+      for (int r = 0; r < kBuildQuad; ++r) pre += r < q ? c4[r] : 0;
+      const int mine = max(0, min(min(cnt_mine, cap), n - pre));
+      const bool banked = nw.banked[wi] != 0;
+      if (!banked)
+        for (int e = 0; e < mine; ++e) nbr[nbr_slot(t, pre + e, cap)] = sbuf[e * blockDim.x + threadIdx.x];
+      const int il = (int)(i - w.offset);
+      auto group = [&](int e) { return (il + sbuf[e * blockDim.x + threadIdx.x]) & 7; };
+      uint64_t L = 0, P = 0, T = 0, R = 0, C = 0;
+      for (int e = 0; banked && e < mine; ++e) L += 1ull << (8 * group(e));
+#pragma unroll
+      for (int r = 0; r < kBuildQuad; ++r) {
+        const uint64_t Lr = __shfl_sync(quad_mask, L, r, kBuildQuad);
+        P += r < q ? Lr : 0ull;
+        T += Lr;
+      }
+      const int lane = (int)(t & 7);
+      for (int k = 0; banked && k < n; ++k) {
+        const int want = (k + lane) & 7;
+        int g = want;
+        if (byte_of(T, g) == 0) {
+          int best = -1;
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+            const int h = (want + d) & 7;
+            if (byte_of(T, h) > best) {
+              best = byte_of(T, h);
+              g = h;
+            }
+          }
+        }
+        const int r = byte_of(R, g), p = byte_of(P, g);
+        R += 1ull << (8 * g);
+        T -= 1ull << (8 * g);
+        if (r >= p && r < p + byte_of(L, g)) {  // the position falls on one of my entries
+          int cur = min(byte_of(C, g), mine - 1);  // mine >= 1 here; stays inside the buffer
+          while (cur + 1 < mine && group(cur) != g) ++cur;
+          nbr[nbr_slot(t, k, cap)] = sbuf[cur * blockDim.x + threadIdx.x];
+          C = (C & ~(0xffull << (8 * g))) | ((uint64_t)(cur + 1) << (8 * g));
+        }
+      }
+    }
     if (far || (q == 0 && count > cap)) atomicOr(&wire_status[wi], kWireNbrOverflow);
     if (q == 0) {
       n_nbr[t] = min(count, cap);
@@ -314,35 +393,48 @@ __global__ void k_list_rows(int64_t N, int cap, const int16_t* __restrict__ nbr,
   if (rows) rows[u] = k < n_nbr[t] ? (int32_t)(i + nbr[nbr_slot(t, k, cap)]) : -1;
 }
 
-__global__ void k_iota(int64_t N, int32_t* a, int32_t* b) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) a[i] = b[i] = (int32_t)i;
+// Block per wire: the wire's atoms in its own slot range in atom order,
+// the padding slots that complete its last tile empty (perm = -1).
+__global__ void k_slot_init(int W, const WireDev* __restrict__ wd, int64_t NS,
+                            int32_t* __restrict__ perm, int32_t* __restrict__ slot_of) {
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const WireDev& wr = wd[w];
+    const int64_t end = w + 1 < W ? wd[w + 1].slot_base : NS;
+    for (int64_t s = wr.slot_base + threadIdx.x; s < end; s += blockDim.x) {
+      const int64_t a = s - wr.slot_base;
+      perm[s] = a < wr.n ? (int32_t)(wr.offset + a) : -1;
+      if (a < wr.n) slot_of[wr.offset + a] = (int32_t)s;
+    }
+  }
 }
 
-// Slot order of the pair passes.  Within each tile of kSlotTile consecutive
-// atoms the atoms are ranked by list length (longest first, ties by index),
-// so that the 32 threads of a warp walk lists of similar length (the core
-// and surface atoms of a wire alternate along its [100] order).  A tile keeps
-// its set of atoms, so its neighbour-index window is unchanged.  Only the
-// speed depends on this order, never a result: every atom's sums run over
-// its own list in list order.  n_nbr is read in the current slot order.
+// Slot order of the pair passes.  Every wire's slots form whole tiles of
+// kSlotTile slots (its count rounded up; the padding slots hold no atom),
+// so a tile never mixes wires and an atom's slot does not depend on the rest
+// of the batch.  Within each tile the atoms are ranked by list length
+// (longest first, ties by slot), so that the 32 threads of a warp walk lists
+// of similar length (the core and surface atoms of a wire alternate along its
+// [100] order); the padding slots stay last.  A tile keeps its set of atoms,
+// so its neighbour-index window is unchanged.  The speed depends on this
+// order, and the list rows are ordered for the lane (slot mod 8) an atom gets
+// (k_nl_build); the lists are rebuilt after this kernel.
 constexpr int kSlotTile = 256;
 __global__ void __launch_bounds__(kSlotTile)
-    k_slot_order(int64_t N, const int32_t* __restrict__ n_nbr, int32_t* __restrict__ perm,
+    k_slot_order(int64_t NS, const int32_t* __restrict__ n_nbr, int32_t* __restrict__ perm,
                  int32_t* __restrict__ slot_of) {
   __shared__ int sn[kSlotTile];
   const int64_t base = (int64_t)blockIdx.x * kSlotTile;
   const int a = threadIdx.x;
-  const int m = (int)(N - base < kSlotTile ? N - base : kSlotTile);
-  const int64_t i = base + a;
-  sn[a] = a < m ? n_nbr[slot_of[i]] : -1;
+  const int64_t s = base + a;
+  const int32_t i = s < NS ? perm[s] : -1;
+  sn[a] = i >= 0 ? n_nbr[s] : -1;
   __syncthreads();
-  if (a < m) {
+  if (s < NS) {
     const int na = sn[a];
     int rank = 0;
-    for (int b = 0; b < m; ++b) rank += (sn[b] > na) || (sn[b] == na && b < a);
-    perm[base + rank] = (int32_t)i;
-    slot_of[i] = (int32_t)(base + rank);
+    for (int b = 0; b < kSlotTile; ++b) rank += (sn[b] > na) || (sn[b] == na && b < a);
+    perm[base + rank] = i;
+    if (i >= 0) slot_of[i] = (int32_t)(base + rank);
   }
 }
 

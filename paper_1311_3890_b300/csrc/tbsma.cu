@@ -42,6 +42,7 @@ struct tbsma_ctx {
   int prec = TBSMA_MIXED;
   int W = 0;
   int64_t N = 0;
+  int64_t NS = 0;  // slots of the pair passes: every wire's atoms padded to whole tiles
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int sm_count = 148;
@@ -80,7 +81,7 @@ struct tbsma_ctx {
   int32_t* cell_count = nullptr;
   int32_t* cell_atoms = nullptr;
   int32_t* cell_of = nullptr;
-  int32_t* perm = nullptr;     // slot -> atom of the pair passes
+  int32_t* perm = nullptr;     // slot -> atom of the pair passes (-1: a tile's padding slot)
   int32_t* slot_of = nullptr;  // atom -> slot
   int32_t* flag = nullptr;
   int32_t* wl_wire = nullptr;
@@ -89,6 +90,8 @@ struct tbsma_ctx {
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
+  int64_t* last_build = nullptr;  // per wire: step of its last list build
+  uint8_t* banked = nullptr;      // per wire: rows in bank-group order at its last build
   uint32_t* wire_status = nullptr;
   NhState* nh = nullptr;            // per-wire Nosé–Hoover state
   BaroState* baro = nullptr;        // per-wire axial barostat state
@@ -111,7 +114,9 @@ struct tbsma_ctx {
   double half_skin2 = 0.0;
   double inv_m = 0.0;
 
-  NlWork nw() const { return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds, chains}; }
+  NlWork nw() const {
+    return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds, chains, last_build, banked};
+  }
 };
 
 namespace {
@@ -227,31 +232,33 @@ tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
 
 tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_rebuild,
                        int64_t* step_counter) {
-  k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, force_all, count_rebuild, step_counter);
+  k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, force_all, count_rebuild, step_counter,
+                               c->step_counter);
   return launch_rebuild(c, s);
 }
 
 template <bool OBS>
 void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
-  const unsigned g = grid_for(c->N, c->block);
+  const unsigned g = grid_for(c->NS, c->block);
   const size_t smem = (size_t)c->wcap * sizeof(int4);
   if (which & 1)
-    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
+    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
                                                  c->wcap, c->pc, c->e_band);
   if (which & 2)
-    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->N, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
-                                               c->wcap, c->pc, c->f32, c->e_band, c->e_atom,
+    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
+                                               c->wcap, c->pc, c->f32, c->f32 + c->N, c->f32 + 2 * c->N,
+                                               c->e_band, c->e_atom,
                                                c->w_atom, c->s_atom);
 }
 
 template <bool OBS, bool DECIDE32>
 void pair_f64(tbsma_ctx* c, cudaStream_t s, int which = 3) {
-  const unsigned g = grid_for(c->N, c->block);
+  const unsigned g = grid_for(c->NS, c->block);
   if (which & 1)
-    k_density_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+    k_density_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
                                                          c->perm, c->cap, c->pc, c->inv64, c->e_band);
   if (which & 2)
-    k_force_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->xd, c->xq, c->nbr, c->n_nbr,
+    k_force_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
                                                        c->perm, c->cap, c->pc, c->inv64, c->f64, c->e_band,
                                                        c->e_atom, c->w_atom, c->s_atom);
 }
@@ -549,7 +556,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   // rounding in the cell coordinate never separates two atoms by two cells)
   const double rl = std::sqrt((double)c->rlist2) * 1.0001;
   c->wires_h.resize(W);
-  int64_t cells = 0;
+  int64_t cells = 0, slots = 0;
   for (int w = 0; w < W; ++w) {
     WireDev& d = c->wires_h[w];
     std::memset(&d, 0, sizeof d);
@@ -580,8 +587,12 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
     }
     d.cell_base = cells;
     cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
+    d.slot_base = slots;
+    slots += (d.n + kSlotTile - 1) / kSlotTile * (int64_t)kSlotTile;
   }
   c->n_cells = cells;
+  c->NS = slots;
+  const int64_t NS = slots;
 
   ALLOC(c->wd, W);
   ALLOC(c->wdyn, W);
@@ -597,12 +608,12 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->e_atom, N);
   ALLOC(c->w_atom, N);
   ALLOC(c->s_atom, N);
-  ALLOC(c->nbr, (size_t)((N + 31) / 32) * 32 * c->cap);
-  ALLOC(c->jrange, N);
+  ALLOC(c->nbr, (size_t)((NS + 31) / 32) * 32 * c->cap);
+  ALLOC(c->jrange, NS);
   ALLOC(c->cell_of, N);
-  ALLOC(c->perm, N);
+  ALLOC(c->perm, NS);
   ALLOC(c->slot_of, N);
-  ALLOC(c->n_nbr, N);
+  ALLOC(c->n_nbr, NS);
   ALLOC(c->cell_count, cells);
   ALLOC(c->cell_atoms, (size_t)cells * kCellCap);
   ALLOC(c->flag, W);
@@ -612,6 +623,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);
+  ALLOC(c->last_build, W);
+  ALLOC(c->banked, W);
   ALLOC(c->wire_status, W);
   ALLOC(c->nh, W);
   ALLOC(c->baro, W);
@@ -627,21 +640,23 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->baro, 0, sizeof(BaroState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_grip, 0, sizeof(double) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->step_counter, 0, sizeof(int64_t), st) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * N, st) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(c->jrange, 0, sizeof(int2) * N, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->n_nbr, 0, sizeof(int32_t) * NS, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->jrange, 0, sizeof(int2) * NS, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->f32, 0, sizeof(float) * 3 * N, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->f64, 0, sizeof(double) * 3 * N, st) == cudaSuccess;
   if (!ok) return bail(TBSMA_ECUDA);
   k_meta<<<std::min(W, 65535), 256, 0, st>>>(W, c->wd, kind, c->meta);
   // build once in atom order, rank each tile's atoms by list length, build again
-  k_iota<<<grid_for(N, 256), 256, 0, st>>>(N, c->perm, c->slot_of);
+  k_slot_init<<<std::min(W, 65535), 256, 0, st>>>(W, c->wd, NS, c->perm, c->slot_of);
   if ((s = refresh(c, 1)) != TBSMA_OK) return bail(s);
-  k_slot_order<<<grid_for(N, kSlotTile), kSlotTile, 0, st>>>(N, c->n_nbr, c->perm, c->slot_of);
+  k_slot_order<<<grid_for(NS, kSlotTile), kSlotTile, 0, st>>>(NS, c->n_nbr, c->perm, c->slot_of);
   if ((s = refresh(c, 1)) != TBSMA_OK) return bail(s);
   if ((s = launch_pair<false>(c, st, c->prec)) != TBSMA_OK) return bail(s);
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(TBSMA_ECUDA);
@@ -866,11 +881,11 @@ tbsma_status tbsma_wire_topology(tbsma_ctx* c, tbsma_topology* out, int32_t* lab
   TB_CUDA(c, cudaMemsetAsync(c->uf_err, 0, sizeof(uint32_t), c->stream));
   k_uf_init<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent);
   if (c->prec == TBSMA_MIXED)
-    k_uf_link<TBSMA_MIXED><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
+    k_uf_link<TBSMA_MIXED><<<grid_for(c->NS, 256), 256, 0, c->stream>>>(c->NS, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
                                                       c->cap, c->pc, c->uf_parent, c->wait_limit,
                                                       c->uf_err);
   else
-    k_uf_link<TBSMA_FP64><<<g, 256, 0, c->stream>>>(c->N, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
+    k_uf_link<TBSMA_FP64><<<grid_for(c->NS, 256), 256, 0, c->stream>>>(c->NS, c->xq, c->xd, c->nbr, c->n_nbr, c->perm,
                                                      c->cap, c->pc, c->uf_parent, c->wait_limit,
                                                      c->uf_err);
   k_uf_compress<<<g, 256, 0, c->stream>>>(c->N, c->uf_parent, c->wait_limit, c->uf_err);

@@ -54,16 +54,17 @@ __global__ void k_uf_init(int64_t N, int* parent) {
   if (i < N) parent[i] = (int)i;
 }
 
-// One thread per slot: link the atom with every list neighbour j > i that
+// One thread per slot (NS slots): link the atom with every list neighbour j > i that
 // interacts under the context's rule (the pair passes' cutoff decision).
 template <int PREC>
-__global__ void k_uf_link(int64_t N, const int4* __restrict__ xq, const double4_32a* __restrict__ xd,
+__global__ void k_uf_link(int64_t NS, const int4* __restrict__ xq, const double4_32a* __restrict__ xd,
                           const int16_t* __restrict__ nbr, const int32_t* __restrict__ n_nbr,
                           const int32_t* __restrict__ perm, int cap, PairConsts pc, int* parent,
                           int limit, uint32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= N) return;
+  if (t >= NS) return;
   const int i = perm[t];
+  if (i < 0) return;  // a tile's padding slot
   const int n = n_nbr[t];
   for (int k = 0; k < n; ++k) {
     const int j = i + nbr[nbr_slot(t, k, cap)];
