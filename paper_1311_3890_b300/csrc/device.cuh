@@ -111,9 +111,17 @@ __host__ __device__ inline double grip_delta(const ProtoDev& p, double delta_con
 
 // Constants of the pair kernels (Eq. 1-2 rewritten with exp2).
 struct PairConsts {
-  // FP32 path: e^{-2q s} = 2^(-kg (r - r0)), e^{-(p-2q) s} = 2^(-kh (r - r0))
-  float rc2f, r0f, kgf, khf, xi2f, Af, fpf, fgf;  // fpf = 2 p A / r0, fgf = 2 q xi^2 / r0
-                                                  // rc2f in fixed-point units^2 (2^52 / A^2)
+  // FP32 path, r in fixed-point units (2^-26 A), s = r / r0 - 1.
+  // Density pass: e^{-2q s} = gC 2^(gA r + gB) with gA = -(2q/r0) log2(e) 2^-26
+  // and gB = -gA r0 2^26 (the two terms cancel exactly at r = r0; one FMA),
+  // gC = 2^(exact - rounded gB) putting back gB's FP32 rounding (in xi2g).
+  // Force pass: e^{-2q s} = 2^(-kgf t), e^{-(p-2q) s} = 2^(-khf t) with
+  // t = r 2^-26 - r0 (an FMA with a single constant: an FMA may read one).
+  float rc2f, r0f, kgf, khf;  // rc2f in fixed-point units^2 (2^52 / A^2)
+  float xi2g;                 // xi^2 gC: rho = xi2g sum 2^(gA r + gB)
+  float Af, fpf;              // fpf = 2 p A / r0
+  float fgf;                  // 2 q xi^2 / r0: the density pass stores a_i = fgf / (2 sqrt(rho_i))
+  float gA, gB;
   // FP64 path
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };

@@ -163,13 +163,17 @@ void fill_pair_consts(tbsma_ctx* c) {
   const double log2e = 1.4426950408889634073599246810019;
   PairConsts& k = c->pc;
   k.rc2f = (float)(P.r_cut * P.r_cut) * 4503599627370496.0f;  // x 2^52: fixed-point units^2
+  const double unit = 1.0 / 67108864.0;  // 2^-26 A
+  k.gA = (float)(-2.0 * P.q / P.r0 * log2e * unit);
+  const double gB = -(double)k.gA * P.r0 / unit;
+  k.gB = (float)gB;
+  k.xi2g = (float)(P.xi * P.xi * std::exp2(gB - (double)k.gB));
+  k.fgf = (float)(2.0 * P.q * P.xi * P.xi / P.r0);
   k.r0f = (float)P.r0;
   k.kgf = (float)(2.0 * P.q / P.r0 * log2e);
   k.khf = (float)((P.p - 2.0 * P.q) / P.r0 * log2e);
-  k.xi2f = (float)(P.xi * P.xi);
-  k.Af = (float)P.A;
   k.fpf = (float)(2.0 * P.p * P.A / P.r0);
-  k.fgf = (float)(2.0 * P.q * P.xi * P.xi / P.r0);
+  k.Af = (float)P.A;
   k.rc2 = P.r_cut * P.r_cut;
   k.r0 = P.r0;
   k.A = P.A;
