@@ -262,9 +262,10 @@ def launches_in(K: int, chains: int) -> int:
 
 # Algorithmic work of one force-pass launch (per atom, n_c list entries inside
 # r_cut, n_s skin entries):
-#   FP32 instructions  22 per in-cutoff entry (3 int->float, r^2 3, test 1,
-#                      r 1 + Newton 3, s 1, two exponent arguments 2, bracket 4,
-#                      f/r 1, F 3) and 7 per skin entry (3 + 3 + 1)
+#   FP32 instructions  21 per in-cutoff entry (3 int->float, r^2 3, test 1,
+#                      r 1 + Newton 3, s 1, two exponent arguments 2, bracket 3:
+#                      a_i + a_j, fp h - that, times g; f/r 1, F 3) and 7 per
+#                      skin entry (3 + 3 + 1)
 #   MUFU               3 per in-cutoff entry (rsqrt, two ex2)
 #   HBM bytes          2 n_list (int16 list) + 4 (count) + 8 (index range)
 #                      + 16 (own packed position) + 12 (F)
@@ -273,13 +274,13 @@ def launches_in(K: int, chains: int) -> int:
 # median SM clock sampled during the timed region; HBM from MEASURED_PEAKS.
 # The roofline time is the slower of the ALU time (FP32 and MUFU pipes run
 # concurrently: the larger of the two) and the HBM time.
-FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 22, 7, 3
+FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 21, 7, 3
 # DRAM bytes (read + write) per atom of one force-pass launch, from an ncu
 # capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms,
-# r_skin 0.40 A: 71.782 MB read + 1.569 MB written), scaled by the atom count
+# r_skin 0.40 A: 71.781 MB read + 1.324 MB written), scaled by the atom count
 # (the traffic is per atom); profiles/pair_integrate_batch32_d3_l40.md.  Set
 # to None when the kernel changes until it is captured again.
-FORCE_TRAFFIC_B_PER_ATOM = 131.5
+FORCE_TRAFFIC_B_PER_ATOM = 131.0
 
 
 def _list_census(eng, r_cut=5.8, chunk=1 << 20):
