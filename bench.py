@@ -62,6 +62,8 @@ def parse():
                    help="pick the pair passes' launch shape with the autotuner first")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the cpu baseline, fp64 comparison and e2e legs")
+    p.add_argument("--table2", action="store_true",
+                   help="context: steps/s of the paper's Table 2 wires, each alone, 10 and 298 K")
     return p.parse_args()
 
 
@@ -488,8 +490,57 @@ def run_ours(args):
     return 0
 
 
+# The paper's Table 2: timesteps per second of one unstretched D3.1 nm wire
+# per GPU (GTX 680, HOOMD-Blue + TB-SMA in FP32) at 10 K and 298 K.
+TABLE2_ATOMS = [8823, 17673, 26523, 35373, 44223, 53073, 61923, 70773, 79623, 88473, 97323, 106173]
+TABLE2_10K = [2536, 1723, 1311, 1045, 881, 758, 655, 584, 514, 470, 427, 396]
+TABLE2_298K = [2286, 1507, 1141, 897, 717, 616, 550, 484, 409, 354, 330, 300]
+
+
+def run_table2(args):
+    """Each Table 2 wire alone in its own mixed-precision context (as the
+    paper ran one system per GPU), 64-atom tiles to spread a small wire over
+    the SMs, the library default list skin: steps/s over the timed steps
+    after the warm-up, at 10 K and at 298 K.  Context only, one JSON line."""
+    import torch
+
+    from inputs.configs import WireSpec, build
+    import paper_1311_3890_b300 as tb
+
+    torch.cuda.set_device(0)
+    steps, warm = min(args.steps, 1000), min(args.warmup, 500)
+    rows = []
+    for k in range(1, 13):
+        row = {"k": k, "length_nm": round(20.4 * k, 1)}
+        for T in (10.0, 298.0):
+            batch = build([WireSpec(3.1, 20.4 * k, T, 0.0, k)])
+            eng = tb.Engine(batch, precision="mixed")
+            eng.set_launch(64, 1280)
+            eng.init_velocities()
+            eng.step(warm, 2.0)
+            eng.step(min(50, steps), 2.0)  # capture the graph outside the timed region
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            eng.step(steps, 2.0)
+            b.record()
+            torch.cuda.synchronize()
+            row["atoms"] = int(batch.n_atoms)
+            row[f"steps_per_s_{int(T)}K"] = steps / (a.elapsed_time(b) / 1e3)
+            eng.close()
+        row["paper_atoms"] = TABLE2_ATOMS[k - 1]
+        row["paper_steps_per_s_10K"] = TABLE2_10K[k - 1]
+        row["paper_steps_per_s_298K"] = TABLE2_298K[k - 1]
+        rows.append(row)
+    print(json.dumps({"context": "paper Table 2 systems, each wire alone per context (mixed "
+                      "precision, B300) against the paper's GTX 680 FP32 steps/s",
+                      "steps": steps, "warmup": warm, "rows": rows}))
+
+
 def main():
     args = parse()
+    if args.table2:
+        return run_table2(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

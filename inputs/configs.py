@@ -91,6 +91,13 @@ def _sweep2048() -> list[WireSpec]:
     return out
 
 
+def _paper_table2() -> list[WireSpec]:
+    """The paper's benchmark systems (Table 2, Results "TB-SMA benchmarks"):
+    unstretched D 3.1 nm wires of length 20.4 k nm, k = 1..12 (8.9k-106k
+    atoms here against the paper's 8.8k-106k), 10 K, no pull."""
+    return [WireSpec(3.1, 20.4 * k, 10.0, 0.0, k) for k in range(1, 13)]
+
+
 def _tiny_batch() -> list[WireSpec]:
     """Three small wires of uneven size and temperature (parity tests)."""
     return [
@@ -113,6 +120,8 @@ WORKLOADS = {
     "ragged512": _ragged512,
     # 2048 trajectories over D {2,3,4} x 24 lengths 5..120 nm x T {10,298}
     "sweep2048": _sweep2048,
+    # the paper's Table 2 systems: D3.1 x L20.4k nm, k = 1..12, 10 K, no pull
+    "paper_table2": _paper_table2,
     "tiny_batch": _tiny_batch,
 }
 
