@@ -279,10 +279,11 @@ def launches_in(K: int, chains: int) -> int:
 FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 21, 7, 3
 # DRAM bytes (read + write) per atom of one force-pass launch, from an ncu
 # capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms,
-# r_skin 0.40 A: 71.781 MB read + 1.324 MB written), scaled by the atom count
-# (the traffic is per atom); profiles/pair_integrate_batch32_d3_l40.md.  Set
-# to None when the kernel changes until it is captured again.
-FORCE_TRAFFIC_B_PER_ATOM = 131.0
+# r_skin 0.40 A, first launch: 72.322 MB read + 1.031 MB written), scaled by
+# the atom count (the traffic is per atom);
+# profiles/pair_integrate_batch32_d3_l40.md.  Set to None when the kernel
+# changes until it is captured again.
+FORCE_TRAFFIC_B_PER_ATOM = 131.5
 
 
 def _list_census(eng, r_cut=5.8, chunk=1 << 20):

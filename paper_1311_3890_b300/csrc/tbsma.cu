@@ -612,7 +612,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->e_atom, N);
   ALLOC(c->w_atom, N);
   ALLOC(c->s_atom, N);
-  ALLOC(c->nbr, (size_t)((NS + 31) / 32) * 32 * c->cap);
+  // + one group row: the force pass prefetches the group after a row's last one
+  ALLOC(c->nbr, (size_t)((NS + 31) / 32) * 32 * c->cap + 32 * 4);
   ALLOC(c->jrange, NS);
   ALLOC(c->cell_of, N);
   ALLOC(c->perm, NS);
