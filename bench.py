@@ -183,6 +183,13 @@ def _oracle_run(batch, first_step: int, steps: int, state=None):
     return state
 
 
+def _workload_atoms(specs) -> int:
+    """Atoms of the whole workload (geometry only, cached per wire shape)."""
+    from inputs.configs import _geometry
+
+    return int(sum(_geometry(float(sp.diameter_nm), float(sp.length_nm)).n for sp in specs))
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host on a bounded sample of the workload."""
     rank, world, _ = _env_rank()
@@ -228,8 +235,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "wires": len(specs), "dt_fs": 2.0,
-                   "temperature_K": specs[0].temperature, "strain_rate_per_s": specs[0].strain_rate},
+        "config": {"workload": args.workload, "wires": len(specs),
+                   "atoms_per_gpu": _workload_atoms(specs), "dt_fs": 2.0,
+                   "temperature_K": specs[0].temperature, "strain_rate_per_s": specs[0].strain_rate,
+                   "precision": "fp64 (oracle)", "observables_every": None,
+                   "l2": "host", "parallelism": f"{len(sample_specs)} host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(sample_specs),
                          "kind": "oracle", "sample": f"{sample}; {N} atoms"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
