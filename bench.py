@@ -316,22 +316,19 @@ def _list_census(eng, r_cut=5.8, chunk=1 << 20):
     return n_in / N, (n_all - n_in) / N
 
 
-def force_roofline(eng, ms, clocks):
-    import torch
-
-    n_c, n_s = _list_census(eng)
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    sms = props.multi_processor_count
-    mhz = clocks.get("sm_mhz") or 2032.0
+def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs):
+    """The force pass's roofline from its algorithmic work (per atom: n_c
+    in-cutoff and n_s skin list entries) and its measured time per launch
+    `ms`, for `sms` SMs at `mhz` and an HBM peak of `hbm_gbs`: the bound is
+    the slower of the FP32 and MUFU pipes (which run concurrently) and the
+    bytes at HBM bandwidth; `achieved` is the bound's work over the time."""
     f = mhz * 1e6
-    N = eng.N
     fp32_ops = N * (FP32_PER_IN * n_c + FP32_PER_SKIN * n_s)
     mufu_ops = N * MUFU_PER_IN * n_c
     bytes_ = N * (2.0 * (n_c + n_s) + 4 + 8 + 16 + 12)
-    hbm, kind = _peaks()
     t_fp32 = fp32_ops / (128 * sms * f)
     t_mufu = mufu_ops / (32 * sms * f)
-    t_hbm = bytes_ / (hbm * 1e9)
+    t_hbm = bytes_ / (hbm_gbs * 1e9)
     t = ms * 1e-3
     if max(t_fp32, t_mufu) >= t_hbm:
         if t_fp32 >= t_mufu:
@@ -341,18 +338,32 @@ def force_roofline(eng, ms, clocks):
             bound = {"bound": "alu", "achieved": mufu_ops / t / 1e12,
                      "peak": 32 * sms * f / 1e12, "unit": "T MUFU-op/s"}
     else:
-        bound = {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s"}
+        bound = {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm_gbs, "unit": "GB/s"}
     bound["frac"] = bound["achieved"] / bound["peak"]
     bound.update({
-        "kernel": "k_force_f32",
-        "traffic": None if FORCE_TRAFFIC_B_PER_ATOM is None else FORCE_TRAFFIC_B_PER_ATOM * N,
-        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per atom, small-case "
-                          "capture scaled by atoms",
         "ms_per_launch": ms,
         "roofline_ms": 1e3 * max(t_fp32, t_mufu, t_hbm),
         "t_fp32_ms": 1e3 * t_fp32, "t_mufu_ms": 1e3 * t_mufu, "t_hbm_ms": 1e3 * t_hbm,
-        "hbm_frac": bytes_ / t / 1e9 / hbm, "hbm_peak_kind": kind,
+        "hbm_frac": bytes_ / t / 1e9 / hbm_gbs,
         "entries_in_cutoff": n_c, "entries_skin": n_s, "sm_mhz": mhz,
+    })
+    return bound
+
+
+def force_roofline(eng, ms, clocks):
+    import torch
+
+    n_c, n_s = _list_census(eng)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    hbm, kind = _peaks()
+    bound = roofline_of(eng.N, n_c, n_s, ms, props.multi_processor_count,
+                        clocks.get("sm_mhz") or 2032.0, hbm)
+    bound.update({
+        "kernel": "k_force_f32",
+        "traffic": None if FORCE_TRAFFIC_B_PER_ATOM is None else FORCE_TRAFFIC_B_PER_ATOM * eng.N,
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per atom, small-case "
+                          "capture scaled by atoms",
+        "hbm_peak_kind": kind,
     })
     return bound
 
