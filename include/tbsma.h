@@ -351,7 +351,7 @@ tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* ctx, int64_t* n);
 tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, int32_t cap);
 
 /* Launch shape of the pair passes: threads per block (64, 128 or 256; one
- * atom per thread, a block is a tile of consecutive atoms) and the tile's
+ * atom per thread, a block is a tile of consecutive atoms of one wire) and the tile's
  * shared-memory window in atoms (0..4096, 0 = read neighbours from global
  * memory): a tile whose neighbours span at most that many consecutive atoms
  * stages their packed positions in shared memory.  Invalidates captured

@@ -126,10 +126,10 @@ struct PairConsts {
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };
 
-// Neighbour lists hold int16 offsets j - i, warp-tiled and grouped by four:
-// entries 4g..4g+3 of atom i form one 8-byte group, and the groups g of the 32
-// atoms of a tile are contiguous (256 bytes), so a warp reads four entries of
-// each of its atoms with one coalesced load.  cap is a multiple of 4.
+// Neighbour lists hold int16 offsets j - i, by slot, warp-tiled and grouped
+// by four: entries 4g..4g+3 of slot t form one 8-byte group, and the groups g
+// of 32 consecutive slots are contiguous (256 bytes), so a warp reads four
+// entries of each of its atoms with one coalesced load.  cap is a multiple of 4.
 constexpr int kMaxOffset = 32767;  // |j - i| an entry can hold
 
 __host__ __device__ __forceinline__ int64_t nbr_group(int64_t i, int g, int cap) {
