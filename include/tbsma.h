@@ -193,7 +193,11 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
  *               moves by -/+ pull_step when (s + 1) is a multiple of
  *               pull_interval, else not at all.
  *   ramp        the thermostat's target at step s is t_start + (T_w -
- *               t_start) min(1, s / ramp_steps); ramp_steps = 0: T_w.
+ *               t_start) clamp((s - ramp_start) / ramp_steps, 0, 1): t_start
+ *               until step ramp_start (counted from tbsma_init), then the
+ *               linear ramp; ramp_steps = 0: T_w throughout.  The paper's
+ *               equilibration (100 ps of barostat at 0.01 K, 400 ps of ramp,
+ *               400 ps at T_w) is ramp_start 50000, ramp_steps 200000.
  *   barostat    (baro_tau_fs > 0; Methods: 100 ps at zero pressure along
  *               [100] with a Nosé–Hoover barostat before the pull) Hoover's
  *               constant-stress equations along x about the mean x, c, of
@@ -219,10 +223,10 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
  * 0.01 K, ramp_steps 200000 (400 ps).  Resets every wire's thermostat
  * state (xi = eta = 0; lambda is kept) and drops captured graphs.  Errors:
  * EINVAL (unknown thermostat or pull, tau_fs <= 0 under Nosé–Hoover,
- * pull_interval < 1 or non-finite pull_step under stepwise pull, t_start < 0
- * or ramp_steps < 0, baro_tau_fs < 0 or non-finite, and with the barostat on
- * baro_modulus <= 0, baro_drag < 0, or any of them or baro_pressure
- * non-finite). */
+ * pull_interval < 1 or non-finite pull_step under stepwise pull, t_start < 0,
+ * ramp_steps < 0 or ramp_start < 0, baro_tau_fs < 0 or non-finite, and with
+ * the barostat on baro_modulus <= 0, baro_drag < 0, or any of them or
+ * baro_pressure non-finite). */
 typedef enum { TBSMA_THERMO_LANGEVIN = 0, TBSMA_THERMO_NOSE_HOOVER = 1 } tbsma_thermostat;
 typedef enum { TBSMA_PULL_CONTINUOUS = 0, TBSMA_PULL_STEPWISE = 1 } tbsma_pull;
 typedef struct {
@@ -237,6 +241,7 @@ typedef struct {
   double baro_modulus;   /* its reference modulus, eV/A^3 */
   double baro_pressure;  /* its target sigma_xx (tension positive), eV/A^3 */
   double baro_drag;      /* its drag gamma_b in units of 1/baro_tau_fs */
+  int64_t ramp_start;    /* first step of the ramp (target t_start before it) */
 } tbsma_protocol;
 
 tbsma_status tbsma_set_protocol(tbsma_ctx* ctx, const tbsma_protocol* protocol);

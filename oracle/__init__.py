@@ -78,6 +78,7 @@ class _Protocol(ctypes.Structure):
         ("baro_modulus", ctypes.c_double),
         ("baro_pressure", ctypes.c_double),
         ("baro_drag", ctypes.c_double),
+        ("ramp_start", ctypes.c_int64),
     ]
 
 
@@ -359,13 +360,14 @@ class Protocol:
     baro_modulus: float = 100.0 / 160.21766208  # 100 GPa in eV/A^3
     baro_pressure: float = 0.0  # target sigma_xx, eV/A^3
     baro_drag: float = 1.0  # barostat drag in units of 1/baro_tau
+    ramp_start: int = 0  # first step of the ramp (t_start before it)
 
     def _c(self):
         th = {"langevin": 0, "nose_hoover": 1}[self.thermostat]
         pl = {"continuous": 0, "stepwise": 1}[self.pull]
         return _Protocol(th, pl, self.tau, self.pull_step, int(self.pull_interval), self.t_start,
                          int(self.ramp_steps), self.baro_tau, self.baro_modulus, self.baro_pressure,
-                         self.baro_drag)
+                         self.baro_drag, int(self.ramp_start))
 
 
 def target_temperature(proto: Protocol, T_w: float, step: int) -> float:

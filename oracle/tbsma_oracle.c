@@ -464,7 +464,9 @@ void or_md_batch(const or_pot* P, const or_md* M, int n_wires, const or_wire* W,
  * thermostat = 0 keeps the Langevin B A O A B step of or_md_steps.
  *
  * Target temperature at step index s (0-based): T(s) = t_start +
- * (T_w - t_start) min(1, s / ramp_steps), or T_w when ramp_steps = 0.  The
+ * (T_w - t_start) clamp((s - ramp_start) / ramp_steps, 0, 1), or T_w when
+ * ramp_steps = 0 (the paper holds 0.01 K during its barostat phase, then
+ * ramps: ramp_start is the first step of the ramp).  The
  * NH half step at the start of step s and the one at its end use T(s).
  *
  * Pull (pull = 1, stepwise): in step s each grip moves by -/+ pull_step
@@ -509,11 +511,13 @@ typedef struct {
   double baro_modulus;   /* its reference modulus B, eV/A^3 */
   double baro_pressure;  /* its target sigma_xx, eV/A^3 */
   double baro_drag;      /* its drag gamma_b in units of 1/tau_b */
+  int64_t ramp_start;    /* first step of the ramp */
 } or_protocol;
 
 double or_target_temperature(const or_protocol* R, double T_w, int64_t s) {
   if (R->ramp_steps <= 0) return T_w;
-  double f = (double)s / (double)R->ramp_steps;
+  if (s < R->ramp_start) return R->t_start;
+  double f = (double)(s - R->ramp_start) / (double)R->ramp_steps;
   if (f > 1.0) f = 1.0;
   return R->t_start + (T_w - R->t_start) * f;
 }

@@ -157,3 +157,50 @@ def pull_to_rupture(eng, report_every: int, max_steps: int, dt: float = 2.0,
         ef, fn = failure(strain[:, w], conn[:, w], neck[:, w])
         out.append(WireResult(sy, ey, ef, fn, strain[:, w], sigma[:, w], conn[:, w], neck[:, w]))
     return out
+
+
+@dataclasses.dataclass
+class PaperRun:
+    log_stretch: np.ndarray  # barostat lambda per wire after the equilibration
+    results: list  # WireResult per wire, strains relative to the equilibrated length
+
+
+def paper_protocol(eng, barostat_steps: int = 50000, ramp_steps: int = 200000,
+                   hold_steps: int = 200000, pull_step: float = 0.05,
+                   pull_interval: int = 10000, report_every: int = 1000,
+                   max_pull_steps: int = 2_000_000, dt: float = 2.0, tau_fs: float = 1000.0,
+                   baro_tau_fs: float = 1000.0, t_start: float = 0.01,
+                   window_fs: float = 500.0) -> PaperRun:
+    """The paper's protocol (Methods, "Simulation details") on every wire of
+    an Engine, from its current state: (1) barostat_steps (100 ps) at zero
+    axial pressure with the Nosé–Hoover barostat and a Nosé–Hoover target of
+    t_start (0.01 K); (2) ramp_steps (400 ps) ramping the target from t_start
+    to each wire's temperature; (3) hold_steps (400 ps) at that temperature;
+    the grips do not move in (1)-(3).  Then the elongation: each grip moves
+    by pull_step (0.05 A) every pull_interval steps (20 ps) until every wire
+    has failed (pull_to_rupture).  The strains of the results are measured
+    against the equilibrated length L0 e^lambda (the barostat's log-stretch),
+    so a failure strain is the paper's elongation over the relaxed wire.
+    Every phase sets the protocol anew, which restarts the thermostat
+    variable; the steps keep counting from tbsma_init."""
+    s0 = int(np.asarray(eng.observables()["step"])[0])
+    common = dict(thermostat="nose_hoover", tau_fs=tau_fs, t_start=t_start,
+                  ramp_steps=max(1, int(ramp_steps)), ramp_start=s0 + int(barostat_steps))
+    hold = dict(pull="stepwise", pull_step=0.0, pull_interval=1)
+    eng.set_protocol(**common, **hold, baro_tau_fs=baro_tau_fs)
+    if barostat_steps > 0:
+        eng.step(int(barostat_steps), dt)
+    lam = np.asarray(eng.barostat()[0], dtype=np.float64).copy()
+    eng.set_protocol(**common, **hold)
+    if ramp_steps + hold_steps > 0:
+        eng.step(int(ramp_steps + hold_steps), dt)
+    eng.set_protocol(**common, pull="stepwise", pull_step=pull_step,
+                     pull_interval=int(pull_interval))
+    res = pull_to_rupture(eng, report_every=report_every, max_steps=max_pull_steps, dt=dt,
+                          window_fs=window_fs)
+    for r, lw in zip(res, lam):
+        f = math.exp(-lw)  # strain = 2 d_grip / L0  ->  2 d_grip / (L0 e^lambda)
+        r.strain = r.strain * f
+        r.eps_y *= f
+        r.eps_f *= f
+    return PaperRun(lam, res)

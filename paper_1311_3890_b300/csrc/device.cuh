@@ -73,6 +73,7 @@ struct ProtoDev {
   long long interval;  // stepwise: steps per event
   double t_start;      // ramp start temperature, K
   long long ramp;      // ramp length in steps, 0 = none
+  long long ramp_start;  // first step of the ramp (t_start before it)
   int baro;            // 1: the axial barostat scales x about BaroState::c
 };
 
@@ -92,11 +93,13 @@ struct NhState {
   float sm1f;
 };
 
-// Target temperature of step s (0-based): linear ramp from t_start to the
-// wire's temperature over `ramp` steps, then constant.
+// Target temperature of step s (0-based): t_start until step ramp_start,
+// then a linear ramp to the wire's temperature over `ramp` steps, then
+// constant (no ramp: the wire's temperature throughout).
 __host__ __device__ inline double target_temperature(const ProtoDev& p, double T_w, long long s) {
   if (p.ramp <= 0) return T_w;
-  double f = (double)s / (double)p.ramp;
+  double f = (double)(s - p.ramp_start) / (double)p.ramp;
+  if (f < 0.0) f = 0.0;
   if (f > 1.0) f = 1.0;
   return p.t_start + (T_w - p.t_start) * f;
 }

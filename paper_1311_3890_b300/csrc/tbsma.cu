@@ -294,6 +294,7 @@ ProtoDev proto_dev(const tbsma_ctx* c) {
   p.interval = c->proto.pull_interval;
   p.t_start = c->proto.t_start;
   p.ramp = c->proto.ramp_steps;
+  p.ramp_start = c->proto.ramp_start;
   p.baro = c->proto.baro_tau_fs > 0.0 ? 1 : 0;
   return p;
 }
@@ -832,8 +833,8 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* c, const tbsma_protocol* p) {
     return fail(c, TBSMA_EINVAL, "tau_fs must be positive");
   if (p->pull == TBSMA_PULL_STEPWISE && (p->pull_interval < 1 || !std::isfinite(p->pull_step)))
     return fail(c, TBSMA_EINVAL, "stepwise pull needs pull_interval >= 1 and a finite pull_step");
-  if (!(p->t_start >= 0.0 && std::isfinite(p->t_start)) || p->ramp_steps < 0)
-    return fail(c, TBSMA_EINVAL, "ramp needs t_start >= 0 and ramp_steps >= 0");
+  if (!(p->t_start >= 0.0 && std::isfinite(p->t_start)) || p->ramp_steps < 0 || p->ramp_start < 0)
+    return fail(c, TBSMA_EINVAL, "ramp needs t_start >= 0, ramp_steps >= 0 and ramp_start >= 0");
   if (!(p->baro_tau_fs >= 0.0 && std::isfinite(p->baro_tau_fs)))
     return fail(c, TBSMA_EINVAL, "baro_tau_fs must be >= 0 (0 = no barostat)");
   if (p->baro_tau_fs > 0.0 &&

@@ -95,6 +95,7 @@ class ProtocolC(ctypes.Structure):
         ("baro_modulus", ctypes.c_double),
         ("baro_pressure", ctypes.c_double),
         ("baro_drag", ctypes.c_double),
+        ("ramp_start", ctypes.c_int64),
     ]
 
 
@@ -325,20 +326,21 @@ class Engine:
                      tau_fs: float = 1000.0, pull_step: float = 0.05, pull_interval: int = 10000,
                      t_start: float = 0.01, ramp_steps: int = 0, baro_tau_fs: float = 0.0,
                      baro_modulus: float = BARO_MODULUS, baro_pressure: float = 0.0,
-                     baro_drag: float = 1.0):
+                     baro_drag: float = 1.0, ramp_start: int = 0):
         """Paper protocol mode (tbsma_set_protocol); the defaults are the paper's
         Nosé–Hoover thermostat and 0.05 A grip steps every 10000 steps, no ramp,
         no barostat (baro_tau_fs > 0 turns on the axial Nosé–Hoover barostat;
-        baro_modulus and baro_pressure in eV/A^3, baro_drag in 1/baro_tau_fs)."""
+        baro_modulus and baro_pressure in eV/A^3, baro_drag in 1/baro_tau_fs);
+        the ramp, when on, starts at step ramp_start (t_start before it)."""
         p = ProtocolC(THERMOSTATS[thermostat], PULLS[pull], tau_fs, pull_step, int(pull_interval),
                       t_start, int(ramp_steps), baro_tau_fs, baro_modulus, baro_pressure,
-                      baro_drag)
+                      baro_drag, int(ramp_start))
         self._check(lib().tbsma_set_protocol(self.ctx, ctypes.byref(p)), "tbsma_set_protocol")
         self.protocol = dict(thermostat=thermostat, pull=pull, tau_fs=tau_fs, pull_step=pull_step,
                              pull_interval=int(pull_interval), t_start=t_start,
                              ramp_steps=int(ramp_steps), baro_tau_fs=baro_tau_fs,
                              baro_modulus=baro_modulus, baro_pressure=baro_pressure,
-                             baro_drag=baro_drag)
+                             baro_drag=baro_drag, ramp_start=int(ramp_start))
 
     def thermostat(self):
         """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""

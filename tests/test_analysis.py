@@ -4,6 +4,7 @@ on synthetic report series with known answers."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_1311_3890_b300.analysis import failure, trailing_mean, yield_point
 
@@ -67,3 +68,65 @@ def test_observed_critical_length_and_failure_map():
     h = failure_map(L, eps_f, eps_y, [0, 30, 50, 70, 90], [0.0, 0.1, 1.0])
     np.testing.assert_array_equal(h, [[1, 9], [0, 10], [10, 0], [10, 0]])
     assert np.isnan(observed_critical_length(L[:20], eps_f[:20], eps_y[:20]))
+
+
+class _FakeEngine:
+    """Records the calls paper_protocol makes; grips move by the pull of the
+    protocol in force, the wire fails at a fixed grip displacement."""
+
+    def __init__(self, lam, L0=40.0, fail_at=6.0):
+        import types
+
+        self.W = 1
+        self.batch = types.SimpleNamespace(L0=np.array([L0]))
+        self.calls, self.step_count, self.d_grip = [], 100, 0.0
+        self.proto, self.lam, self.fail_at = {}, lam, fail_at
+
+    def observables(self):
+        L0 = self.batch.L0[0]
+        return {"step": np.array([self.step_count]), "strain": np.array([2 * self.d_grip / L0]),
+                "sigma_xx": np.array([0.01 * self.d_grip])}
+
+    def set_protocol(self, **kw):
+        self.calls.append(("set_protocol", kw))
+        self.proto = kw
+
+    def step(self, n, dt):
+        self.calls.append(("step", n))
+        if self.proto.get("pull") == "stepwise" and self.proto["pull_step"] > 0:
+            events = (self.step_count + n) // self.proto["pull_interval"] - \
+                self.step_count // self.proto["pull_interval"]
+            self.d_grip += events * self.proto["pull_step"]
+        self.step_count += n
+
+    def barostat(self):
+        return np.array([self.lam]), np.array([0.0])
+
+    def topology(self):
+        return {"connected": np.array([self.d_grip < self.fail_at]), "neck": np.array([3])}
+
+
+def test_paper_protocol_phases_and_strain_reference():
+    """Four phases in order: barostat at t_start with the grips held, ramp and
+    hold without barostat, then the stepwise pull; the ramp starts where the
+    barostat phase ends (counted from the engine's current step), and the
+    strains come back relative to the equilibrated length L0 e^lambda."""
+    from paper_1311_3890_b300.analysis import paper_protocol
+
+    lam = -0.04
+    eng = _FakeEngine(lam)
+    run = paper_protocol(eng, barostat_steps=500, ramp_steps=300, hold_steps=200, pull_step=0.05,
+                         pull_interval=20, report_every=100, max_pull_steps=20000)
+    sets = [kw for name, kw in eng.calls if name == "set_protocol"]
+    steps = [n for name, n in eng.calls if name == "step"]
+    assert len(sets) == 3 and steps[:2] == [500, 500]
+    assert sets[0]["baro_tau_fs"] > 0 and sets[0]["pull_step"] == 0.0
+    assert all(s.get("baro_tau_fs", 0.0) == 0.0 for s in sets[1:])
+    assert sets[1]["pull_step"] == 0.0 and sets[2]["pull_step"] == 0.05
+    assert all(s["ramp_start"] == 100 + 500 and s["ramp_steps"] == 300 and s["t_start"] == 0.01
+               for s in sets)
+    assert run.log_stretch[0] == lam
+    r = run.results[0]
+    # failure at a grip displacement of 6 A: strain 2 * 6 / (40 e^lambda)
+    assert r.eps_f == pytest.approx(2 * 6.0 / (40.0 * math.exp(lam)), rel=1e-12)
+    assert r.strain[-1] == pytest.approx(2 * eng.d_grip / (40.0 * math.exp(lam)), rel=1e-12)

@@ -38,7 +38,8 @@ def _oracle_proto(orc, p):
     return orc.Protocol(thermostat=p["thermostat"], pull=p["pull"], tau=p.get("tau_fs", 1000.0),
                         pull_step=p.get("pull_step", 0.05),
                         pull_interval=p.get("pull_interval", 10000),
-                        t_start=p.get("t_start", 0.01), ramp_steps=p.get("ramp_steps", 0))
+                        t_start=p.get("t_start", 0.01), ramp_steps=p.get("ramp_steps", 0),
+                        ramp_start=p.get("ramp_start", 0))
 
 
 def _oracle_wire(orc, b, w, v0):
@@ -103,6 +104,33 @@ def test_langevin_ramp_matches_oracle(tb, orc, prec, xtol, vtol):
                                       brute_max=3000)
         assert np.max(np.abs(x[s] - st.x)) < xtol
         assert np.max(np.abs(v[s] - st.v)) < vtol
+    eng.close()
+
+
+@pytest.mark.parametrize("prec,xtol,vtol,xirel", [("fp64", 1e-9, 1e-11, 1e-8),
+                                                   ("mixed", 2e-5, 2e-6, 1e-3)])
+def test_delayed_ramp_matches_oracle(tb, orc, prec, xtol, vtol, xirel):
+    """The ramp's start step (the paper holds 0.01 K through its barostat
+    phase): Nosé–Hoover with the target at t_start for 60 steps, then
+    ramped over 100 steps, 200 steps in all, against the oracle."""
+    p = dict(thermostat="nose_hoover", pull="stepwise", tau_fs=200.0, pull_step=0.05,
+             pull_interval=40, t_start=0.01, ramp_steps=100, ramp_start=60)
+    b = workload("tiny_batch")
+    eng = tb.Engine(b, precision=prec)
+    eng.init_velocities()
+    v0 = eng.velocities()
+    eng.set_protocol(**p)
+    eng.step(200, 2.0)
+    x, v = eng.positions(), eng.velocities()
+    xi, _ = eng.thermostat()
+    proto = _oracle_proto(orc, p)
+    for w in range(b.n_wires):
+        s = b.wire_slice(w)
+        st, nh = orc.md_steps_protocol(_oracle_wire(orc, b, w, v0), proto, 200, 2.0,
+                                       brute_max=3000)
+        assert np.max(np.abs(x[s] - st.x)) < xtol
+        assert np.max(np.abs(v[s] - st.v)) < vtol
+        assert xi[w] == pytest.approx(nh[0], rel=xirel, abs=1e-12)
     eng.close()
 
 

@@ -159,6 +159,32 @@ def test_ramp_is_followed_by_a_strong_thermostat(orc):
     assert np.mean(temps) == pytest.approx(np.mean(targets), rel=0.04)
 
 
+def test_delayed_ramp_holds_t_start_then_ramps(orc):
+    """ramp_start: the target stays at t_start until the ramp's first step
+    (the paper's 0.01 K barostat phase), then follows the ramp.  A strongly
+    damped Langevin gas started at 150 K cools to ~0 K during the hold and
+    tracks the ramp after it."""
+    x = _gas(216)
+    n = x.shape[0]
+    proto = orc.Protocol(thermostat="langevin", pull="continuous", t_start=0.01, ramp_steps=2000,
+                         ramp_start=1500)
+    for step, want in ((0, 0.01), (1499, 0.01), (1500, 0.01), (2500, 100.005), (3500, 200.0),
+                       (10 ** 6, 200.0)):
+        assert orc.target_temperature(proto, 200.0, step) == pytest.approx(want)
+    off = orc.Protocol(thermostat="langevin", pull="continuous", ramp_steps=0, ramp_start=1500)
+    assert orc.target_temperature(off, 200.0, 0) == 200.0
+    st = orc.WireState(x=x.copy(), v=orc.init_velocities(np.zeros(n, np.uint8), 4, 150.0),
+                       kind=np.zeros(n, np.uint8), L0=1.0, temperature=200.0, gamma=0.05, seed=9)
+    temps = []
+    for s in range(3500):
+        st, _ = orc.md_steps_protocol(st, proto, 1, 2.0)
+        temps.append(2 * _kin(orc, st.v) / (3 * n * orc.kb()))
+    temps = np.array(temps)
+    assert np.mean(temps[1000:1500]) < 0.5  # held at 0.01 K: cooled from 150 K
+    targets = [orc.target_temperature(proto, 200.0, s) for s in range(3000, 3500)]
+    assert np.mean(temps[3000:3500]) == pytest.approx(np.mean(targets), rel=0.04)
+
+
 def test_protocol_langevin_continuous_equals_md_steps(orc):
     """With the Langevin thermostat, continuous pull and no ramp the protocol
     integrator is the B A O A B integrator, bit for bit."""
