@@ -10,7 +10,11 @@ than itself: closed forms for the dimer and trimer, the bulk fcc shell sum and
 Au's experimental lattice constant, central finite differences of the energy,
 invariances, brute force vs cell-list pair sets, NVE energy conservation, the
 Ornstein-Uhlenbeck law of the O step, the dimer vibration period, Triton's
-Philox4x32-10, and the affine-strain derivative of the energy for Eq. 5.
+Philox4x32-10, the affine-strain derivative of the energy for Eq. 5, the
+Nosé–Hoover invariants (free particles, extended energy at O(dt^2)), the
+barostat's extended energy, target stress and a fixed-strain scan of the
+zero-stress length, and scipy's connected components and per-plane counts
+for the topology.
 """
 
 from __future__ import annotations
