@@ -204,3 +204,64 @@ def paper_protocol(eng, barostat_steps: int = 50000, ramp_steps: int = 200000,
         r.eps_y *= f
         r.eps_f *= f
     return PaperRun(lam, res)
+
+
+@dataclasses.dataclass
+class Campaign:
+    lengths_nm: np.ndarray  # initial length per wire
+    log_stretch: np.ndarray
+    eps_y: np.ndarray
+    sigma_y: np.ndarray  # eV/A^3
+    eps_f: np.ndarray  # nan where a wire did not fail
+    final_neck: np.ndarray
+    brittle: np.ndarray  # post-yield strain below the cut
+    critical_length_nm: float  # observed L_C (nan without a ductile/brittle pair)
+    failure_map: np.ndarray  # counts per (length bin, post-yield strain bin)
+    length_edges: np.ndarray
+    strain_edges: np.ndarray
+
+
+def campaign(eng, lengths_nm, length_edges=None, strain_edges=None, cut: float = 0.1,
+             **protocol) -> Campaign:
+    """The paper's statistical experiment on a batch (Results, "Nanowire
+    elongation"; Figures 4-10, Eq. 6): the whole protocol on every wire of
+    `eng` (paper_protocol, keyword arguments passed on), then per wire the
+    yield point, failure strain and final neck, the brittle/ductile split at
+    post-yield strain `cut`, the failure map over (initial length,
+    post-yield strain) bins and the observed critical length.  `lengths_nm`
+    gives each wire's initial length (the batch's own wire order)."""
+    run = paper_protocol(eng, **protocol)
+    L = np.asarray(lengths_nm, dtype=np.float64)
+    eps_y = np.array([r.eps_y for r in run.results])
+    eps_f = np.array([r.eps_f for r in run.results])
+    if length_edges is None:
+        u = np.unique(L)
+        mids = 0.5 * (u[1:] + u[:-1]) if u.size > 1 else np.array([])
+        length_edges = np.concatenate([[u[0] - 1.0], mids, [u[-1] + 1.0]])
+    if strain_edges is None:
+        strain_edges = np.linspace(0.0, 1.0, 21)
+    ok = np.isfinite(eps_f)
+    return Campaign(
+        lengths_nm=L, log_stretch=run.log_stretch, eps_y=eps_y,
+        sigma_y=np.array([r.sigma_y for r in run.results]), eps_f=eps_f,
+        final_neck=np.array([r.final_neck for r in run.results]),
+        brittle=np.where(ok, brittle(np.where(ok, eps_f, 0.0), eps_y, cut), False),
+        critical_length_nm=observed_critical_length(L[ok], eps_f[ok], eps_y[ok], cut),
+        failure_map=failure_map(L[ok], eps_f[ok], eps_y[ok], length_edges, strain_edges),
+        length_edges=np.asarray(length_edges), strain_edges=np.asarray(strain_edges))
+
+
+def save_results(path: str, results) -> None:
+    """Per-wire report histories and readings of pull_to_rupture or
+    paper_protocol into one compressed .npz (wire w's arrays under
+    "w{w}_strain", "w{w}_sigma", "w{w}_connected", "w{w}_neck"; the readings
+    as arrays over wires)."""
+    arrays = {}
+    for w, r in enumerate(results):
+        arrays[f"w{w}_strain"] = np.asarray(r.strain)
+        arrays[f"w{w}_sigma"] = np.asarray(r.sigma)
+        arrays[f"w{w}_connected"] = np.asarray(r.connected)
+        arrays[f"w{w}_neck"] = np.asarray(r.neck)
+    for k in ("sigma_y", "eps_y", "eps_f", "final_neck"):
+        arrays[k] = np.array([getattr(r, k) for r in results])
+    np.savez_compressed(path, **arrays)

@@ -130,3 +130,52 @@ def test_paper_protocol_phases_and_strain_reference():
     # failure at a grip displacement of 6 A: strain 2 * 6 / (40 e^lambda)
     assert r.eps_f == pytest.approx(2 * 6.0 / (40.0 * math.exp(lam)), rel=1e-12)
     assert r.strain[-1] == pytest.approx(2 * eng.d_grip / (40.0 * math.exp(lam)), rel=1e-12)
+
+
+def test_campaign_and_saved_results(tmp_path):
+    """campaign on two fake wires of different length: readings per wire,
+    the failure map counts both, and save_results writes every history."""
+    from paper_1311_3890_b300.analysis import campaign, save_results
+
+    class TwoWires(_FakeEngine):
+        def __init__(self):
+            super().__init__(-0.03)
+            self.W = 2
+            self.batch.L0 = np.array([40.0, 80.0])
+            self.d = np.zeros(2)
+
+        def observables(self):
+            return {"step": np.array([self.step_count] * 2),
+                    "strain": 2 * self.d / self.batch.L0,
+                    "sigma_xx": 0.01 * self.d * np.exp(-self.d / 2.0)}  # peaks at 2 A
+
+        def step(self, n, dt):
+            before = self.d_grip
+            super().step(n, dt)
+            self.d += self.d_grip - before
+
+        def barostat(self):
+            return np.array([-0.03, -0.03]), np.zeros(2)
+
+        def topology(self):
+            return {"connected": self.d < np.array([6.0, 4.0]), "neck": np.array([3, 3])}
+
+    eng = TwoWires()
+    c = campaign(eng, [4.0, 8.0], barostat_steps=100, ramp_steps=100, hold_steps=100,
+                 pull_step=0.05, pull_interval=20, report_every=100, max_pull_steps=20000)
+    f = math.exp(0.03)
+    assert c.eps_f == pytest.approx([2 * 6.0 / 40.0 * f, 2 * 4.0 / 80.0 * f], rel=1e-9)
+    assert c.failure_map.sum() == 2 and c.failure_map.shape == (2, 20)
+    assert np.all(c.eps_y < c.eps_f)
+    assert np.all(c.log_stretch == -0.03)
+    from paper_1311_3890_b300.analysis import paper_protocol  # noqa: F401
+
+    eng2 = TwoWires()
+    run = paper_protocol(eng2, barostat_steps=100, ramp_steps=100, hold_steps=100,
+                         pull_step=0.05, pull_interval=20, report_every=100,
+                         max_pull_steps=20000)
+    p = tmp_path / "run.npz"
+    save_results(str(p), run.results)
+    z = np.load(p)
+    assert set(z.files) >= {"w0_strain", "w1_neck", "eps_f", "final_neck"}
+    np.testing.assert_array_equal(z["w1_neck"], run.results[1].neck)

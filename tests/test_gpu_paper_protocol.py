@@ -41,3 +41,25 @@ def test_paper_protocol_equilibrates_and_pulls_to_rupture():
         d_grip = r.strain[-1] * w.L0 * math.exp(lam) / 2.0
         assert d_grip / 0.05 == pytest.approx(round(d_grip / 0.05), abs=1e-6)
     eng.close()
+
+
+def test_campaign_over_two_lengths(tmp_path):
+    """analysis.campaign on notched D2 wires of 4 and 6 nm (shortened
+    phases): every wire fails, the failure map counts each wire once in its
+    length bin, and the saved histories load back."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1311_3890_b300 as tb
+    from paper_1311_3890_b300.analysis import campaign, save_results
+
+    lengths = [4.0, 6.0]
+    wires = [fcc_wire(2.0, L, notch_depth=2.5, temperature=10.0, strain_rate=0.0, seed=7)
+             for L in lengths]
+    eng = tb.Engine(pack(wires), precision="mixed")
+    eng.init_velocities()
+    c = campaign(eng, lengths, barostat_steps=1000, ramp_steps=300, hold_steps=300,
+                 pull_step=0.05, pull_interval=20, report_every=100, max_pull_steps=60000,
+                 tau_fs=200.0, baro_tau_fs=100.0)
+    assert np.all(np.isfinite(c.eps_f)) and np.all(c.eps_y < c.eps_f)
+    assert c.failure_map.sum(axis=1).tolist() == [1, 1]
+    eng.close()
