@@ -14,7 +14,11 @@ Philox4x32-10, the affine-strain derivative of the energy for Eq. 5, the
 Nosé–Hoover invariants (free particles, extended energy at O(dt^2)), the
 barostat's extended energy, target stress and a fixed-strain scan of the
 zero-stress length, and scipy's connected components and per-plane counts
-for the topology.
+for the topology.  The tabulated EAM (tests/test_oracle_eam.py): exactness
+for quadratics and the third-order error of its interpolant, closed-form
+dimer and trimer energies and forces, the linear continuation of the
+embedding, TB-SMA itself when the tables sample Eq. 1-2, finite
+differences and invariances.
 """
 
 from __future__ import annotations
@@ -121,6 +125,12 @@ def _declare(L):
     L.or_observables.argtypes = [_P, _P, _P, _I, _P, _P, _P, _D, _I, _P]
     L.or_topology.argtypes = [_I, _P, _P, _D, _D, _L, _P, _P]
     L.or_topology.restype = _L
+    L.or_eam_interp.argtypes = [_P, _I, _D, _D, _P]
+    L.or_eam_interp.restype = _D
+    L.or_eam_energy_forces.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P]
+    L.or_eam_energy_forces.restype = _D
+    L.or_eam_on_pairs.argtypes = [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.or_eam_on_pairs.restype = _D
 
 
 def _ptr(a: np.ndarray | None):
@@ -505,3 +515,81 @@ def observables(st: WireState, pot: Potential = AU, mass: float = MASS_AU,
         _ptr(_f64(st.v)), _ptr(kind), st.d_grip, brute_max, _ptr(out),
     )
     return Observables(*[float(t) for t in out])
+
+
+# ------------------------------------------------------------- tabulated EAM
+class _Eam(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_void_p), ("n_rho", ctypes.c_int), ("d_rho", ctypes.c_double),
+                ("f", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("n_r", ctypes.c_int),
+                ("d_r", ctypes.c_double), ("r_cut", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class EamTables:
+    """EAM functions sampled on uniform grids: F(k d_rho) for k < len(F),
+    f(k d_r) and phi(k d_r) for k < len(f); pairs with r <= r_cut interact.
+    E = sum_i F(rho_i) + 1/2 sum_{i != j} phi(r_ij), rho_i = sum_j f(r_ij)."""
+
+    F: np.ndarray
+    d_rho: float
+    f: np.ndarray
+    phi: np.ndarray
+    d_r: float
+    r_cut: float
+
+    def _c(self):
+        self._keep = [_f64(self.F), _f64(self.f), _f64(self.phi)]
+        assert self._keep[0].size >= 3 and self._keep[1].size == self._keep[2].size >= 3
+        return _Eam(self._keep[0].ctypes.data, self._keep[0].size, self.d_rho,
+                    self._keep[1].ctypes.data, self._keep[2].ctypes.data, self._keep[1].size,
+                    self.d_r, self.r_cut)
+
+
+def eam_interp(y: np.ndarray, h: float, s) -> tuple[np.ndarray, np.ndarray]:
+    """The tables' interpolant (cubic Hermite, finite-difference node slopes,
+    straight-line continuation past the ends): value and derivative at s."""
+    y = _f64(y)
+    s = np.atleast_1d(np.asarray(s, dtype=np.float64))
+    val, der = np.empty_like(s), np.empty_like(s)
+    d = ctypes.c_double(0.0)
+    for k, sk in enumerate(s):
+        val[k] = lib().or_eam_interp(_ptr(y), y.size, h, float(sk), ctypes.byref(d))
+        der[k] = d.value
+    return val, der
+
+
+def eam(x: np.ndarray, tab: EamTables, brute_max: int = 2000) -> Forces:
+    """Tabulated EAM energy and forces (two passes), pairs from scratch;
+    eB = F(rho_i), eR = 1/2 sum_j phi(r_ij)."""
+    x = _f64(x)
+    n = x.shape[0]
+    F = np.zeros((n, 3))
+    rho, eB, eR, w, S = (np.zeros(n) for _ in range(5))
+    npairs = ctypes.c_long(0)
+    t = tab._c()
+    E = lib().or_eam_energy_forces(
+        ctypes.byref(t), n, _ptr(x), brute_max, _ptr(F), _ptr(rho), _ptr(eB), _ptr(eR),
+        _ptr(w), _ptr(S), ctypes.byref(npairs),
+    )
+    return Forces(E, F, rho, eB, eR, w, S, int(npairs.value))
+
+
+def eam_energy(x: np.ndarray, tab: EamTables, brute_max: int = 2000) -> float:
+    x = _f64(x)
+    t = tab._c()
+    return lib().or_eam_energy_forces(ctypes.byref(t), x.shape[0], _ptr(x), brute_max,
+                                      None, None, None, None, None, None, None)
+
+
+def eam_on_pairs(x, start, nbr, tab: EamTables) -> Forces:
+    """Tabulated EAM on a caller-given pair set."""
+    x = _f64(x)
+    n = x.shape[0]
+    start = np.ascontiguousarray(start, dtype=np.int32)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    F = np.zeros((n, 3))
+    rho, eB, eR, w, S = (np.zeros(n) for _ in range(5))
+    t = tab._c()
+    E = lib().or_eam_on_pairs(ctypes.byref(t), n, _ptr(x), _ptr(start), _ptr(nbr), _ptr(rho),
+                              _ptr(F), _ptr(eB), _ptr(eR), _ptr(w), _ptr(S))
+    return Forces(E, F, rho, eB, eR, w, S, int(nbr.shape[0]))

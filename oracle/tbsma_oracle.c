@@ -830,3 +830,139 @@ void or_observables(const or_pot* P, const or_md* M, const or_wire* W, int n, co
   out[5] = 2.0 * d_grip / W->L0;
   free(w);
 }
+
+/* ======================================================================
+ * Tabulated embedded-atom method (EAM) on the same pair sets.
+ *
+ * The paper builds its TB-SMA force on the two-stage structure of the EAM
+ * implementation it cites (Introduction; Methods, "TB-SMA potential"): a
+ * density loop over i's neighbours, then a force loop that needs the
+ * embedding derivative of both i and j.  EAM in its general form:
+ *   rho_i = sum_j f(r_ij),   E = sum_i [ F(rho_i) + 1/2 sum_j phi(r_ij) ],
+ *   F_i   = -sum_j [ phi'(r_ij) + (F'(rho_i) + F'(rho_j)) f'(r_ij) ] (r_i - r_j)/r_ij,
+ * pairs j != i with r_ij <= r_cut.  TB-SMA is the case f = xi^2 e^{-2qs},
+ * phi = 2 A e^{-ps}, F = -sqrt(rho).
+ *
+ * F, f and phi are given as samples on uniform grids (F at rho = k d_rho,
+ * f and phi at r = k d_r, k = 0..n-1).  Between samples each is the cubic
+ * Hermite interpolant whose node slopes are finite differences of the
+ * samples: central (y[k+1] - y[k-1]) / 2h inside, the one-sided second-order
+ * forms (-3 y0 + 4 y1 - y2) / 2h and (3 y[n-1] - 4 y[n-2] + y[n-3]) / 2h at
+ * the ends (all exact for quadratics, so a quadratic is reproduced exactly).
+ * Beyond the last sample (or below 0) a function continues as the straight
+ * line through its end sample with its end slope.
+ * ==================================================================== */
+typedef struct {
+  const double* F;   /* n_rho samples of F(rho), eV */
+  int n_rho;
+  double d_rho;
+  const double* f;   /* n_r samples of f(r) */
+  const double* phi; /* n_r samples of phi(r), eV */
+  int n_r;
+  double d_r;
+  double r_cut;
+} or_eam;
+
+static double node_slope(const double* y, int n, double h, int k) {
+  if (k == 0) return (-3.0 * y[0] + 4.0 * y[1] - y[2]) / (2.0 * h);
+  if (k == n - 1) return (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) / (2.0 * h);
+  return (y[k + 1] - y[k - 1]) / (2.0 * h);
+}
+
+/* Value and derivative of the interpolant of y[0..n) (spacing h) at s. */
+double or_eam_interp(const double* y, int n, double h, double s, double* dyds) {
+  const double s_max = (n - 1) * h;
+  if (s < 0.0 || s > s_max) {
+    const int k = s < 0.0 ? 0 : n - 1;
+    const double m = node_slope(y, n, h, k);
+    if (dyds) *dyds = m;
+    return y[k] + m * (s - k * h);
+  }
+  int k = (int)floor(s / h);
+  if (k > n - 2) k = n - 2;
+  const double u = s / h - k;
+  const double m0 = node_slope(y, n, h, k), m1 = node_slope(y, n, h, k + 1);
+  /* Hermite basis on [0, 1] and its derivative */
+  const double h00 = 2 * u * u * u - 3 * u * u + 1, h10 = u * u * u - 2 * u * u + u;
+  const double h01 = -2 * u * u * u + 3 * u * u, h11 = u * u * u - u * u;
+  const double d00 = 6 * u * u - 6 * u, d10 = 3 * u * u - 4 * u + 1;
+  const double d01 = -6 * u * u + 6 * u, d11 = 3 * u * u - 2 * u;
+  if (dyds) *dyds = (d00 * y[k] + d01 * y[k + 1]) / h + d10 * m0 + d11 * m1;
+  return h00 * y[k] + h10 * h * m0 + h01 * y[k + 1] + h11 * h * m1;
+}
+
+/* EAM energy and forces on a given pair set, two passes.  Outputs as in
+ * or_tbsma (NULL skips): rho, F, eB[i] = F(rho_i), eR[i] = 1/2 sum_j phi,
+ * w[i] = 1/2 sum_j (x_j - x_i) F_ij,x, S[i] = sum_j |f_ij| with f_ij the
+ * bracket's magnitude along (r_i - r_j)/r.  Returns E. */
+double or_eam_on_pairs(const or_eam* T, int n, const double* x, const int* start, const int* nbr,
+                       double* rho, double* F, double* eB, double* eR, double* w, double* S) {
+  double* dF = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double E = 0.0;
+  /* pass 1: densities and embedding energies */
+  for (int i = 0; i < n; ++i) {
+    double r_i = 0.0;
+    for (int k = start[i]; k < start[i + 1]; ++k)
+      r_i += or_eam_interp(T->f, T->n_r, T->d_r, sqrt(dist2(x, i, nbr[k])), NULL);
+    const double e_b = or_eam_interp(T->F, T->n_rho, T->d_rho, r_i, &dF[i]);
+    if (rho) rho[i] = r_i;
+    if (eB) eB[i] = e_b;
+    E += e_b;
+  }
+  /* pass 2: forces, pair energy, virial */
+  for (int i = 0; i < n; ++i) {
+    double fx = 0.0, fy = 0.0, fz = 0.0, e_r = 0.0, wi = 0.0, si = 0.0;
+    for (int k = start[i]; k < start[i + 1]; ++k) {
+      const int j = nbr[k];
+      const double dx = x[3 * i + 0] - x[3 * j + 0];
+      const double dy = x[3 * i + 1] - x[3 * j + 1];
+      const double dz = x[3 * i + 2] - x[3 * j + 2];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      double dphi, df;
+      const double phi = or_eam_interp(T->phi, T->n_r, T->d_r, r, &dphi);
+      or_eam_interp(T->f, T->n_r, T->d_r, r, &df);
+      /* -dE/dr_ij, the pair's force along (r_i - r_j)/r */
+      const double f = -(dphi + (dF[i] + dF[j]) * df);
+      fx += f * dx / r;
+      fy += f * dy / r;
+      fz += f * dz / r;
+      e_r += 0.5 * phi;
+      wi += 0.5 * (-dx) * (f * dx / r);
+      si += fabs(f);
+    }
+    if (F) {
+      F[3 * i + 0] = fx;
+      F[3 * i + 1] = fy;
+      F[3 * i + 2] = fz;
+    }
+    if (eR) eR[i] = e_r;
+    if (w) w[i] = wi;
+    if (S) S[i] = si;
+    E += e_r;
+  }
+  free(dF);
+  return E;
+}
+
+/* Pair set (brute force if n <= brute_max, else cells) + EAM. */
+double or_eam_energy_forces(const or_eam* T, int n, const double* x, int brute_max, double* F,
+                            double* rho, double* eB, double* eR, double* w, double* S,
+                            long* n_pairs_out) {
+  long cap = 64L * n + 64;
+  int* start = (int*)malloc(sizeof(int) * (n + 1));
+  int* nbr = NULL;
+  long k;
+  for (;;) {
+    nbr = (int*)malloc(sizeof(int) * cap);
+    k = (n <= brute_max) ? or_pairs_brute(n, x, T->r_cut, start, nbr, cap)
+                         : or_pairs_cells(n, x, T->r_cut, start, nbr, cap);
+    if (k >= 0) break;
+    free(nbr);
+    cap *= 2;
+  }
+  double E = or_eam_on_pairs(T, n, x, start, nbr, rho, F, eB, eR, w, S);
+  if (n_pairs_out) *n_pairs_out = k;
+  free(start);
+  free(nbr);
+  return E;
+}
