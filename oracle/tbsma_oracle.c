@@ -882,13 +882,17 @@ double or_eam_interp(const double* y, int n, double h, double s, double* dyds) {
   if (k > n - 2) k = n - 2;
   const double u = s / h - k;
   const double m0 = node_slope(y, n, h, k), m1 = node_slope(y, n, h, k + 1);
-  /* Hermite basis on [0, 1] and its derivative */
-  const double h00 = 2 * u * u * u - 3 * u * u + 1, h10 = u * u * u - 2 * u * u + u;
-  const double h01 = -2 * u * u * u + 3 * u * u, h11 = u * u * u - u * u;
-  const double d00 = 6 * u * u - 6 * u, d10 = 3 * u * u - 4 * u + 1;
-  const double d01 = -6 * u * u + 6 * u, d11 = 3 * u * u - 2 * u;
-  if (dyds) *dyds = (d00 * y[k] + d01 * y[k + 1]) / h + d10 * m0 + d11 * m1;
-  return h00 * y[k] + h10 * h * m0 + h01 * y[k + 1] + h11 * h * m1;
+  /* Hermite basis on [0, 1] and its derivative.  h00 = 1 - h01 and
+   * d00 = -d01, so the two sample terms are grouped through the sample
+   * difference (exact in floating point for neighbouring samples): summing
+   * h00 y_k and h01 y_{k+1} separately would cancel to a few ulp of y, not of
+   * the derivative. */
+  const double h01 = -2 * u * u * u + 3 * u * u, h10 = u * u * u - 2 * u * u + u;
+  const double h11 = u * u * u - u * u;
+  const double d01 = -6 * u * u + 6 * u, d10 = 3 * u * u - 4 * u + 1, d11 = 3 * u * u - 2 * u;
+  const double dy = y[k + 1] - y[k];
+  if (dyds) *dyds = d01 * dy / h + d10 * m0 + d11 * m1;
+  return y[k] + h01 * dy + h10 * h * m0 + h11 * h * m1;
 }
 
 /* EAM energy and forces on a given pair set, two passes.  Outputs as in
