@@ -62,6 +62,9 @@ def parse():
                    help="pick the pair passes' launch shape with the autotuner first")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the cpu baseline, fp64 comparison and e2e legs")
+    p.add_argument("--potential", default="tbsma", choices=["tbsma", "eam"],
+                   help="eam: the tabulated-EAM pair passes (tbsma_set_eam) on Au tables that "
+                        "sample the TB-SMA functions; device-timed line only (no extras)")
     p.add_argument("--table2", action="store_true",
                    help="context: steps/s of the paper's Table 2 wires, each alone, 10 and 298 K")
     return p.parse_args()
@@ -287,6 +290,12 @@ def launches_in(K: int, chains: int) -> int:
 # The roofline time is the slower of the ALU time (FP32 and MUFU pipes run
 # concurrently: the larger of the two) and the HBM time.
 FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 21, 7, 3
+# The tabulated-EAM force pass (--potential eam) per in-cutoff entry: the
+# same geometry (6), radius (4, one MUFU rsqrt), bracket (2), scale (1) and
+# accumulation (3), plus the interval and t of r (5: FMUL, F2I, I2F, two
+# FFMA) and two quadratic derivative polynomials (4) in place of the two ex2;
+# MUFU 1; skin entries as above.
+EAM_PER_IN = (25, 7, 1)
 # DRAM bytes (read + write) per atom of one force-pass launch, from an ncu
 # capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms,
 # r_skin 0.40 A, first launch: 72.322 MB read + 1.031 MB written), scaled by
@@ -294,6 +303,19 @@ FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 21, 7, 3
 # profiles/pair_integrate_batch32_d3_l40.md.  Set to None when the kernel
 # changes until it is captured again.
 FORCE_TRAFFIC_B_PER_ATOM = 131.5
+
+
+def au_eam_tables(d_r=0.002, d_rho=0.005, rho_max=120.0, r_cut=5.8):
+    """Au as a tabulated EAM for the --potential eam line: the TB-SMA
+    functions of Table 1 sampled on uniform grids (f = xi^2 e^{-2q s},
+    phi = 2 A e^{-p s}, F = -sqrt(rho)), so that the EAM run has the TB-SMA
+    run's dynamics and rebuild cadence and only the pair arithmetic differs."""
+    A, xi, p, q, r0 = 0.2061, 1.790, 10.229, 4.036, 2.884
+    r = np.arange(int(np.ceil((r_cut + 0.05) / d_r)) + 1) * d_r
+    s = r / r0 - 1.0
+    rho = np.arange(int(np.ceil(rho_max / d_rho)) + 1) * d_rho
+    return dict(F=-np.sqrt(rho), d_rho=d_rho, f=xi * xi * np.exp(-2.0 * q * s),
+                phi=2.0 * A * np.exp(-p * s), d_r=d_r)
 
 
 def _list_census(eng, r_cut=5.8, chunk=1 << 20):
@@ -316,15 +338,16 @@ def _list_census(eng, r_cut=5.8, chunk=1 << 20):
     return n_in / N, (n_all - n_in) / N
 
 
-def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs):
+def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs, per_in=(FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN)):
     """The force pass's roofline from its algorithmic work (per atom: n_c
     in-cutoff and n_s skin list entries) and its measured time per launch
     `ms`, for `sms` SMs at `mhz` and an HBM peak of `hbm_gbs`: the bound is
     the slower of the FP32 and MUFU pipes (which run concurrently) and the
     bytes at HBM bandwidth; `achieved` is the bound's work over the time."""
     f = mhz * 1e6
-    fp32_ops = N * (FP32_PER_IN * n_c + FP32_PER_SKIN * n_s)
-    mufu_ops = N * MUFU_PER_IN * n_c
+    fp32_in, fp32_skin, mufu_in = per_in
+    fp32_ops = N * (fp32_in * n_c + fp32_skin * n_s)
+    mufu_ops = N * mufu_in * n_c
     bytes_ = N * (2.0 * (n_c + n_s) + 4 + 8 + 16 + 12)
     t_fp32 = fp32_ops / (128 * sms * f)
     t_mufu = mufu_ops / (32 * sms * f)
@@ -350,17 +373,19 @@ def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs):
     return bound
 
 
-def force_roofline(eng, ms, clocks):
+def force_roofline(eng, ms, clocks, eam=False):
     import torch
 
     n_c, n_s = _list_census(eng)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     hbm, kind = _peaks()
     bound = roofline_of(eng.N, n_c, n_s, ms, props.multi_processor_count,
-                        clocks.get("sm_mhz") or 2032.0, hbm)
+                        clocks.get("sm_mhz") or 2032.0, hbm,
+                        **({"per_in": EAM_PER_IN} if eam else {}))
+    traffic = None if (eam or FORCE_TRAFFIC_B_PER_ATOM is None) else FORCE_TRAFFIC_B_PER_ATOM * eng.N
     bound.update({
-        "kernel": "k_force_f32",
-        "traffic": None if FORCE_TRAFFIC_B_PER_ATOM is None else FORCE_TRAFFIC_B_PER_ATOM * eng.N,
+        "kernel": "k_force_f32<EAM>" if eam else "k_force_f32",
+        "traffic": traffic,
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per atom, small-case "
                           "capture scaled by atoms",
         "hbm_peak_kind": kind,
@@ -385,6 +410,9 @@ def run_ours(args):
     N, W = batch.n_atoms, batch.n_wires
     params = tb.au_params(r_skin=R_SKIN)
     eng = tb.Engine(batch, precision="mixed", params=params)
+    eam = args.potential == "eam"
+    if eam:
+        eng.set_eam(**au_eam_tables())
     eng.init_velocities()
     eng.step(max(3, args.warmup), 2.0)
     launch = LAUNCH
@@ -433,7 +461,7 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    roof = force_roofline(eng, res[2], ck)
+    roof = force_roofline(eng, res[2], ck, eam=eam)
     roof["density_ms_per_launch"] = res[1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -442,6 +470,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
                    "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
+                   "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
                    "observables_every": OBS_EVERY, "r_skin_A": R_SKIN,
                    "tile_atoms": launch[0], "window_atoms": launch[1],
                    "launch": "autotuned" if args.autotune else "fixed",
@@ -455,7 +484,7 @@ def run_ours(args):
         "rebuilds_per_wire": float(ob["n_rebuilds"].mean()),
     }
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and not eam and rank == 0:
         # end to end through the public API: pinned host state in, K steps in
         # segments, per-wire observables and state out every segment
         seg = max(1, min(args.e2e_seg, args.steps))

@@ -293,6 +293,46 @@ tbsma_status tbsma_wire_topology(tbsma_ctx* ctx, tbsma_topology* out, int32_t* l
  * context still usable.  Errors: EINVAL (steps < 1). */
 tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
 
+/* Tabulated embedded-atom method (EAM), the general form of the two-stage
+ * many-body force the paper builds TB-SMA on (Introduction; Methods,
+ * "TB-SMA potential": the force is computed in two kernels, each looping
+ * over atom i's neighbours, as in the EAM implementation it cites):
+ *   rho_i = sum_j f(r_ij),   E = sum_i [F(rho_i) + 1/2 sum_j phi(r_ij)],
+ *   F_i = -sum_j [phi'(r_ij) + (F'(rho_i) + F'(rho_j)) f'(r_ij)] (r_i - r_j)/r_ij,
+ * over pairs j != i with r_ij <= params.r_cut.  TB-SMA (Eq. 1-3) is the case
+ * f = xi^2 e^{-2q s}, phi = 2 A e^{-p s}, F = -sqrt(rho).
+ *
+ * The functions are given as samples on uniform grids: F[k] = F(k d_rho)
+ * for k < n_rho, f[k] = f(k d_r) and phi[k] = phi(k d_r) for k < n_r (host
+ * arrays of doubles, read during the call only).  Between samples each is
+ * the cubic Hermite interpolant whose node slopes are the finite
+ * differences (y[k+1] - y[k-1]) / 2h inside and (-3 y0 + 4 y1 - y2) / 2h,
+ * (3 y[n-1] - 4 y[n-2] + y[n-3]) / 2h at the two ends; F continues past
+ * either end of its grid as the tangent line at the end sample. */
+typedef struct {
+  const double* F;   /* n_rho samples of the embedding energy F(rho), eV */
+  int32_t n_rho;
+  double d_rho;      /* rho grid spacing (rho in the units of f) */
+  const double* f;   /* n_r samples of the density function f(r) */
+  const double* phi; /* n_r samples of the pair energy phi(r), eV */
+  int32_t n_r;
+  double d_r;        /* r grid spacing, A */
+} tbsma_eam;
+
+/* Switch the context's potential to the tabulated EAM (tables != NULL) or
+ * back to TB-SMA with the context's parameters (tables == NULL).  The
+ * tables are copied to library-owned device memory (any earlier EAM tables
+ * are freed, after the context's stream has drained).  The neighbour lists,
+ * r_cut and r_skin are unchanged; the forces of the current positions are
+ * recomputed (enqueued), so the next step starts from the new potential.
+ * Both precisions use the tables: MIXED in FP32 (coefficients rounded once
+ * from the FP64 ones), FP64 in FP64; energies (tbsma_atom_energies,
+ * tbsma_reduce_observables) are FP64 sums.  A checkpoint holds no tables:
+ * set the same tables before tbsma_restore_state.  Errors: EINVAL (null
+ * arrays, n_rho or n_r < 3 or > 2^22, spacings not positive and finite, a
+ * non-finite sample, (n_r - 1) d_r < r_cut), ENOMEM, ECUDA. */
+tbsma_status tbsma_set_eam(tbsma_ctx* ctx, const tbsma_eam* tables);
+
 /* Checkpoint / resume.  A wire's counters: grip displacement (A), the
  * Nosé–Hoover state, the barostat's log-stretch and strain rate, the number
  * of list rebuilds and its status word. */

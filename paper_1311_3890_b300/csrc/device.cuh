@@ -129,6 +129,28 @@ struct PairConsts {
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
 };
 
+// Tabulated EAM tables on the device (tbsma_set_eam).  Each function is a
+// piecewise cubic over its grid's intervals: on interval k, with t = s/h - k
+// in [0, 1), value = c0 + t (c1 + t (c2 + t c3)); the coefficients are the
+// cubic Hermite interpolant of the samples with finite-difference node
+// slopes, formed on the host.  FP32 tables serve the mixed pair passes (r in
+// fixed-point units, so the grid scale 2^-26 / d_r comes split in two floats
+// for a full-precision t), FP64 tables the FP64 passes and every energy.
+struct EamDev {
+  const float4* f32;   // [n_r - 1] value coefficients of f (density pass)
+  const float4* d32;   // [2 (n_r - 1)] per interval {f'0, f'1, f'2, phi'0}, {phi'1, phi'2, 0, 0},
+                       // derivative coefficients per A: f'(t) = f'0 + t (f'1 + t f'2)
+  const float4* p32;   // [n_r - 1] value coefficients of phi (pair energy)
+  const float4* F32;   // [n_rho - 1] value coefficients of F (embedding slope)
+  const double* f64;   // [4 (n_r - 1)] value coefficients of f, c0..c3 per interval
+  const double* p64;   // [4 (n_r - 1)] of phi
+  const double* F64;   // [4 (n_rho - 1)] of F
+  float inv_dr_hi, inv_dr_lo;  // 2^-26 / d_r = hi + lo (r in fixed-point units)
+  float inv_drho_hi, inv_drho_lo;
+  int kmax_r, kmax_rho;        // last interval: n - 2
+  double inv_dr, inv_drho;     // 1 / d_r, 1 / d_rho
+};
+
 // Neighbour lists hold int16 offsets j - i, by slot, warp-tiled and grouped
 // by four: entries 4g..4g+3 of slot t form one 8-byte group, and the groups g
 // of 32 consecutive slots are contiguous (256 bytes), so a warp reads four

@@ -110,6 +110,9 @@ struct tbsma_ctx {
   double graph_dt = -1.0;
 
   PairConsts pc{};
+  bool eam_on = false;           // tabulated EAM instead of Eq. 1-3 (tbsma_set_eam)
+  EamDev eam{};
+  std::vector<void*> eam_allocs;  // the EAM tables (replaced by every tbsma_set_eam)
   float rlist2 = 0.f;
   double half_skin2 = 0.0;
   double inv_m = 0.0;
@@ -199,6 +202,28 @@ void fill_pair_consts(tbsma_ctx* c) {
   c->cap = std::min(kMaxCap, std::max(kMinCap, want));
 }
 
+// Cubic coefficients c0..c3 (in y per grid step, t = s/h - k) on every
+// interval k of the Hermite interpolant of y[0..n) whose node slopes are the
+// finite differences of the samples: central inside, one-sided second order
+// at the two ends.  From the Hermite basis: c0 = y_k, c1 = m_k,
+// c2 = 3 (y_{k+1} - y_k) - 2 m_k - m_{k+1}, c3 = 2 (y_k - y_{k+1}) + m_k + m_{k+1}.
+std::vector<double> hermite_cubics(const double* y, int n) {
+  auto m = [&](int k) {
+    if (k == 0) return 0.5 * (-3.0 * y[0] + 4.0 * y[1] - y[2]);
+    if (k == n - 1) return 0.5 * (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]);
+    return 0.5 * (y[k + 1] - y[k - 1]);
+  };
+  std::vector<double> c(4 * (size_t)(n - 1));
+  for (int k = 0; k + 1 < n; ++k) {
+    const double a = y[k], b = y[k + 1], ma = m(k), mb = m(k + 1);
+    c[4 * (size_t)k + 0] = a;
+    c[4 * (size_t)k + 1] = ma;
+    c[4 * (size_t)k + 2] = 3.0 * (b - a) - 2.0 * ma - mb;
+    c[4 * (size_t)k + 3] = 2.0 * (a - b) + ma + mb;
+  }
+  return c;
+}
+
 // ------------------------------------------------------------- launchers
 tbsma_status launch_pack(tbsma_ctx* c, cudaStream_t s, int check) {
   const unsigned g = grid_for(c->N, 256);
@@ -241,30 +266,44 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   return launch_rebuild(c, s);
 }
 
-template <bool OBS>
-void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
+template <bool OBS, bool EAM>
+void pair_f32_pot(tbsma_ctx* c, cudaStream_t s, int which) {
   const unsigned g = grid_for(c->NS, c->block);
   const size_t smem = (size_t)c->wcap * sizeof(int4);
   if (which & 1)
-    k_density_f32<OBS><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
-                                                 c->wcap, c->pc, c->e_band);
+    k_density_f32<OBS, EAM><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange,
+                                                      c->cap, c->wcap, c->pc, c->e_band, c->eam);
   if (which & 2)
-    k_force_f32<OBS><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange, c->cap,
-                                               c->wcap, c->pc, c->f32, c->f32 + c->N, c->f32 + 2 * c->N,
-                                               c->e_band, c->e_atom,
-                                               c->w_atom, c->s_atom);
+    k_force_f32<OBS, EAM><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange,
+                                                    c->cap, c->wcap, c->pc, c->f32, c->f32 + c->N,
+                                                    c->f32 + 2 * c->N, c->e_band, c->e_atom,
+                                                    c->w_atom, c->s_atom, c->eam);
+}
+
+template <bool OBS>
+void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
+  if (c->eam_on) pair_f32_pot<OBS, true>(c, s, which);
+  else pair_f32_pot<OBS, false>(c, s, which);
+}
+
+template <bool OBS, bool DECIDE32, bool EAM>
+void pair_f64_pot(tbsma_ctx* c, cudaStream_t s, int which) {
+  const unsigned g = grid_for(c->NS, c->block);
+  if (which & 1)
+    k_density_f64<OBS, DECIDE32, EAM><<<g, c->block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                              c->perm, c->cap, c->pc, c->inv64,
+                                                              c->e_band, c->eam);
+  if (which & 2)
+    k_force_f64<OBS, DECIDE32, EAM><<<g, c->block, 0, s>>>(c->N, c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
+                                                            c->perm, c->cap, c->pc, c->inv64, c->f64,
+                                                            c->e_band, c->e_atom, c->w_atom, c->s_atom,
+                                                            c->eam);
 }
 
 template <bool OBS, bool DECIDE32>
 void pair_f64(tbsma_ctx* c, cudaStream_t s, int which = 3) {
-  const unsigned g = grid_for(c->NS, c->block);
-  if (which & 1)
-    k_density_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                         c->perm, c->cap, c->pc, c->inv64, c->e_band);
-  if (which & 2)
-    k_force_f64<OBS, DECIDE32><<<g, c->block, 0, s>>>(c->N, c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
-                                                       c->perm, c->cap, c->pc, c->inv64, c->f64, c->e_band,
-                                                       c->e_atom, c->w_atom, c->s_atom);
+  if (c->eam_on) pair_f64_pot<OBS, DECIDE32, true>(c, s, which);
+  else pair_f64_pot<OBS, DECIDE32, false>(c, s, which);
 }
 
 // prec: arithmetic of the pass; decide32: FP64 pass taking the FP32 cutoff rule
@@ -528,10 +567,17 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int smem_max = kMaxWindow * (int)sizeof(int4);
-  if (cudaFuncSetAttribute(k_density_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_density_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
+  const auto smem_attr = [&](const void* k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) == cudaSuccess;
+  };
+  if (!smem_attr((const void*)k_density_f32<false, false>) ||
+      !smem_attr((const void*)k_density_f32<true, false>) ||
+      !smem_attr((const void*)k_force_f32<false, false>) ||
+      !smem_attr((const void*)k_force_f32<true, false>) ||
+      !smem_attr((const void*)k_density_f32<false, true>) ||
+      !smem_attr((const void*)k_density_f32<true, true>) ||
+      !smem_attr((const void*)k_force_f32<false, true>) ||
+      !smem_attr((const void*)k_force_f32<true, true>))
     return bail(TBSMA_ECUDA);
   const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
   if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
@@ -848,6 +894,96 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* c, const tbsma_protocol* p) {
   return TBSMA_OK;
 }
 
+tbsma_status tbsma_set_eam(tbsma_ctx* c, const tbsma_eam* t) {
+  if (!c) return TBSMA_EINVAL;
+  constexpr int kMaxSamples = 1 << 22;
+  if (t) {
+    if (!t->F || !t->f || !t->phi) return fail(c, TBSMA_EINVAL, "null EAM table");
+    if (t->n_rho < 3 || t->n_r < 3 || t->n_rho > kMaxSamples || t->n_r > kMaxSamples)
+      return fail(c, TBSMA_EINVAL, "EAM tables need 3 to 2^22 samples");
+    if (!(t->d_rho > 0.0 && std::isfinite(t->d_rho) && t->d_r > 0.0 && std::isfinite(t->d_r)))
+      return fail(c, TBSMA_EINVAL, "EAM grid spacings must be positive and finite");
+    if ((t->n_r - 1) * t->d_r < c->P.r_cut)
+      return fail(c, TBSMA_EINVAL, "the EAM r grid ends before r_cut");
+    for (int k = 0; k < t->n_rho; ++k)
+      if (!std::isfinite(t->F[k])) return fail(c, TBSMA_EINVAL, "non-finite EAM sample");
+    for (int k = 0; k < t->n_r; ++k)
+      if (!std::isfinite(t->f[k]) || !std::isfinite(t->phi[k]))
+        return fail(c, TBSMA_EINVAL, "non-finite EAM sample");
+  }
+  // kernels in flight (or a captured graph) may hold the old tables
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  for (void* p : c->eam_allocs) cudaFree(p);
+  c->eam_allocs.clear();
+  c->eam = EamDev{};
+  c->eam_on = false;
+  if (t) {
+    const std::vector<double> cf = hermite_cubics(t->f, t->n_r);
+    const std::vector<double> cp = hermite_cubics(t->phi, t->n_r);
+    const std::vector<double> cF = hermite_cubics(t->F, t->n_rho);
+    const size_t nr = (size_t)t->n_r - 1, nF = (size_t)t->n_rho - 1;
+    std::vector<float4> f32(nr), d32(2 * nr), p32(nr), F32(nF);
+    const double idr = 1.0 / t->d_r;
+    for (size_t k = 0; k < nr; ++k) {
+      const double* a = &cf[4 * k];
+      const double* b = &cp[4 * k];
+      f32[k] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+      p32[k] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
+      d32[2 * k] = make_float4((float)(a[1] * idr), (float)(2.0 * a[2] * idr), (float)(3.0 * a[3] * idr),
+                               (float)(b[1] * idr));
+      d32[2 * k + 1] = make_float4((float)(2.0 * b[2] * idr), (float)(3.0 * b[3] * idr), 0.f, 0.f);
+    }
+    for (size_t k = 0; k < nF; ++k)
+      F32[k] = make_float4((float)cF[4 * k], (float)cF[4 * k + 1], (float)cF[4 * k + 2],
+                           (float)cF[4 * k + 3]);
+    // one allocation, every table 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_f32 = 0, o_d32 = o_f32 + up(nr * 16), o_p32 = o_d32 + up(2 * nr * 16);
+    const size_t o_F32 = o_p32 + up(nr * 16), o_f64 = o_F32 + up(nF * 16);
+    const size_t o_p64 = o_f64 + up(nr * 32), o_F64 = o_p64 + up(nr * 32);
+    const size_t total = o_F64 + up(nF * 32);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc (EAM tables)");
+    c->eam_allocs.push_back(base);
+    char* b = static_cast<char*>(base);
+    const struct {
+      size_t off;
+      const void* src;
+      size_t bytes;
+    } parts[] = {{o_f32, f32.data(), nr * 16},     {o_d32, d32.data(), 2 * nr * 16},
+                 {o_p32, p32.data(), nr * 16},     {o_F32, F32.data(), nF * 16},
+                 {o_f64, cf.data(), nr * 32},      {o_p64, cp.data(), nr * 32},
+                 {o_F64, cF.data(), nF * 32}};
+    for (const auto& q : parts)
+      TB_CUDA(c, cudaMemcpyAsync(b + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, c->stream));
+    TB_CUDA(c, cudaStreamSynchronize(c->stream));  // the host staging vectors go out of scope
+    EamDev& d = c->eam;
+    d.f32 = reinterpret_cast<const float4*>(b + o_f32);
+    d.d32 = reinterpret_cast<const float4*>(b + o_d32);
+    d.p32 = reinterpret_cast<const float4*>(b + o_p32);
+    d.F32 = reinterpret_cast<const float4*>(b + o_F32);
+    d.f64 = reinterpret_cast<const double*>(b + o_f64);
+    d.p64 = reinterpret_cast<const double*>(b + o_p64);
+    d.F64 = reinterpret_cast<const double*>(b + o_F64);
+    const double ifx = idr / kFixedScale;  // per fixed-point unit of r
+    d.inv_dr_hi = (float)ifx;
+    d.inv_dr_lo = (float)(ifx - (double)d.inv_dr_hi);
+    const double irho = 1.0 / t->d_rho;
+    d.inv_drho_hi = (float)irho;
+    d.inv_drho_lo = (float)(irho - (double)d.inv_drho_hi);
+    d.kmax_r = t->n_r - 2;
+    d.kmax_rho = t->n_rho - 2;
+    d.inv_dr = idr;
+    d.inv_drho = irho;
+    c->eam_on = true;
+  }
+  TB_TRY(refresh(c, 0));
+  TB_TRY(launch_pair<false>(c, c->stream, c->prec));
+  return TBSMA_OK;
+}
+
 tbsma_status tbsma_get_barostat(tbsma_ctx* c, double* lambda, double* zeta) {
   if (!c) return TBSMA_EINVAL;
   std::vector<BaroState> b(c->W);
@@ -1027,6 +1163,7 @@ void tbsma_destroy(tbsma_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
   for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->eam_allocs) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }

@@ -115,6 +115,14 @@ class WireStateC(ctypes.Structure):
                 ("status", ctypes.c_uint32)]
 
 
+class EamC(ctypes.Structure):
+    """tbsma_eam (include/tbsma.h)."""
+
+    _fields_ = [("F", ctypes.c_void_p), ("n_rho", ctypes.c_int32), ("d_rho", ctypes.c_double),
+                ("f", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("n_r", ctypes.c_int32),
+                ("d_r", ctypes.c_double)]
+
+
 THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
 BARO_MODULUS = 100.0 / 160.21766208  # 100 GPa in eV/A^3: the barostat's reference modulus
 PULLS = {"continuous": 0, "stepwise": 1}
@@ -139,6 +147,7 @@ SIGNATURES = [
     ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_get_barostat", ctypes.c_int, [_P, _P, _P]),
+    ("tbsma_set_eam", ctypes.c_int, [_P, _P]),
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -341,6 +350,23 @@ class Engine:
                              ramp_steps=int(ramp_steps), baro_tau_fs=baro_tau_fs,
                              baro_modulus=baro_modulus, baro_pressure=baro_pressure,
                              baro_drag=baro_drag, ramp_start=int(ramp_start))
+
+    def set_eam(self, F=None, d_rho: float = 0.0, f=None, phi=None, d_r: float = 0.0,
+                r_cut: float | None = None):
+        """Tabulated EAM (tbsma_set_eam): F sampled at k d_rho, f and phi at
+        k d_r; F=None returns to TB-SMA.  Pairs interact within the context's
+        r_cut (params); a table set's own r_cut, if given, must equal it."""
+        if r_cut is not None and r_cut != self.params.r_cut:
+            raise ValueError(f"the tables' r_cut {r_cut} differs from the context's {self.params.r_cut}")
+        if F is None:
+            self._check(lib().tbsma_set_eam(self.ctx, None), "tbsma_set_eam")
+            return
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (F, f, phi)]
+        if keep[1].size != keep[2].size:
+            raise ValueError("f and phi need the same number of samples")
+        t = EamC(keep[0].ctypes.data, keep[0].size, float(d_rho), keep[1].ctypes.data,
+                 keep[2].ctypes.data, keep[1].size, float(d_r))
+        self._check(lib().tbsma_set_eam(self.ctx, ctypes.byref(t)), "tbsma_set_eam")
 
     def thermostat(self):
         """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""

@@ -43,6 +43,21 @@ def test_roofline_bound_and_fraction():
     assert math.isclose(h["frac"], h["hbm_frac"], rel_tol=1e-12)
 
 
+def test_eam_roofline_and_tables():
+    """--potential eam: 25 FP32 instructions and one MUFU op per in-cutoff
+    entry; the Au tables cover r_cut and sample the TB-SMA functions."""
+    N, n_c, n_s, sms, mhz = 4463360, 44.87, 0.82, 148, 2032.0
+    r = bench.roofline_of(N, n_c, n_s, 0.30, sms, mhz, 6503.7, per_in=bench.EAM_PER_IN)
+    assert r["bound"] == "alu" and r["unit"] == "T FP32-inst/s"
+    assert math.isclose(r["roofline_ms"], 1e3 * N * (25 * n_c + 7 * n_s) / (128 * sms * mhz * 1e6),
+                        rel_tol=1e-12)
+    t = bench.au_eam_tables()
+    assert (t["f"].size - 1) * t["d_r"] >= 5.8 and t["f"].size == t["phi"].size
+    k = int(round(2.884 / t["d_r"]))
+    assert math.isclose(t["f"][k], 1.790 ** 2 * math.exp(-2 * 4.036 * (k * t["d_r"] / 2.884 - 1)))
+    assert t["F"][0] == 0.0 and math.isclose(t["F"][-1], -math.sqrt((t["F"].size - 1) * t["d_rho"]))
+
+
 def test_workload_atoms_matches_the_built_batch():
     from inputs.configs import WORKLOADS, build
 
