@@ -139,7 +139,8 @@ struct PairConsts {
 struct EamDev {
   const float4* f32;   // [n_r - 1] value coefficients of f (density pass)
   const float4* d32;   // [2 (n_r - 1)] per interval {f'0, f'1, f'2, phi'0}, {phi'1, phi'2, 0, 0},
-                       // derivative coefficients per A: f'(t) = f'0 + t (f'1 + t f'2)
+                       // derivative coefficients per A: f'(t) = f'0 + t (f'1 + t f'2);
+                       // 32-byte records, 32-byte aligned (read with one 256-bit load)
   const float4* p32;   // [n_r - 1] value coefficients of phi (pair energy)
   const float4* F32;   // [n_rho - 1] value coefficients of F (embedding slope)
   const double* f64;   // [4 (n_r - 1)] value coefficients of f, c0..c3 per interval
