@@ -16,6 +16,9 @@
  *           gripping layers per end pulled apart along [100].
  *   Eq. 4   strain = (L - L0)/L0;  Eq. 5  virial stress sigma_xx.
  *   Results "TB-SMA benchmarks": Verlet list with a buffer (skin) radius.
+ *   Introduction: the two-stage force follows the EAM implementation the
+ *           paper cites; tbsma_set_eam runs a tabulated EAM through the
+ *           same two passes.
  *
  * Units: Angstrom, eV, amu, fs.  Strain rate in 1/s, temperature in K,
  * Langevin friction gamma in 1/fs.
