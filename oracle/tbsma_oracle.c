@@ -24,6 +24,9 @@
  *               (r_i - r_j) / r_ij
  * with phi = A exp(-p s), g = xi^2 exp(-2 q s), s = r/r0 - 1.  The two passes
  * (density, then force) follow the paper's two-kernel scheme.
+ *
+ * The last section holds a tabulated EAM (the general form of that scheme)
+ * on the same pair sets: or_eam_interp, or_eam_on_pairs, or_eam_energy_forces.
  */
 
 #include <math.h>
