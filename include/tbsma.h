@@ -336,6 +336,14 @@ typedef struct {
  * non-finite sample, (n_r - 1) d_r < r_cut), ENOMEM, ECUDA. */
 tbsma_status tbsma_set_eam(tbsma_ctx* ctx, const tbsma_eam* tables);
 
+/* The interpolant tbsma_set_eam builds from one sample table, as cubic
+ * coefficients per interval (host only: no context, no GPU): for interval
+ * k = 0 .. n-2, with t = s/h - k, y(t) = c[4k] + t (c[4k+1] + t (c[4k+2] +
+ * t c[4k+3])) in units of y per grid step (divide derivatives in t by h).
+ * samples: n doubles (host); coeffs: 4 (n - 1) doubles (host, caller-owned).
+ * Errors: EINVAL (null pointers, n < 3 or > 2^22). */
+tbsma_status tbsma_eam_cubics(const double* samples, int32_t n, double* coeffs);
+
 /* Checkpoint / resume.  A wire's counters: grip displacement (A), the
  * Nosé–Hoover state, the barostat's log-stretch and strain rate, the number
  * of list rebuilds and its status word. */

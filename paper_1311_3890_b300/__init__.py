@@ -12,6 +12,7 @@ from .tbsma import (  # noqa: F401
     Engine,
     TbsmaError,
     au_params,
+    eam_cubics,
     lib,
     normals,
     philox4x32_10,

@@ -29,6 +29,7 @@ constexpr int kGraphChunk = 50;  // steps per captured graph
 constexpr int kMinCap = 64;   // neighbour-list row length, bounds (list_capacity)
 constexpr int kMaxCap = 128;
 constexpr int kMaxWindow = 4096; // largest shared-memory window of a pair-pass tile, atoms
+constexpr int kMaxEamSamples = 1 << 22;  // samples per EAM table
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
@@ -894,9 +895,16 @@ tbsma_status tbsma_set_protocol(tbsma_ctx* c, const tbsma_protocol* p) {
   return TBSMA_OK;
 }
 
+tbsma_status tbsma_eam_cubics(const double* y, int32_t n, double* coeffs) {
+  if (!y || !coeffs || n < 3 || n > kMaxEamSamples) return TBSMA_EINVAL;
+  const std::vector<double> c = hermite_cubics(y, n);
+  std::copy(c.begin(), c.end(), coeffs);
+  return TBSMA_OK;
+}
+
 tbsma_status tbsma_set_eam(tbsma_ctx* c, const tbsma_eam* t) {
   if (!c) return TBSMA_EINVAL;
-  constexpr int kMaxSamples = 1 << 22;
+  constexpr int kMaxSamples = kMaxEamSamples;
   if (t) {
     if (!t->F || !t->f || !t->phi) return fail(c, TBSMA_EINVAL, "null EAM table");
     if (t->n_rho < 3 || t->n_r < 3 || t->n_rho > kMaxSamples || t->n_r > kMaxSamples)

@@ -148,6 +148,7 @@ SIGNATURES = [
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_get_barostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_eam", ctypes.c_int, [_P, _P]),
+    ("tbsma_eam_cubics", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -465,6 +466,17 @@ class Engine:
 
     def velocities(self) -> np.ndarray:
         return self.v.view(3, self.N).T.cpu().numpy()
+
+
+def eam_cubics(samples) -> np.ndarray:
+    """The per-interval cubic coefficients (n-1, 4) tbsma_set_eam derives
+    from a sample table (host only; tbsma_eam_cubics)."""
+    y = np.ascontiguousarray(samples, dtype=np.float64)
+    out = np.empty((max(y.size - 1, 0), 4))
+    st = lib().tbsma_eam_cubics(_hptr(y), y.size, _hptr(out))
+    if st != 0:
+        raise TbsmaError(st, "tbsma_eam_cubics")
+    return out
 
 
 def philox4x32_10(ctr, key, stream=None):
