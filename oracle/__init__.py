@@ -18,7 +18,10 @@ for the topology.  The tabulated EAM (tests/test_oracle_eam.py): exactness
 for quadratics and the third-order error of its interpolant, closed-form
 dimer and trimer energies and forces, the linear continuation of the
 embedding, TB-SMA itself when the tables sample Eq. 1-2, finite
-differences and invariances.
+differences and invariances; its MD and stress (EamPotential,
+tests/test_oracle_eam_md.py): a velocity-Verlet loop over its forces, the
+strain derivative of its energy, O(dt^2) energy conservation with a smooth
+table, and the TB-SMA trajectory when the tables sample Eq. 1-2.
 """
 
 from __future__ import annotations
@@ -56,7 +59,8 @@ def lib():
 
 
 class _Pot(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_double) for k in ("A", "xi", "p", "q", "r0", "r_cut")]
+    _fields_ = [(k, ctypes.c_double) for k in ("A", "xi", "p", "q", "r0", "r_cut")] + [
+        ("eam", ctypes.c_void_p)]
 
 
 class _Md(ctypes.Structure):
@@ -154,7 +158,7 @@ class Potential:
     r_cut: float = 5.8
 
     def _c(self):
-        return _Pot(self.A, self.xi, self.p, self.q, self.r0, self.r_cut)
+        return _Pot(self.A, self.xi, self.p, self.q, self.r0, self.r_cut, None)
 
 
 AU = Potential()
@@ -227,7 +231,9 @@ def energy(x: np.ndarray, pot: Potential = AU, brute_max: int = 2000) -> float:
 
 
 def tbsma_on_pairs(x, start, nbr, pot: Potential = AU) -> Forces:
-    """Eq. 1-3 on a caller-given pair set."""
+    """Eq. 1-3 on a caller-given pair set (an EamPotential: its EAM)."""
+    if isinstance(pot, EamPotential):
+        return eam_on_pairs(x, start, nbr, pot.tab)
     x = _f64(x)
     n = x.shape[0]
     start = np.ascontiguousarray(start, dtype=np.int32)
@@ -543,6 +549,20 @@ class EamTables:
         return _Eam(self._keep[0].ctypes.data, self._keep[0].size, self.d_rho,
                     self._keep[1].ctypes.data, self._keep[2].ctypes.data, self._keep[1].size,
                     self.d_r, self.r_cut)
+
+
+class EamPotential:
+    """A tabulated EAM in place of TB-SMA for every oracle function that takes
+    a potential (md_steps, md_batch, md_steps_protocol, observables, ...):
+    pairs within tab.r_cut; r0 only sets the hard-sphere volume of Eq. 5."""
+
+    def __init__(self, tab: EamTables, r0: float = AU.r0):
+        self.tab, self.r0, self.r_cut = tab, r0, tab.r_cut
+
+    def _c(self):
+        self._e = self.tab._c()  # kept alive with the struct that points to it
+        return _Pot(0.0, 0.0, 0.0, 0.0, self.r0, self.r_cut,
+                    ctypes.cast(ctypes.pointer(self._e), ctypes.c_void_p))
 
 
 def eam_interp(y: np.ndarray, h: float, s) -> tuple[np.ndarray, np.ndarray]:

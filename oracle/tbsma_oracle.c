@@ -45,8 +45,24 @@
 /* 1 amu*A^2/fs^2 expressed in eV: amu * 1e-20 m^2 / 1e-30 s^2 / eV */
 #define OR_MVV2E (OR_AMU_KG * 1.0e10 / OR_EV_J)
 
+/* Tabulated EAM functions (see the last section). */
+typedef struct {
+  const double* F;   /* n_rho samples of F(rho), eV */
+  int n_rho;
+  double d_rho;
+  const double* f;   /* n_r samples of f(r) */
+  const double* phi; /* n_r samples of phi(r), eV */
+  int n_r;
+  double d_r;
+  double r_cut;
+} or_eam;
+
+/* The potential: TB-SMA (Eq. 1-3) with these parameters, or, when eam is
+ * not NULL, the tabulated EAM it points to (pairs within eam->r_cut; r0 then
+ * only sets the hard-sphere volume of Eq. 5). */
 typedef struct {
   double A, xi, p, q, r0, r_cut;
+  const or_eam* eam;
 } or_pot;
 
 typedef struct {
@@ -238,10 +254,16 @@ double or_tbsma(const or_pot* P, int n, const double* x, const int* start, const
   return E;
 }
 
-/* Convenience: pair set (brute force if n <= brute_max, else cells) + Eq. 1-3. */
+double or_eam_energy_forces(const or_eam* T, int n, const double* x, int brute_max, double* F,
+                            double* rho, double* eB, double* eR, double* w, double* S,
+                            long* n_pairs_out);
+
+/* Convenience: pair set (brute force if n <= brute_max, else cells) + Eq. 1-3
+ * (or the tabulated EAM when P->eam is set). */
 double or_energy_forces(const or_pot* P, int n, const double* x, int brute_max, double* F,
                         double* rho, double* eB, double* eR, double* w, double* S,
                         long* n_pairs_out) {
+  if (P->eam) return or_eam_energy_forces(P->eam, n, x, brute_max, F, rho, eB, eR, w, S, n_pairs_out);
   long cap = 64L * n + 64;
   int* start = (int*)malloc(sizeof(int) * (n + 1));
   int* nbr = NULL;
@@ -855,17 +877,6 @@ void or_observables(const or_pot* P, const or_md* M, const or_wire* W, int n, co
  * Beyond the last sample (or below 0) a function continues as the straight
  * line through its end sample with its end slope.
  * ==================================================================== */
-typedef struct {
-  const double* F;   /* n_rho samples of F(rho), eV */
-  int n_rho;
-  double d_rho;
-  const double* f;   /* n_r samples of f(r) */
-  const double* phi; /* n_r samples of phi(r), eV */
-  int n_r;
-  double d_r;
-  double r_cut;
-} or_eam;
-
 static double node_slope(const double* y, int n, double h, int k) {
   if (k == 0) return (-3.0 * y[0] + 4.0 * y[1] - y[2]) / (2.0 * h);
   if (k == n - 1) return (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) / (2.0 * h);
