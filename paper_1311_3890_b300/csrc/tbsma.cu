@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tbsma.h"
 #include "device.cuh"
 #include "md.cuh"
@@ -26,6 +28,16 @@ using namespace tbsma;
 namespace {
 
 constexpr int kGraphChunk = 50;  // steps per captured graph
+
+// An NVTX range over one library call, for timeline tools (nsys): the
+// header-only NVTX3 API does nothing unless a tool is attached.  Inside the
+// step graphs the kernels' own names mark the phases.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 constexpr int kMinCap = 64;   // neighbour-list row length, bounds (list_capacity)
 constexpr int kMaxCap = 128;
 constexpr int kMaxWindow = 4096; // largest shared-memory window of a pair-pass tile, atoms
@@ -474,6 +486,7 @@ tbsma_status set_dt(tbsma_ctx* c, double dt) {
 }
 
 tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
+  NvtxRange range_("capture step graph");
   drop_graph(c);
   cudaGraph_t g = nullptr;
   TB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -531,6 +544,7 @@ extern "C" {
 tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, int32_t n_wires,
                         const tbsma_wire* wires, double* x, double* v, const uint8_t* kind,
                         void* cuda_stream, tbsma_ctx** out) {
+  NvtxRange range_("tbsma_init");
   if (!out) return TBSMA_EINVAL;
   *out = nullptr;
   if (!params || !wires || !x || !v || !kind || n_wires < 1) return TBSMA_EINVAL;
@@ -720,6 +734,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
 }
 
 tbsma_status tbsma_init_velocities(tbsma_ctx* c) {
+  NvtxRange range_("tbsma_init_velocities");
   if (!c) return TBSMA_EINVAL;
   k_init_velocities<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->meta, c->N, c->v,
                                                                   c->P.mass * kMvv2e);
@@ -728,6 +743,7 @@ tbsma_status tbsma_init_velocities(tbsma_ctx* c) {
 }
 
 tbsma_status tbsma_build_neighbors(tbsma_ctx* c, int32_t force_all, int32_t* n_rebuilt) {
+  NvtxRange range_("tbsma_build_neighbors");
   if (!c) return TBSMA_EINVAL;
   TB_TRY(refresh(c, force_all ? 1 : 0));
   if (n_rebuilt) {
@@ -740,6 +756,7 @@ tbsma_status tbsma_build_neighbors(tbsma_ctx* c, int32_t force_all, int32_t* n_r
 }
 
 tbsma_status tbsma_compute_forces(tbsma_ctx* c, float* f32_out, double* f64_out) {
+  NvtxRange range_("tbsma_compute_forces");
   if (!c) return TBSMA_EINVAL;
   TB_TRY(refresh(c, 0));
   const int other = c->prec == TBSMA_MIXED ? TBSMA_FP64 : TBSMA_MIXED;
@@ -755,6 +772,7 @@ tbsma_status tbsma_compute_forces(tbsma_ctx* c, float* f32_out, double* f64_out)
 }
 
 tbsma_status tbsma_atom_energies(tbsma_ctx* c, double* e_out, double* w_out) {
+  NvtxRange range_("tbsma_atom_energies");
   if (!c) return TBSMA_EINVAL;
   TB_TRY(refresh(c, 0));
   TB_TRY(launch_pair<true>(c, c->stream, c->prec));
@@ -766,6 +784,7 @@ tbsma_status tbsma_atom_energies(tbsma_ctx* c, double* e_out, double* w_out) {
 }
 
 tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
+  NvtxRange range_("tbsma_step_nvt_pull");
   if (!c) return TBSMA_EINVAL;
   if (n_steps < 0 || !(dt_fs > 0.0)) return fail(c, TBSMA_EINVAL, "n_steps < 0 or dt <= 0");
   if (n_steps == 0) return TBSMA_OK;
@@ -783,6 +802,7 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
 }
 
 tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
+  NvtxRange range_("tbsma_reduce_observables");
   if (!c || !out) return TBSMA_EINVAL;
   TB_TRY(refresh(c, 0));
   TB_TRY(launch_pair<true>(c, c->stream, c->prec));
@@ -798,6 +818,7 @@ tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
 }
 
 tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
+  NvtxRange range_("tbsma_force_check");
   if (!c || !out) return TBSMA_EINVAL;
   TB_TRY(refresh(c, 0));
   TB_TRY(launch_pair<false>(c, c->stream, TBSMA_MIXED));
@@ -812,6 +833,7 @@ tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
 }
 
 tbsma_status tbsma_upload_state(tbsma_ctx* c, const double* x_host, const double* v_host) {
+  NvtxRange range_("tbsma_upload_state");
   if (!c) return TBSMA_EINVAL;
   const size_t bytes = 3 * (size_t)c->N * sizeof(double);
   if (x_host) TB_CUDA(c, cudaMemcpyAsync(c->x, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -824,6 +846,7 @@ tbsma_status tbsma_upload_state(tbsma_ctx* c, const double* x_host, const double
 }
 
 tbsma_status tbsma_download_state(tbsma_ctx* c, double* x_host, double* v_host) {
+  NvtxRange range_("tbsma_download_state");
   if (!c) return TBSMA_EINVAL;
   const size_t bytes = 3 * (size_t)c->N * sizeof(double);
   if (x_host) TB_CUDA(c, cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -903,6 +926,7 @@ tbsma_status tbsma_eam_cubics(const double* y, int32_t n, double* coeffs) {
 }
 
 tbsma_status tbsma_set_eam(tbsma_ctx* c, const tbsma_eam* t) {
+  NvtxRange range_("tbsma_set_eam");
   if (!c) return TBSMA_EINVAL;
   constexpr int kMaxSamples = kMaxEamSamples;
   if (t) {
@@ -1020,6 +1044,7 @@ tbsma_status tbsma_get_thermostat(tbsma_ctx* c, double* xi, double* eta) {
 }
 
 tbsma_status tbsma_wire_topology(tbsma_ctx* c, tbsma_topology* out, int32_t* labels) {
+  NvtxRange range_("tbsma_wire_topology");
   if (!c || !out) return TBSMA_EINVAL;
   if (!c->uf_parent) {
     if (alloc(c, &c->uf_parent, c->N) != TBSMA_OK || alloc(c, &c->uf_err, 1) != TBSMA_OK ||
@@ -1074,6 +1099,7 @@ tbsma_status rebuild_all(tbsma_ctx* c) {
 
 tbsma_status tbsma_save_state(tbsma_ctx* c, double* x_host, double* v_host,
                               tbsma_wire_state* wires, int64_t* step) {
+  NvtxRange range_("tbsma_save_state");
   if (!c || !x_host || !v_host || !wires || !step) return TBSMA_EINVAL;
   TB_TRY(rebuild_all(c));
   const size_t bytes = 3 * (size_t)c->N * sizeof(double);
@@ -1108,6 +1134,7 @@ tbsma_status tbsma_save_state(tbsma_ctx* c, double* x_host, double* v_host,
 
 tbsma_status tbsma_restore_state(tbsma_ctx* c, const double* x_host, const double* v_host,
                                  const tbsma_wire_state* wires, int64_t step) {
+  NvtxRange range_("tbsma_restore_state");
   if (!c || !x_host || !v_host || !wires || step < 0) return TBSMA_EINVAL;
   const size_t bytes = 3 * (size_t)c->N * sizeof(double);
   std::vector<double> dg(c->W);
@@ -1137,6 +1164,7 @@ tbsma_status tbsma_restore_state(tbsma_ctx* c, const double* x_host, const doubl
 }
 
 tbsma_status tbsma_run_pass(tbsma_ctx* c, int32_t pass, int32_t reps) {
+  NvtxRange range_("tbsma_run_pass");
   if (!c || (pass != 1 && pass != 2) || reps < 1) return TBSMA_EINVAL;
   for (int r = 0; r < reps; ++r) TB_TRY(launch_one_pass(c, c->stream, pass));
   return TBSMA_OK;
