@@ -64,7 +64,7 @@ def parse():
                    help="skip the cpu baseline, fp64 comparison and e2e legs")
     p.add_argument("--potential", default="tbsma", choices=["tbsma", "eam"],
                    help="eam: the tabulated-EAM pair passes (tbsma_set_eam) on Au tables that "
-                        "sample the TB-SMA functions; device-timed line only (no extras)")
+                        "sample the TB-SMA functions (every leg, the oracle's included)")
     p.add_argument("--table2", action="store_true",
                    help="context: steps/s of the paper's Table 2 wires, each alone, 10 and 298 K")
     return p.parse_args()
@@ -136,11 +136,14 @@ class Clocks:
 
 
 # --------------------------------------------------------- CPU oracle leg
-def oracle_sample(batch, budget_s: float, steps: int | None = None):
-    """Time the FP64 oracle on the first wires of the batch, one per thread.
+def oracle_sample(batch, budget_s: float, steps: int | None = None, eam: bool = False):
+    """Time the FP64 oracle on the first wires of the batch, one per thread
+    (eam: with the Au EAM tables of au_eam_tables in place of TB-SMA).
 
     Returns (atom-steps/s, threads used, description, atoms, steps)."""
     import oracle
+
+    kw = {"pot": oracle.EamPotential(oracle.EamTables(**au_eam_tables(), r_cut=5.8))} if eam else {}
 
     threads = oracle.max_threads()
     W = min(threads, batch.n_wires)
@@ -150,23 +153,29 @@ def oracle_sample(batch, budget_s: float, steps: int | None = None):
     v = np.zeros_like(x)
     args = (batch.kind[:N], batch.offset[:W], n, batch.L0[:W], batch.strain_rate[:W],
             batch.temperature[:W], batch.gamma[:W], batch.seed[:W])
-    F, xb, dg, nr = oracle.md_batch(x, v, *args, 0, 1, 2.0, brute_max=0)  # includes first forces
+    F, xb, dg, nr = oracle.md_batch(x, v, *args, 0, 1, 2.0, brute_max=0, **kw)  # includes first forces
     t = time.perf_counter()
-    oracle.md_batch(x, v, *args, 1, 1, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg, n_rebuild=nr)
+    oracle.md_batch(x, v, *args, 1, 1, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg, n_rebuild=nr,
+                    **kw)
     per_step = time.perf_counter() - t
     if steps is None:
         steps = int(max(2, min(500, budget_s / max(per_step, 1e-6))))
     t = time.perf_counter()
     oracle.md_batch(x, v, *args, 2, steps, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg,
-                    n_rebuild=nr)
+                    n_rebuild=nr, **kw)
     el = time.perf_counter() - t
     desc = f"{W} of {batch.n_wires} wires ({N} atoms, one per thread) x {steps} MD steps"
+    if eam:
+        desc += ", tabulated EAM"
     return N * steps / el, W, desc, N, steps
 
 
-def _oracle_run(batch, first_step: int, steps: int, state=None):
-    """Run the FP64 oracle on a batch (one wire per host thread); returns the state."""
+def _oracle_run(batch, first_step: int, steps: int, state=None, eam: bool = False):
+    """Run the FP64 oracle on a batch (one wire per host thread; eam: with the
+    Au EAM tables of au_eam_tables); returns the state."""
     import oracle
+
+    kw = {"pot": oracle.EamPotential(oracle.EamTables(**au_eam_tables(), r_cut=5.8))} if eam else {}
 
     N = int(batch.n.sum())
     W = len(batch.n)
@@ -178,11 +187,11 @@ def _oracle_run(batch, first_step: int, steps: int, state=None):
             s = slice(int(batch.offset[w]), int(batch.offset[w]) + int(batch.n[w]))
             v[s] = oracle.init_velocities(batch.kind[s], int(batch.seed[w]),
                                           float(batch.temperature[w]))
-        F, xb, dg, nr = oracle.md_batch(x, v, *a, 0, 0, 2.0, brute_max=0)
+        F, xb, dg, nr = oracle.md_batch(x, v, *a, 0, 0, 2.0, brute_max=0, **kw)
         state = (x, v, F, xb, dg, nr)
     x, v, F, xb, dg, nr = state
     oracle.md_batch(x, v, *a, first_step, steps, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg,
-                    n_rebuild=nr)
+                    n_rebuild=nr, **kw)
     return state
 
 
@@ -206,10 +215,11 @@ def run_reference(args):
     total = args.steps + args.warmup
     budget_s = 120.0
     # one step of the first wire, alone, sizes the sample
+    eam = args.potential == "eam"
     one = build(specs[:1])
-    st = _oracle_run(one, 0, 1)
+    st = _oracle_run(one, 0, 1, eam=eam)
     t = time.perf_counter()
-    _oracle_run(one, 1, 2, st)
+    _oracle_run(one, 1, 2, st, eam=eam)
     t_wire = (time.perf_counter() - t) / 2
     if total * t_wire <= budget_s:
         sample_specs = specs[: min(threads, len(specs))]
@@ -228,9 +238,9 @@ def run_reference(args):
                   f"steps fit ~{budget_s:.0f} s), one per host thread")
     sub = build(sample_specs)
     N = int(sub.n.sum())
-    st = _oracle_run(sub, 0, max(1, args.warmup))
+    st = _oracle_run(sub, 0, max(1, args.warmup), eam=eam)
     t = time.perf_counter()
-    _oracle_run(sub, max(1, args.warmup), args.steps, st)
+    _oracle_run(sub, max(1, args.warmup), args.steps, st, eam=eam)
     el = time.perf_counter() - t
     value = N * args.steps / el
     line = {
@@ -242,6 +252,7 @@ def run_reference(args):
                    "atoms_per_gpu": _workload_atoms(specs), "dt_fs": 2.0,
                    "temperature_K": specs[0].temperature, "strain_rate_per_s": specs[0].strain_rate,
                    "precision": "fp64 (oracle)", "observables_every": None,
+                   "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
                    "l2": "host", "parallelism": f"{len(sample_specs)} host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(sample_specs),
                          "kind": "oracle", "sample": f"{sample}; {N} atoms"},
@@ -484,7 +495,7 @@ def run_ours(args):
         "rebuilds_per_wire": float(ob["n_rebuilds"].mean()),
     }
 
-    if not args.no_extras and not eam and rank == 0:
+    if not args.no_extras and rank == 0:
         # end to end through the public API: pinned host state in, K steps in
         # segments, per-wire observables and state out every segment
         seg = max(1, min(args.e2e_seg, args.steps))
@@ -515,6 +526,8 @@ def run_ours(args):
                              length_nm=40.0, L0=float(batch.L0[w]), temperature=10.0,
                              strain_rate=1e8, gamma=float(batch.gamma[w]), seed=int(batch.seed[w]))])
             e1 = tb.Engine(one, precision="fp64", params=params)
+            if eam:
+                e1.set_eam(**au_eam_tables())
             e1.set_launch(64, 0)  # one 17k-atom wire: small tiles to occupy every SM
             e1.init_velocities()
             e1.step(5, 2.0)
@@ -530,7 +543,7 @@ def run_ours(args):
             "value": tot_as / (tot_ms / 1e3), "unit": UNIT,
             "sample": "8 of the 256 wires, each alone in its own context, 20 steps"}
         if world == 1:
-            v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0)
+            v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0, eam=eam)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": desc}
     eng.close()

@@ -58,6 +58,15 @@ def test_eam_roofline_and_tables():
     assert t["F"][0] == 0.0 and math.isclose(t["F"][-1], -math.sqrt((t["F"].size - 1) * t["d_rho"]))
 
 
+def test_oracle_sample_runs_the_eam(orc):
+    """The cpu_baseline leg of --potential eam times the oracle's EAM MD."""
+    from inputs import workload
+
+    b = workload("tiny_batch")
+    v, cores, desc, n, steps = bench.oracle_sample(b, budget_s=0.1, steps=2, eam=True)
+    assert v > 0 and steps == 2 and "EAM" in desc and n == b.n[:cores].sum()
+
+
 def test_workload_atoms_matches_the_built_batch():
     from inputs.configs import WORKLOADS, build
 
