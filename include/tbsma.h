@@ -333,7 +333,8 @@ typedef struct {
  * tbsma_reduce_observables) are FP64 sums.  A checkpoint holds no tables:
  * set the same tables before tbsma_restore_state.  Errors: EINVAL (null
  * arrays, n_rho or n_r < 3 or > 2^22, spacings not positive and finite, a
- * non-finite sample, (n_r - 1) d_r < r_cut), ENOMEM, ECUDA. */
+ * non-finite sample, (n_r - 1) d_r < r_cut: nothing changed), ENOMEM or
+ * ECUDA (the earlier tables are gone: the context is left on TB-SMA). */
 tbsma_status tbsma_set_eam(tbsma_ctx* ctx, const tbsma_eam* tables);
 
 /* The interpolant tbsma_set_eam builds from one sample table, as cubic
