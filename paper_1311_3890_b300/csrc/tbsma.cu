@@ -536,6 +536,71 @@ tbsma_status refresh(tbsma_ctx* c, int force_all) {
   return TBSMA_OK;
 }
 
+// Upload validated EAM tables (tbsma_set_eam) and switch the context to them;
+// on an error the context keeps eam_on = false.
+tbsma_status upload_eam(tbsma_ctx* c, const tbsma_eam* t) {
+  const std::vector<double> cf = hermite_cubics(t->f, t->n_r);
+  const std::vector<double> cp = hermite_cubics(t->phi, t->n_r);
+  const std::vector<double> cF = hermite_cubics(t->F, t->n_rho);
+  const size_t nr = (size_t)t->n_r - 1, nF = (size_t)t->n_rho - 1;
+  std::vector<float4> f32(nr), d32(2 * nr), p32(nr), F32(nF);
+  const double idr = 1.0 / t->d_r;
+  for (size_t k = 0; k < nr; ++k) {
+    const double* a = &cf[4 * k];
+    const double* b = &cp[4 * k];
+    f32[k] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+    p32[k] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
+    d32[2 * k] = make_float4((float)(a[1] * idr), (float)(2.0 * a[2] * idr), (float)(3.0 * a[3] * idr),
+                             (float)(b[1] * idr));
+    d32[2 * k + 1] = make_float4((float)(2.0 * b[2] * idr), (float)(3.0 * b[3] * idr), 0.f, 0.f);
+  }
+  for (size_t k = 0; k < nF; ++k)
+    F32[k] = make_float4((float)cF[4 * k], (float)cF[4 * k + 1], (float)cF[4 * k + 2],
+                         (float)cF[4 * k + 3]);
+  // one allocation, every table 256-byte aligned
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_f32 = 0, o_d32 = o_f32 + up(nr * 16), o_p32 = o_d32 + up(2 * nr * 16);
+  const size_t o_F32 = o_p32 + up(nr * 16), o_f64 = o_F32 + up(nF * 16);
+  const size_t o_p64 = o_f64 + up(nr * 32), o_F64 = o_p64 + up(nr * 32);
+  const size_t total = o_F64 + up(nF * 32);
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc (EAM tables)");
+  c->eam_allocs.push_back(base);
+  char* b = static_cast<char*>(base);
+  const struct {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  } parts[] = {{o_f32, f32.data(), nr * 16},     {o_d32, d32.data(), 2 * nr * 16},
+               {o_p32, p32.data(), nr * 16},     {o_F32, F32.data(), nF * 16},
+               {o_f64, cf.data(), nr * 32},      {o_p64, cp.data(), nr * 32},
+               {o_F64, cF.data(), nF * 32}};
+  for (const auto& q : parts)
+    TB_CUDA(c, cudaMemcpyAsync(b + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));  // the host staging vectors go out of scope
+  EamDev& d = c->eam;
+  d.f32 = reinterpret_cast<const float4*>(b + o_f32);
+  d.d32 = reinterpret_cast<const float4*>(b + o_d32);
+  d.p32 = reinterpret_cast<const float4*>(b + o_p32);
+  d.F32 = reinterpret_cast<const float4*>(b + o_F32);
+  d.f64 = reinterpret_cast<const double*>(b + o_f64);
+  d.p64 = reinterpret_cast<const double*>(b + o_p64);
+  d.F64 = reinterpret_cast<const double*>(b + o_F64);
+  const double ifx = idr / kFixedScale;  // per fixed-point unit of r
+  d.inv_dr_hi = (float)ifx;
+  d.inv_dr_lo = (float)(ifx - (double)d.inv_dr_hi);
+  const double irho = 1.0 / t->d_rho;
+  d.inv_drho_hi = (float)irho;
+  d.inv_drho_lo = (float)(irho - (double)d.inv_drho_hi);
+  d.kmax_r = t->n_r - 2;
+  d.kmax_rho = t->n_rho - 2;
+  d.inv_dr = idr;
+  d.inv_drho = irho;
+  c->eam_on = true;
+  return TBSMA_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -951,65 +1016,14 @@ tbsma_status tbsma_set_eam(tbsma_ctx* c, const tbsma_eam* t) {
   c->eam = EamDev{};
   c->eam_on = false;
   if (t) {
-    const std::vector<double> cf = hermite_cubics(t->f, t->n_r);
-    const std::vector<double> cp = hermite_cubics(t->phi, t->n_r);
-    const std::vector<double> cF = hermite_cubics(t->F, t->n_rho);
-    const size_t nr = (size_t)t->n_r - 1, nF = (size_t)t->n_rho - 1;
-    std::vector<float4> f32(nr), d32(2 * nr), p32(nr), F32(nF);
-    const double idr = 1.0 / t->d_r;
-    for (size_t k = 0; k < nr; ++k) {
-      const double* a = &cf[4 * k];
-      const double* b = &cp[4 * k];
-      f32[k] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
-      p32[k] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
-      d32[2 * k] = make_float4((float)(a[1] * idr), (float)(2.0 * a[2] * idr), (float)(3.0 * a[3] * idr),
-                               (float)(b[1] * idr));
-      d32[2 * k + 1] = make_float4((float)(2.0 * b[2] * idr), (float)(3.0 * b[3] * idr), 0.f, 0.f);
+    const tbsma_status st = upload_eam(c, t);
+    if (st != TBSMA_OK) {
+      // the earlier tables are gone: leave the context on TB-SMA with its forces
+      const std::string msg = c->err;
+      if (refresh(c, 0) == TBSMA_OK) launch_pair<false>(c, c->stream, c->prec);
+      c->err = msg;
+      return st;
     }
-    for (size_t k = 0; k < nF; ++k)
-      F32[k] = make_float4((float)cF[4 * k], (float)cF[4 * k + 1], (float)cF[4 * k + 2],
-                           (float)cF[4 * k + 3]);
-    // one allocation, every table 256-byte aligned
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t o_f32 = 0, o_d32 = o_f32 + up(nr * 16), o_p32 = o_d32 + up(2 * nr * 16);
-    const size_t o_F32 = o_p32 + up(nr * 16), o_f64 = o_F32 + up(nF * 16);
-    const size_t o_p64 = o_f64 + up(nr * 32), o_F64 = o_p64 + up(nr * 32);
-    const size_t total = o_F64 + up(nF * 32);
-    void* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, total);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc (EAM tables)");
-    c->eam_allocs.push_back(base);
-    char* b = static_cast<char*>(base);
-    const struct {
-      size_t off;
-      const void* src;
-      size_t bytes;
-    } parts[] = {{o_f32, f32.data(), nr * 16},     {o_d32, d32.data(), 2 * nr * 16},
-                 {o_p32, p32.data(), nr * 16},     {o_F32, F32.data(), nF * 16},
-                 {o_f64, cf.data(), nr * 32},      {o_p64, cp.data(), nr * 32},
-                 {o_F64, cF.data(), nF * 32}};
-    for (const auto& q : parts)
-      TB_CUDA(c, cudaMemcpyAsync(b + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, c->stream));
-    TB_CUDA(c, cudaStreamSynchronize(c->stream));  // the host staging vectors go out of scope
-    EamDev& d = c->eam;
-    d.f32 = reinterpret_cast<const float4*>(b + o_f32);
-    d.d32 = reinterpret_cast<const float4*>(b + o_d32);
-    d.p32 = reinterpret_cast<const float4*>(b + o_p32);
-    d.F32 = reinterpret_cast<const float4*>(b + o_F32);
-    d.f64 = reinterpret_cast<const double*>(b + o_f64);
-    d.p64 = reinterpret_cast<const double*>(b + o_p64);
-    d.F64 = reinterpret_cast<const double*>(b + o_F64);
-    const double ifx = idr / kFixedScale;  // per fixed-point unit of r
-    d.inv_dr_hi = (float)ifx;
-    d.inv_dr_lo = (float)(ifx - (double)d.inv_dr_hi);
-    const double irho = 1.0 / t->d_rho;
-    d.inv_drho_hi = (float)irho;
-    d.inv_drho_lo = (float)(irho - (double)d.inv_drho_hi);
-    d.kmax_r = t->n_r - 2;
-    d.kmax_rho = t->n_rho - 2;
-    d.inv_dr = idr;
-    d.inv_drho = irho;
-    c->eam_on = true;
   }
   TB_TRY(refresh(c, 0));
   TB_TRY(launch_pair<false>(c, c->stream, c->prec));
