@@ -369,6 +369,16 @@ class Engine:
                  keep[2].ctypes.data, keep[1].size, float(d_r))
         self._check(lib().tbsma_set_eam(self.ctx, ctypes.byref(t)), "tbsma_set_eam")
 
+    def set_eam_setfl(self, path: str, element=0):
+        """set_eam from one element of a DYNAMO setfl file (eam_files.read_setfl);
+        the file's cutoff and mass must equal the context's r_cut and mass."""
+        from .eam_files import read_setfl
+
+        t = read_setfl(path, element)
+        if abs(t["mass"] - self.params.mass) > 1e-6 * self.params.mass:
+            raise ValueError(f"the file's mass {t['mass']} differs from the context's {self.params.mass}")
+        self.set_eam(t["F"], t["d_rho"], t["f"], t["phi"], t["d_r"], r_cut=t["r_cut"])
+
     def thermostat(self):
         """(xi, eta) per wire, numpy arrays (tbsma_get_thermostat)."""
         xi = np.zeros(self.W)
