@@ -112,7 +112,7 @@ typedef struct {
 typedef struct {
   int64_t step;       /* steps done since init */
   double strain;      /* Eq. 4 */
-  double e_pot;       /* E_C of the wire, eV (Eq. 3) */
+  double e_pot;       /* E_C of the wire, eV (Eq. 3; or the EAM energy) */
   double e_kin;       /* 1/2 m sum_mobile |v|^2, eV */
   double temp;        /* 2 E_kin / (3 N_mobile k_B), K */
   double sigma_xx;    /* Eq. 5, eV/A^3 (x 160.2177 for GPa) */
@@ -161,10 +161,11 @@ tbsma_status tbsma_build_neighbors(tbsma_ctx* ctx, int32_t force_all, int32_t* n
  * SoA 3*N device arrays.  f32_out (nullable) receives the MIXED-precision
  * forces, f64_out (nullable) the FP64 forces, both on the same list; either
  * precision can be asked of any context.  The context's own force buffer
- * (used by the next step) is refreshed in the context's precision. */
+ * (used by the next step) is refreshed in the context's precision.  After
+ * tbsma_set_eam every pass (here and in the other calls) uses the EAM. */
 tbsma_status tbsma_compute_forces(tbsma_ctx* ctx, float* f32_out, double* f64_out);
 
-/* Per-atom energies E_B^i + E_R^i (Eq. 1-2) and axial pair virials
+/* Per-atom energies E_B^i + E_R^i (Eq. 1-2; EAM: F(rho_i) + 1/2 sum_j phi) and axial pair virials
  * 1/2 sum_j r_x,ij F_x,ij at the current positions, context precision,
  * into device arrays of N doubles (either nullable). */
 tbsma_status tbsma_atom_energies(tbsma_ctx* ctx, double* e_out, double* w_out);
