@@ -311,8 +311,10 @@ EAM_PER_IN = (25, 7, 1)
 # capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms,
 # r_skin 0.40 A, first launch: 72.322 MB read + 1.031 MB written), scaled by
 # the atom count (the traffic is per atom);
-# profiles/pair_integrate_batch32_d3_l40.md.  Set to None when the kernel
-# changes until it is captured again.
+# profiles/pair_integrate_batch32_d3_l40.md.  The kernel has since gained a
+# template flag for the tabulated EAM; its TB-SMA instantiation keeps the
+# same arithmetic, registers (32) and spills (0).  Set to None when the
+# TB-SMA kernel changes until it is captured again.
 FORCE_TRAFFIC_B_PER_ATOM = 131.5
 
 
