@@ -1,14 +1,22 @@
 #!/usr/bin/env python
 """Aggregate TB-SMA atom-steps/s of the batched mixed-precision wire MD step.
 
-Workload: 256 independent Au [100] wires, D = 3 nm, L = 40 nm (17435 atoms
-each, 4.46M atoms), Philox seeds 0..255, 10 K, strain rate 1e8 1/s, dt = 2 fs,
-synthetic fcc geometry.  One bench step = one MD step of every wire: B A O A,
-displacement check, list rebuilds as they occur, density pass, force pass,
-B.  Inputs (4.46M atoms, ~1.6 GB of state and lists) are far larger than the
-126 MB L2, so no flush is needed between steps.
+Workload (default): the statistical sweep of 2048 independent Au [100]
+wires, D in {2, 3, 4} nm x 24 lengths from 5 to 120 nm x T in {10, 298} K
+(trajectory t takes class t mod 144), 55.8M atoms, Philox seeds 0..2047,
+strain rate 1e8 1/s, dt = 2 fs, synthetic fcc geometry (the paper's >2000
+trajectories of Results, "Nanowire elongation").  The wires start from the
+perfect lattice with Gaussian velocities at T and run 2000 untimed
+equilibration steps (surface relaxation and the thermostat bring the list
+rebuild cadence to its steady state), then W warm-up steps, then K timed
+steps.  One bench step = one MD step of every wire: B A O A, displacement
+check, list rebuilds as they occur, density pass, force pass, B; the
+per-wire observables are reduced after every 1000 timed steps and at the end.
+Inputs (~25 GB of state and lists) are far larger than the 126 MB L2, so no
+flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
 
 Under torchrun each rank runs its own full batch (seeds offset by rank):
 weak scaling, no collective on the data path; rank 0 prints one JSON line.
@@ -32,7 +40,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "batch256_d3_l40"
+WORKLOAD = "sweep2048"
+EQUIL_STEPS = 2000  # untimed equilibration before the warm-up steps (steady rebuild cadence)
 LAUNCH = (256, 1280)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
 GRAPH_CHUNK = 50  # steps per captured graph (library constant)
 # List skin (A).  Results do not depend on it (every pass tests r_cut); at
@@ -52,9 +61,11 @@ UNIT = "atom-steps/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10000)
-    p.add_argument("--warmup", type=int, default=2000,
-                   help="untimed steps first, so that the rebuild cadence is in steady state")
+    p.add_argument("--steps", type=int, default=5000)
+    p.add_argument("--warmup", type=int, default=100, help="untimed steps after the equilibration")
+    p.add_argument("--equil", type=int, default=EQUIL_STEPS,
+                   help="untimed equilibration steps from the lattice start (part of the input "
+                        "recipe: the rebuild cadence is then in steady state)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--e2e-seg", type=int, default=100, help="MD steps per end-to-end segment")
@@ -135,10 +146,64 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------- wire samples
+def strata_of(specs):
+    """Wires grouped by (diameter, temperature): {key: [wire indices]}."""
+    out = {}
+    for w, sp in enumerate(specs):
+        out.setdefault((float(sp.diameter_nm), float(sp.temperature)), []).append(w)
+    return dict(sorted(out.items()))
+
+
+def stratified_sample(specs, atoms, per_stratum: int):
+    """per_stratum wires of every (diameter, temperature) stratum, spread
+    evenly over the stratum's sizes (atoms[w]); largest first."""
+    picks = []
+    for ws in strata_of(specs).values():
+        order = sorted(ws, key=lambda w: (atoms[w], w))
+        k = min(per_stratum, len(order))
+        idx = sorted({int(round((j + 0.5) / k * len(order) - 0.5)) for j in range(k)})
+        picks += [order[i] for i in idx]
+    return sorted(picks, key=lambda w: (-atoms[w], w))
+
+
+def extrapolate(specs, atoms, sampled: dict) -> float:
+    """Workload rate from per-wire samples {w: (atom_steps, seconds)}: the
+    rate of each (diameter, temperature) stratum is its samples' atom-steps
+    over their time; the workload's time per step is the sum over strata of
+    the stratum's atoms over its rate."""
+    t = 0.0
+    total = 0
+    for ws in strata_of(specs).values():
+        got = [sampled[w] for w in ws if w in sampled]
+        rate = sum(a for a, _ in got) / sum(s for _, s in got)
+        n = sum(int(atoms[w]) for w in ws)
+        t += n / rate
+        total += n
+    return total / t
+
+
+def _subbatch(batch, wires):
+    """The wires `wires` of a batch (in that order) as a new batch."""
+    from inputs.wires import Wire, pack
+
+    out = []
+    for w in wires:
+        s = batch.wire_slice(w)
+        out.append(Wire(x=batch.x[s].copy(), kind=batch.kind[s].copy(), diameter_nm=0.0,
+                        length_nm=0.0, L0=float(batch.L0[w]),
+                        temperature=float(batch.temperature[w]),
+                        strain_rate=float(batch.strain_rate[w]), gamma=float(batch.gamma[w]),
+                        seed=int(batch.seed[w])))
+    return pack(out)
+
+
 # --------------------------------------------------------- CPU oracle leg
-def oracle_sample(batch, budget_s: float, steps: int | None = None, eam: bool = False):
-    """Time the FP64 oracle on the first wires of the batch, one per thread
-    (eam: with the Au EAM tables of au_eam_tables in place of TB-SMA).
+def oracle_sample(batch, budget_s: float, steps: int | None = None, eam: bool = False,
+                  wires=None):
+    """Time the FP64 oracle on sample wires of the batch (default: the first
+    wires), one wire per task over the host threads, largest first (eam:
+    with the Au EAM tables of au_eam_tables in place of TB-SMA).
 
     Returns (atom-steps/s, threads used, description, atoms, steps)."""
     import oracle
@@ -146,13 +211,15 @@ def oracle_sample(batch, budget_s: float, steps: int | None = None, eam: bool = 
     kw = {"pot": oracle.EamPotential(oracle.EamTables(**au_eam_tables(), r_cut=5.8))} if eam else {}
 
     threads = oracle.max_threads()
-    W = min(threads, batch.n_wires)
-    n = batch.n[:W]
+    if wires is None:
+        wires = list(range(min(threads, batch.n_wires)))
+    sub = _subbatch(batch, wires)
+    W = sub.n_wires
+    n = sub.n
     N = int(n.sum())
-    x = batch.x[:N].copy()
+    x = sub.x.copy()
     v = np.zeros_like(x)
-    args = (batch.kind[:N], batch.offset[:W], n, batch.L0[:W], batch.strain_rate[:W],
-            batch.temperature[:W], batch.gamma[:W], batch.seed[:W])
+    args = (sub.kind, sub.offset, n, sub.L0, sub.strain_rate, sub.temperature, sub.gamma, sub.seed)
     F, xb, dg, nr = oracle.md_batch(x, v, *args, 0, 1, 2.0, brute_max=0, **kw)  # includes first forces
     t = time.perf_counter()
     oracle.md_batch(x, v, *args, 1, 1, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg, n_rebuild=nr,
@@ -164,10 +231,11 @@ def oracle_sample(batch, budget_s: float, steps: int | None = None, eam: bool = 
     oracle.md_batch(x, v, *args, 2, steps, 2.0, brute_max=0, F=F, x_build=xb, d_grip=dg,
                     n_rebuild=nr, **kw)
     el = time.perf_counter() - t
-    desc = f"{W} of {batch.n_wires} wires ({N} atoms, one per thread) x {steps} MD steps"
+    desc = (f"{W} of {batch.n_wires} wires ({N} atoms; one wire per task, {min(threads, W)} "
+            f"host threads) x {steps} MD steps")
     if eam:
         desc += ", tabulated EAM"
-    return N * steps / el, W, desc, N, steps
+    return N * steps / el, min(threads, W), desc, N, steps
 
 
 def _oracle_run(batch, first_step: int, steps: int, state=None, eam: bool = False):
@@ -202,6 +270,23 @@ def _workload_atoms(specs) -> int:
     return int(sum(_geometry(float(sp.diameter_nm), float(sp.length_nm)).n for sp in specs))
 
 
+def _spec_atoms(specs):
+    from inputs.configs import _geometry
+
+    return [_geometry(float(sp.diameter_nm), float(sp.length_nm)).n for sp in specs]
+
+
+def workload_config(specs) -> dict:
+    """The workload's shape for the JSON line's config."""
+    d = sorted({float(sp.diameter_nm) for sp in specs})
+    L = sorted({float(sp.length_nm) for sp in specs})
+    T = sorted({float(sp.temperature) for sp in specs})
+    rates = sorted({float(sp.strain_rate) for sp in specs})
+    return {"wires": len(specs), "diameters_nm": d,
+            "lengths_nm": L if len(L) <= 4 else f"{len(L)} from {L[0]:g} to {L[-1]:g}",
+            "temperatures_K": T, "strain_rate_per_s": rates[0] if len(rates) == 1 else rates}
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host on a bounded sample of the workload."""
     rank, world, _ = _env_rank()
@@ -212,30 +297,36 @@ def run_reference(args):
 
     threads = oracle.max_threads()
     specs = WORKLOADS[args.workload]()
+    atoms = _spec_atoms(specs)
     total = args.steps + args.warmup
     budget_s = 120.0
-    # one step of the first wire, alone, sizes the sample
     eam = args.potential == "eam"
-    one = build(specs[:1])
-    st = _oracle_run(one, 0, 1, eam=eam)
+    # a stratified sample: three wires per host thread, spread over the
+    # (diameter, temperature) strata and their sizes, largest first
+    n_strata = len(strata_of(specs))
+    picks = stratified_sample(specs, atoms, max(1, (3 * threads + n_strata - 1) // n_strata))
+    sample_specs = [specs[w] for w in picks]
+    # one step of the sample sizes it
+    probe = build(sample_specs)
+    st = _oracle_run(probe, 0, 1, eam=eam)
     t = time.perf_counter()
-    _oracle_run(one, 1, 2, st, eam=eam)
-    t_wire = (time.perf_counter() - t) / 2
-    if total * t_wire <= budget_s:
-        sample_specs = specs[: min(threads, len(specs))]
-        sample = (f"{len(sample_specs)} of {len(specs)} wires of the workload, whole, one per "
-                  f"host thread")
+    _oracle_run(probe, 1, 1, st, eam=eam)
+    t_step = time.perf_counter() - t
+    if total * t_step <= budget_s:
+        sample = (f"{len(sample_specs)} of {len(specs)} wires of the workload, whole, stratified over "
+                  f"diameter and temperature, one wire per task on {threads} host threads")
     else:
-        # the same wires shortened (same diameter, temperature, pull, seeds) so that
-        # warm-up + timed steps fit the budget: per-atom work of the oracle is that
-        # of the full wires (same cross-section and neighbourhoods)
-        frac = budget_s / (total * t_wire)
-        length = max(3.0, round(specs[0].length_nm * frac, 1))
-        sample_specs = [WireSpec(sp.diameter_nm, length, sp.temperature, sp.strain_rate, sp.seed,
-                                 sp.gamma) for sp in specs[: min(threads, len(specs))]]
-        sample = (f"{len(sample_specs)} wires D {specs[0].diameter_nm} nm x L {length} nm (the "
-                  f"workload's wires shortened from {specs[0].length_nm} nm so that {total} "
-                  f"steps fit ~{budget_s:.0f} s), one per host thread")
+        # the same wires shortened (same diameter, temperature, pull and seeds) so
+        # that warm-up + timed steps fit the budget: per-atom work of the oracle
+        # is that of the full wires (same cross-section and neighbourhoods)
+        frac = budget_s / (total * t_step)
+        sample_specs = [WireSpec(sp.diameter_nm, max(3.0, round(sp.length_nm * frac, 1)),
+                                 sp.temperature, sp.strain_rate, sp.seed, sp.gamma)
+                        for sp in sample_specs]
+        sample = (f"{len(sample_specs)} of {len(specs)} wires of the workload, stratified over "
+                  f"diameter and temperature, each shortened to {100 * frac:.1f} % of its length "
+                  f"(at least 3 nm) so that {total} steps fit ~{budget_s:.0f} s, one wire per "
+                  f"task on {threads} host threads")
     sub = build(sample_specs)
     N = int(sub.n.sum())
     st = _oracle_run(sub, 0, max(1, args.warmup), eam=eam)
@@ -243,18 +334,17 @@ def run_reference(args):
     _oracle_run(sub, max(1, args.warmup), args.steps, st, eam=eam)
     el = time.perf_counter() - t
     value = N * args.steps / el
+    cfg = {"workload": args.workload, "atoms_per_gpu": _workload_atoms(specs), "dt_fs": 2.0}
+    cfg.update(workload_config(specs))
+    cfg.update({"precision": "fp64 (oracle)", "observables_every": None,
+                "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
+                "l2": "host", "parallelism": f"{threads} host threads"})
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "wires": len(specs),
-                   "atoms_per_gpu": _workload_atoms(specs), "dt_fs": 2.0,
-                   "temperature_K": specs[0].temperature, "strain_rate_per_s": specs[0].strain_rate,
-                   "precision": "fp64 (oracle)", "observables_every": None,
-                   "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
-                   "l2": "host", "parallelism": f"{len(sample_specs)} host threads"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(sample_specs),
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads,
                          "kind": "oracle", "sample": f"{sample}; {N} atoms"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -286,36 +376,44 @@ def launches_in(K: int, chains: int) -> int:
     return n
 
 
-# Algorithmic work of one force-pass launch (per atom, n_c list entries inside
-# r_cut, n_s skin entries):
-#   FP32 instructions  21 per in-cutoff entry (3 int->float, r^2 3, test 1,
-#                      r 1 + Newton 3, s 1, two exponent arguments 2, bracket 3:
-#                      a_i + a_j, fp h - that, times g; f/r 1, F 3) and 7 per
-#                      skin entry (3 + 3 + 1)
-#   MUFU               3 per in-cutoff entry (rsqrt, two ex2)
-#   HBM bytes          2 n_list (int16 list) + 4 (count) + 8 (index range)
-#                      + 16 (own packed position) + 12 (F)
-# Peaks: 128 FP32 lanes and 32 MUFU results per clock per SM (the MUFU rate
-# measured with an ex2 throughput probe on this GPU: 29.9/clk/SM), at the
-# median SM clock sampled during the timed region; HBM from MEASURED_PEAKS.
-# The roofline time is the slower of the ALU time (FP32 and MUFU pipes run
+# Algorithmic work of the pair passes per in-cutoff pair (list entry with
+# r <= r_cut; n_c per atom, both sides of each pair counted): the method's
+# arithmetic, without list decoding, addressing or the fixed-point
+# conversions of this implementation.
+#   force pass  19 FP32: 3 coordinate differences, r^2 (3), the cutoff test,
+#               r = r^2 rsqrt(r^2) (1), s (1), two exponent arguments (2), the
+#               bracket (a_i + a_j, fp h minus that, times g: 3), f/r (1), the
+#               three force components (3), one Newton step on r (1);
+#               3 MUFU (rsqrt, two ex2)
+#   density     11 FP32: differences (3), r^2 (3), test (1), r (1), the
+#               exponent argument (1), the term (1), the sum (1); 2 MUFU
+# HBM bytes per atom of one launch (the list stays in HBM): 2 per list
+# entry (int16; skin entries included) + 4 (count) + 8 (index range)
+# + 16 (own packed position) + 12 (F, force pass) or 4 (a_i, density pass).
+# Peaks: 128 FP32 lanes and 32 MUFU results per clock per SM (an ex2
+# throughput measurement on this GPU gave 29.8/clk/SM), at the median SM
+# clock sampled during the timed region; HBM from MEASURED_PEAKS.  The
+# roofline time is the slower of the ALU time (FP32 and MUFU pipes run
 # concurrently: the larger of the two) and the HBM time.
-FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN = 21, 7, 3
+PASS_MODEL = {
+    "force": {"fp32_in": 19, "fp32_skin": 0, "mufu_in": 3, "bytes_out": 12},
+    "density": {"fp32_in": 11, "fp32_skin": 0, "mufu_in": 2, "bytes_out": 4},
+}
+# The force pass's instruction count in this implementation (the three
+# int->float conversions per entry included, 7 per skin entry: conversions,
+# r^2, test), reported beside the method's count.
+FORCE_IMPL_MODEL = {"fp32_in": 21, "fp32_skin": 7, "mufu_in": 3, "bytes_out": 12}
 # The tabulated-EAM force pass (--potential eam) per in-cutoff entry: the
 # same geometry (6), radius (4, one MUFU rsqrt), bracket (2), scale (1) and
 # accumulation (3), plus the interval and t of r (5: FMUL, F2I, I2F, two
 # FFMA) and two quadratic derivative polynomials (4) in place of the two ex2;
 # MUFU 1; skin entries as above.
-EAM_PER_IN = (25, 7, 1)
-# DRAM bytes (read + write) per atom of one force-pass launch, from an ncu
-# capture of the current k_force_f32 on 32 D3 x L40 wires (557,920 atoms,
-# r_skin 0.40 A, first launch: 72.322 MB read + 1.031 MB written), scaled by
-# the atom count (the traffic is per atom);
-# profiles/pair_integrate_batch32_d3_l40.md.  The kernel has since gained a
-# template flag for the tabulated EAM; its TB-SMA instantiation keeps the
-# same arithmetic, registers (32) and spills (0).  Set to None when the
-# TB-SMA kernel changes until it is captured again.
-FORCE_TRAFFIC_B_PER_ATOM = 131.5
+EAM_MODEL = {"fp32_in": 25, "fp32_skin": 7, "mufu_in": 1, "bytes_out": 12}
+# DRAM bytes (read + write) per atom of one force-pass launch from an ncu
+# capture of the current kernel on a smaller case of the same workload,
+# scaled by the atom count (the traffic is per atom); None until the
+# current kernel has been captured.
+FORCE_TRAFFIC_B_PER_ATOM = None
 
 
 def au_eam_tables(d_r=0.002, d_rho=0.005, rho_max=120.0, r_cut=5.8):
@@ -351,17 +449,17 @@ def _list_census(eng, r_cut=5.8, chunk=1 << 20):
     return n_in / N, (n_all - n_in) / N
 
 
-def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs, per_in=(FP32_PER_IN, FP32_PER_SKIN, MUFU_PER_IN)):
-    """The force pass's roofline from its algorithmic work (per atom: n_c
-    in-cutoff and n_s skin list entries) and its measured time per launch
-    `ms`, for `sms` SMs at `mhz` and an HBM peak of `hbm_gbs`: the bound is
-    the slower of the FP32 and MUFU pipes (which run concurrently) and the
-    bytes at HBM bandwidth; `achieved` is the bound's work over the time."""
+def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs, model=PASS_MODEL["force"]):
+    """A pair pass's roofline from its algorithmic work (per atom: n_c
+    in-cutoff and n_s skin list entries, `model` the counts per entry) and
+    its measured time per launch `ms`, for `sms` SMs at `mhz` and an HBM
+    peak of `hbm_gbs`: the bound is the slower of the FP32 and MUFU pipes
+    (which run concurrently) and the bytes at HBM bandwidth; `achieved` is
+    the bound's work over the time."""
     f = mhz * 1e6
-    fp32_in, fp32_skin, mufu_in = per_in
-    fp32_ops = N * (fp32_in * n_c + fp32_skin * n_s)
-    mufu_ops = N * mufu_in * n_c
-    bytes_ = N * (2.0 * (n_c + n_s) + 4 + 8 + 16 + 12)
+    fp32_ops = N * (model["fp32_in"] * n_c + model["fp32_skin"] * n_s)
+    mufu_ops = N * model["mufu_in"] * n_c
+    bytes_ = N * (2.0 * (n_c + n_s) + 4 + 8 + 16 + model["bytes_out"])
     t_fp32 = fp32_ops / (128 * sms * f)
     t_mufu = mufu_ops / (32 * sms * f)
     t_hbm = bytes_ / (hbm_gbs * 1e9)
@@ -386,24 +484,65 @@ def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs, per_in=(FP32_PER_IN, FP32_PE
     return bound
 
 
-def force_roofline(eng, ms, clocks, eam=False):
+def pass_rooflines(eng, ms_force, ms_density, clocks, eam=False):
+    """The force pass's roofline (the dominant kernel), with the density
+    pass's beside it."""
     import torch
 
     n_c, n_s = _list_census(eng)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     hbm, kind = _peaks()
-    bound = roofline_of(eng.N, n_c, n_s, ms, props.multi_processor_count,
-                        clocks.get("sm_mhz") or 2032.0, hbm,
-                        **({"per_in": EAM_PER_IN} if eam else {}))
+    sms, mhz = props.multi_processor_count, clocks.get("sm_mhz") or 2032.0
+    force_model = EAM_MODEL if eam else PASS_MODEL["force"]
+    bound = roofline_of(eng.N, n_c, n_s, ms_force, sms, mhz, hbm, model=force_model)
     traffic = None if (eam or FORCE_TRAFFIC_B_PER_ATOM is None) else FORCE_TRAFFIC_B_PER_ATOM * eng.N
     bound.update({
         "kernel": "k_force_f32<EAM>" if eam else "k_force_f32",
+        "model": ("EAM: 25 FP32 + 1 MUFU per in-cutoff entry, 7 FP32 per skin entry" if eam else
+                  "19 FP32 + 3 MUFU per in-cutoff pair (the method's arithmetic)"),
         "traffic": traffic,
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per atom, small-case "
-                          "capture scaled by atoms",
+                          "capture of the same workload scaled by atoms",
         "hbm_peak_kind": kind,
     })
+    if not eam:
+        impl = roofline_of(eng.N, n_c, n_s, ms_force, sms, mhz, hbm, model=FORCE_IMPL_MODEL)
+        bound["frac_impl_count"] = impl["frac"]
+        d = roofline_of(eng.N, n_c, n_s, ms_density, sms, mhz, hbm, model=PASS_MODEL["density"])
+        bound["density"] = {k: d[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                              "ms_per_launch", "roofline_ms")}
+    else:
+        bound["density_ms_per_launch"] = ms_density
     return bound
+
+
+def fp64_one_wire_per_launch(tb, specs, batch, params, eam=False, steps=20):
+    """The plain FP64 path, one wire per context, on a stratified sample of
+    the workload's wires (two per diameter and temperature), extrapolated to
+    the workload per stratum (see extrapolate)."""
+    import torch
+
+    picks = stratified_sample(specs, batch.n, 2)
+    sampled = {}
+    for w in picks:
+        one = _subbatch(batch, [w])
+        e1 = tb.Engine(one, precision="fp64", params=params)
+        if eam:
+            e1.set_eam(**au_eam_tables())
+        e1.set_launch(64, 0)  # one wire: small tiles to spread it over the SMs
+        e1.init_velocities()
+        e1.step(5, 2.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        e1.step(steps, 2.0)
+        b.record()
+        torch.cuda.synchronize()
+        sampled[w] = (one.n_atoms * steps, a.elapsed_time(b) / 1e3)
+        e1.close()
+    return {"value": extrapolate(specs, batch.n, sampled), "unit": UNIT,
+            "sample": (f"{len(picks)} of {len(specs)} wires (two per diameter and temperature, "
+                       f"spread over lengths), each alone in its own FP64 context, {steps} steps; "
+                       f"per-stratum rates weighted by the workload's atoms")}
 
 
 def run_ours(args):
@@ -426,20 +565,25 @@ def run_ours(args):
     eam = args.potential == "eam"
     if eam:
         eng.set_eam(**au_eam_tables())
-    eng.init_velocities()
-    eng.step(max(3, args.warmup), 2.0)
     launch = LAUNCH
+    eng.set_launch(*launch)
+    eng.init_velocities()
+    # the input recipe: equilibrate from the lattice start (untimed), so that
+    # surface relaxation is over and list rebuilds come at their steady rate
+    if args.equil > 0:
+        eng.step(args.equil, 2.0)
     if args.autotune:
         from paper_1311_3890_b300.autotune import tune
 
         launch, _ = tune(eng)
-    eng.set_launch(*launch)
+        eng.set_launch(*launch)
+    eng.step(max(3, args.warmup), 2.0)
     # capture the step graph the timed calls will replay (50-step chunks, or
     # all K steps when K < 50) outside the timed region
     eng.step(min(_chunks(args.steps)[0], GRAPH_CHUNK), 2.0)
     torch.cuda.synchronize()
 
-    chains0 = eng.rebuild_chains()
+    rs0 = eng.rebuild_stats()
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -456,14 +600,27 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     t_ms = ev0.elapsed_time(ev1)
-    chains = eng.rebuild_chains() - chains0
+    rs1 = eng.rebuild_stats()
+    chains = rs1["chains"] - rs0["chains"]
     t_max, atoms_all = aggregate(t_ms, N, device="cuda")
     value = atoms_all * args.steps / (t_max / 1e3)
+
+    # where the time goes: the next K steps enqueued directly with an event
+    # after each phase (same kernels), then one observables report alone
+    split_steps = min(args.steps, 500)
+    ph = eng.step_profile(split_steps, 2.0)
+    rs2 = eng.rebuild_stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    eng.observables()
+    b.record()
+    torch.cuda.synchronize()
+    obs_ms = a.elapsed_time(b)
 
     # force-error gate on the final state (same positions, same list)
     fc = eng.force_check()
 
-    # dominant kernel (force pass) timed alone with CUDA events on the library's stream
+    # the pair passes timed alone with CUDA events on the library's stream
     reps = 20
     res = {}
     for which in (1, 2):
@@ -474,34 +631,49 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    roof = force_roofline(eng, res[2], ck, eam=eam)
-    roof["density_ms_per_launch"] = res[1]
+    roof = pass_rooflines(eng, res[2], res[1], ck, eam=eam)
+    cfg = {"workload": args.workload, "atoms_per_gpu": N, "dt_fs": 2.0}
+    cfg.update(workload_config(specs))
+    cfg.update({"precision": "mixed",
+                "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
+                "equilibration_steps": args.equil, "observables_every": OBS_EVERY,
+                "r_skin_A": R_SKIN, "tile_atoms": launch[0], "window_atoms": launch[1],
+                "launch": "autotuned" if args.autotune else "fixed",
+                "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "mixed f32 pair / f64 state",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "wires": W, "atoms_per_gpu": N, "dt_fs": 2.0,
-                   "temperature_K": 10.0, "strain_rate_per_s": 1e8, "precision": "mixed",
-                   "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
-                   "observables_every": OBS_EVERY, "r_skin_A": R_SKIN,
-                   "tile_atoms": launch[0], "window_atoms": launch[1],
-                   "launch": "autotuned" if args.autotune else "fixed",
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"},
+        "data": "synthetic", "config": cfg,
         "roofline": roof,
         "clocks": ck,
         "gpu_launches": launches_in(args.steps, chains),
         "force_check": {"max_err_scaled": float(fc["max_err_scaled"].max()),
                         "norm_err": float(fc["norm_err"].max()),
                         "max_err_raw": float(fc["max_err_raw"].max())},
-        "rebuilds_per_wire": float(ob["n_rebuilds"].mean()),
+        "timed_window": {
+            "rebuilt_wires": rs1["wires"] - rs0["wires"],
+            "rebuilt_atoms": rs1["atoms"] - rs0["atoms"],
+            "rebuilt_atoms_per_atom_step": (rs1["atoms"] - rs0["atoms"]) / (N * args.steps),
+            "reports": len(_chunks(args.steps)),
+        },
+        "split": {
+            "steps": split_steps,
+            "how": "the steps after the timed window, enqueued directly with a CUDA event after "
+                   "each phase (same kernels as the graph), then one observables report alone",
+            "ms_per_step": {k: v / split_steps for k, v in ph.items()},
+            "sum_ms_per_step": sum(ph.values()) / split_steps,
+            "observables_ms_per_report": obs_ms,
+            "rebuilt_wires": rs2["wires"] - rs1["wires"],
+            "rebuilt_atoms": rs2["atoms"] - rs1["atoms"],
+        },
     }
 
     if not args.no_extras and rank == 0:
         # end to end through the public API: pinned host state in, K steps in
         # segments, per-wire observables and state out every segment
         seg = max(1, min(args.e2e_seg, args.steps))
-        n_seg = max(1, args.steps // seg)
+        n_seg = max(1, min(10, args.steps // seg))
         xh = torch.empty(3 * N, dtype=torch.float64).pin_memory()
         vh = torch.empty(3 * N, dtype=torch.float64).pin_memory()
         eng.download(xh, vh)
@@ -517,37 +689,18 @@ def run_ours(args):
         line["e2e"] = {"value": N * seg * n_seg / el, "unit": UNIT,
                        "h2d_bytes_per_step": 48.0 * N / seg,
                        "d2h_bytes_per_step": (48.0 * N + obs_bytes) / seg,
-                       "segment_steps": seg}
-        # plain FP64, one wire per launch, on a sample of the same wires
-        from inputs.wires import Wire, pack
-
-        tot_as, tot_ms = 0.0, 0.0
-        for w in range(8):
-            s = batch.wire_slice(w)
-            one = pack([Wire(x=batch.x[s].copy(), kind=batch.kind[s].copy(), diameter_nm=3.0,
-                             length_nm=40.0, L0=float(batch.L0[w]), temperature=10.0,
-                             strain_rate=1e8, gamma=float(batch.gamma[w]), seed=int(batch.seed[w]))])
-            e1 = tb.Engine(one, precision="fp64", params=params)
-            if eam:
-                e1.set_eam(**au_eam_tables())
-            e1.set_launch(64, 0)  # one 17k-atom wire: small tiles to occupy every SM
-            e1.init_velocities()
-            e1.step(5, 2.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            e1.step(20, 2.0)
-            b.record()
-            torch.cuda.synchronize()
-            tot_ms += a.elapsed_time(b)
-            tot_as += one.n_atoms * 20
-            e1.close()
-        line["fp64_one_wire_per_launch"] = {
-            "value": tot_as / (tot_ms / 1e3), "unit": UNIT,
-            "sample": "8 of the 256 wires, each alone in its own context, 20 steps"}
+                       "segment_steps": seg, "segments": n_seg}
+        line["fp64_one_wire_per_launch"] = fp64_one_wire_per_launch(tb, specs, batch, params, eam)
         if world == 1:
-            v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0, eam=eam)
+            import oracle
+
+            threads = oracle.max_threads()
+            n_strata = len(strata_of(specs))
+            picks = stratified_sample(specs, batch.n,
+                                      max(1, (3 * threads + n_strata - 1) // n_strata))
+            v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0, eam=eam, wires=picks)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": desc}
+                                    "sample": desc + ", stratified over diameter and temperature"}
     eng.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -81,6 +81,10 @@ typedef enum { TBSMA_FP64 = 0, TBSMA_MIXED = 1 } tbsma_precision;
                                        neighbour more than 32767 positions away in the atom order */
 #define TBSMA_WIRE_CELL_OVERFLOW 4u /* a cell holds more atoms than its capacity */
 #define TBSMA_WIRE_RANGE 8u         /* an atom is more than 1e7 A from its wire's centre */
+#define TBSMA_WIRE_GRID_CLAMP 16u   /* not a fault: an atom lay outside its wire's cell grid at a
+                                       list build (the list is still exact while no cell
+                                       overflows); the next call that synchronises grows the
+                                       grid and clears the bit */
 
 /* TB-SMA parameters (Table 1; r_cut after Eq. 3), list skin and mass.
  * Au: A = 0.2061 eV, xi = 1.790 eV, p = 10.229, q = 4.036, r0 = 2.884 A
@@ -175,8 +179,20 @@ tbsma_status tbsma_atom_energies(tbsma_ctx* ctx, double* e_out, double* w_out);
  * density pass, force pass, B (under the Nosé–Hoover protocol: NH B A,
  * ..., B NH; see tbsma_set_protocol).  Replays a captured CUDA graph; the first
  * call with a new dt captures it.  Synchronises at the end to read the
- * wires' status words.  Errors: EINVAL (n_steps < 0, dt_fs <= 0), EWIRE,
- * EOVERFLOW, ECUDA. */
+ * wires' status words (and, in a call of more than 1000 steps, every 1000
+ * steps).
+ * Cell grids grow: each wire's cell grid is planned at init with room for
+ * the wire to double its length; an atom outside it at a list build is
+ * binned into an edge cell and marks the wire (TBSMA_WIRE_GRID_CLAMP), and
+ * at the next status read the library re-plans that wire's grid around
+ * its current extent (again with room to double), growing its cell
+ * storage if needed, and rebuilds its list.  Forces are unaffected unless
+ * an edge cell overflowed before that (TBSMA_WIRE_CELL_OVERFLOW): then the
+ * grid is grown all the same, the forces are recomputed, the bit is
+ * cleared, and the call returns EOVERFLOW at once (the steps since that
+ * wire's previous list build used a list that missed atoms; repeat them
+ * from saved state: the retry runs on the grown grid).
+ * Errors: EINVAL (n_steps < 0, dt_fs <= 0), EWIRE, EOVERFLOW, ECUDA. */
 tbsma_status tbsma_step_nvt_pull(tbsma_ctx* ctx, int64_t n_steps, double dt_fs);
 
 /* Paper protocol mode (Methods, "Simulation details": Nosé–Hoover
@@ -406,6 +422,15 @@ int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
  * per step and per position refresh (they return at once when no wire is
  * flagged).  Synchronises.  Errors: EINVAL (null). */
 tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* ctx, int64_t* n);
+
+/* List-build accounting since tbsma_init (host out[3]): out[0] launches of
+ * the rebuild chain (as tbsma_get_rebuild_chains), out[1] wires whose lists
+ * were built, out[2] atoms whose lists were built (both summed over every
+ * build: step loop, refreshes, init).  The difference of two reads gives
+ * the rebuilds inside a stretch of steps (Results, "TB-SMA benchmarks": the
+ * list rebuild rate is what separates the 10 K and 298 K timings).
+ * Synchronises.  Errors: EINVAL (null). */
+tbsma_status tbsma_get_rebuild_stats(tbsma_ctx* ctx, int64_t* out);
 tbsma_status tbsma_get_neighbors(tbsma_ctx* ctx, int32_t* n_nbr, int32_t* nbr, int32_t cap);
 
 /* Launch shape of the pair passes: threads per block (64, 128 or 256; one
@@ -423,6 +448,25 @@ tbsma_status tbsma_set_launch(tbsma_ctx* ctx, int32_t block_threads, int32_t win
  * caller can bracket this call with CUDA events on the same stream to time a
  * pass alone.  Errors: EINVAL (pass not 1 or 2, reps < 1). */
 tbsma_status tbsma_run_pass(tbsma_ctx* ctx, int32_t pass, int32_t reps);
+
+/* Phases of one MD step, as tbsma_step_profile splits its time. */
+#define TBSMA_PHASE_INTEGRATE 0 /* thermostat half steps + B A O A + pack + displacement check */
+#define TBSMA_PHASE_PLAN 1      /* flagged wires -> rebuild work list, step counter */
+#define TBSMA_PHASE_REBUILD 2   /* cell clear, bin, sort, list build of the flagged wires */
+#define TBSMA_PHASE_DENSITY 3   /* pass 1 (Eq. 1) */
+#define TBSMA_PHASE_FORCE 4     /* pass 2 (Eq. 2-3 derivative) */
+#define TBSMA_PHASE_KICK 5      /* closing half kick (+ thermostat end half step) */
+#define TBSMA_N_PHASES 6
+
+/* The same steps as tbsma_step_nvt_pull (identical kernels, order and
+ * results), enqueued directly instead of through the graph, with a CUDA
+ * event after every phase; phase_ms (host, TBSMA_N_PHASES doubles) receives
+ * the summed milliseconds of each phase over the n_steps steps.  For
+ * measurement: the events between phases serialise nothing that the graph
+ * overlaps (the step is one stream), but each launch pays its own launch
+ * latency.  Synchronises.  Errors: EINVAL (n_steps outside [1, 2^20],
+ * dt_fs <= 0, a barostat protocol), and those of tbsma_step_nvt_pull. */
+tbsma_status tbsma_step_profile(tbsma_ctx* ctx, int64_t n_steps, double dt_fs, double* phase_ms);
 
 /* Philox4x32-10 (Salmon et al., SC'11) on the device, as the thermostat
  * uses it: out[4i..4i+4) = philox(ctr[4i..4i+4), key[2i..2i+2)).  Device
@@ -452,8 +496,12 @@ tbsma_status tbsma_normals(uint64_t seed, const uint32_t* atoms, int64_t n, int6
  * The per-atom density scratch lives in one file-scope device array of
  * TBSMA_NOALLOC_MAX_ATOMS doubles (128 KiB) that every GPU loading this
  * library holds until the process exits.
- *   - The first call on each device looks that array up (a CUDA runtime
- *     query with the device current); make that first call before any
+ *   - Every call looks that array's device address up with the caller's
+ *     device current (a CUDA runtime query, no allocation, no host-side
+ *     cache: the address is right for whichever device and context is
+ *     current, and concurrent calls from several host threads share no
+ *     host state).  The first lookup on a device may load the library's
+ *     module there, so make the first call on each device before any
  *     stream capture.
  *   - All calls share the array: two calls whose kernels overlap on the GPU
  *     (e.g. issued on different streams) race and give wrong forces.
@@ -461,8 +509,10 @@ tbsma_status tbsma_normals(uint64_t seed, const uint32_t* atoms, int64_t n, int6
  *     slot it reads, so nothing carries over between calls.
  * Errors: EOVERFLOW if n_atoms > TBSMA_NOALLOC_MAX_ATOMS (nothing launched),
  * EINVAL for null pointers, n_atoms < 0 or bad parameters, ECUDA if the
- * lookup or a launch fails.  n_atoms == 0 is a no-op.  Asynchronous on
- * cuda_stream. */
+ * lookup or one of this call's two launches fails.  A launch error left
+ * pending by an earlier, unrelated CUDA call also gives ECUDA: it is left
+ * pending for its owner (not cleared) and nothing is launched.  n_atoms == 0
+ * is a no-op.  Asynchronous on cuda_stream. */
 #define TBSMA_NOALLOC_MAX_ATOMS 16384
 tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t n_atoms, const double* x,
                                   double* f_out, void* cuda_stream);

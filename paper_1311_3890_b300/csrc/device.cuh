@@ -30,6 +30,10 @@ constexpr uint32_t kWireNonFinite = 1u;
 constexpr uint32_t kWireNbrOverflow = 2u;
 constexpr uint32_t kWireCellOverflow = 4u;
 constexpr uint32_t kWireRange = 8u;
+// Not a fault: an atom lay outside its wire's cell grid at a list build and
+// was binned into an edge cell (the list is still exact while no cell
+// overflows).  The host grows the wire's grid and clears the bit.
+constexpr uint32_t kWireGridClamp = 16u;
 
 constexpr int kCellCap = 32;  // atoms per cell (one per lane in the sort and build)
 

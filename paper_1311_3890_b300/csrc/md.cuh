@@ -299,14 +299,23 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// double -> float by truncating the mantissa on the integer pipe (|d| below
-// the float range gives 0, above it Inf; non-finite values are caught by
-// finite_bits on the double).  Used only for FP32 increments of a velocity.
+// double -> float rounded to nearest, ties to even, on the integer pipe: the
+// top 23 of the 52 mantissa bits, plus one where the 29 dropped bits are
+// above half an ulp, or exactly half with an odd result (a carry out of the
+// mantissa steps the exponent, up to Inf).  |d| below the normal float range
+// gives a signed 0, above it Inf; non-finite values are caught by
+// finite_bits on the double.  This is the value a round-to-nearest
+// conversion gives for every normal float result (an unbiased rounding: a
+// truncating one would shrink every position increment formed from v by up
+// to one ulp).  Used only for FP32 increments of a velocity.
 __device__ __forceinline__ float narrow(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const int e = (int)((hi >> 20) & 0x7ffu) - 896;
   const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned body = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : (((unsigned)e << 23) | m));
+  const unsigned drop = lo & 0x1fffffffu;  // the 29 dropped bits; half an ulp is 1 << 28
+  const unsigned up = (drop > 0x10000000u || (drop == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  const unsigned body =
+      e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : ((((unsigned)e << 23) | m) + up));
   return __uint_as_float((hi & 0x80000000u) | body);
 }
 

@@ -7,9 +7,10 @@
 // cells and atoms); the other kernels stride over that list, so a step in
 // which no wire moved far enough costs four near-empty launches.
 //
-// Cells: a fixed grid per wire (edge >= list radius), atoms outside the grid
+// Cells: a grid per wire (edge >= list radius), atoms outside the grid
 // clamped into edge cells (clamping is monotone, so two atoms within one
-// edge of each other still land in adjacent cells).  Each cell holds up to
+// edge of each other still land in adjacent cells) and the wire marked
+// (kWireGridClamp) so that the host grows its grid.  Each cell holds up to
 // kCellCap atom indices, sorted ascending so that the list order, and hence
 // every force sum, is deterministic.
 #pragma once
@@ -30,6 +31,7 @@ struct NlWork {
   int64_t* chains;      // [1] launches of the rebuild chain (clear, bin, sort, build)
   int64_t* last_build;  // [W] step of the wire's last list build
   uint8_t* banked;      // [W] the wire's rows in bank-group order (k_nl_build) at this build
+  int64_t* rebuilt;     // [2] wires and atoms whose lists were built, accumulated
 };
 
 // Shortest life (steps) of a wire's previous list for which its rebuilt
@@ -135,6 +137,8 @@ __global__ void __launch_bounds__(1024)
     nw.wl_atom[nf] = tot[1];
     if (step_counter) step_counter[0] += 1;
     nw.chains[0] += 1;
+    nw.rebuilt[0] += nf;
+    nw.rebuilt[1] += tot[1];
   }
 }
 
@@ -150,9 +154,12 @@ __global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* c
   }
 }
 
-__device__ __forceinline__ int cell_coord(double rel, double lo, double einv, int n) {
-  const int c = (int)floor((rel - lo) * einv);
-  return min(max(c, 0), n - 1);
+// Cell coordinate along one axis, clamped into the grid; `out` is set when
+// the atom lies outside it.
+__device__ __forceinline__ int cell_coord(double rel, double lo, double einv, int n, bool& out) {
+  const double u = floor((rel - lo) * einv);
+  out |= !(u >= 0.0 && u < (double)n);
+  return u >= 0.0 ? (u < (double)n ? (int)u : n - 1) : 0;  // NaN: cell 0 (flagged non-finite elsewhere)
 }
 
 // Bin the atoms of flagged wires (positions from the caller's FP64 array).
@@ -169,9 +176,11 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
     const int wi = nw.wl_wire[k];
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (idx - nw.wl_atom[k]);
-    const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0]);
-    const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1]);
-    const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2]);
+    bool out = false;
+    const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0], out);
+    const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1], out);
+    const int cz = cell_coord(x[2 * N + i] - w.origin[2], w.glo[2], w.einv[2], w.nc[2], out);
+    if (out) atomicOr(&wire_status[wi], kWireGridClamp);
     const int64_t c = w.cell_base + ((int64_t)cx * w.nc[1] + cy) * w.nc[2] + cz;
     cell_of[i] = (cx << 20) | (cy << 10) | cz;
     const int slot = atomicAdd(&cell_count[c], 1);

@@ -28,6 +28,7 @@ using namespace tbsma;
 namespace {
 
 constexpr int kGraphChunk = 50;  // steps per captured graph
+constexpr int64_t kGrowCheckSteps = 1000;  // steps between cell-grid checks inside one step call
 
 // An NVTX range over one library call, for timeline tools (nsys): the
 // header-only NVTX3 API does nothing unless a tool is attached.  Inside the
@@ -103,6 +104,12 @@ struct tbsma_ctx {
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
+  int64_t* rebuilt = nullptr;  // [2] wires and atoms whose lists were built (accumulated)
+  tbsma_wire* wires_d = nullptr;  // the wire table of tbsma_init (per-wire bounding boxes)
+  double* bbox_d = nullptr;       // [W][7] bounding boxes and mobile counts (k_bbox)
+  int64_t cells_alloc = 0;        // capacity of cell_count / cell_atoms, cells
+  double cell_edge = 0.0;         // smallest cell edge of the grids (list radius + guard), A
+  std::vector<cudaEvent_t> prof_ev;  // event pool of tbsma_step_profile
   int64_t* last_build = nullptr;  // per wire: step of its last list build
   uint8_t* banked = nullptr;      // per wire: rows in bank-group order at its last build
   uint32_t* wire_status = nullptr;
@@ -131,7 +138,8 @@ struct tbsma_ctx {
   double inv_m = 0.0;
 
   NlWork nw() const {
-    return NlWork{flag, wl_wire, wl_cell, wl_atom, n_flagged, n_rebuilds, chains, last_build, banked};
+    return NlWork{flag,   wl_wire,    wl_cell, wl_atom, n_flagged, n_rebuilds,
+                  chains, last_build, banked,  rebuilt};
   }
 };
 
@@ -172,6 +180,25 @@ tbsma_status alloc(tbsma_ctx* c, T** p, size_t count) {
 
 inline unsigned grid_for(int64_t threads, int block) {
   return (unsigned)std::max<int64_t>(1, (threads + block - 1) / block);
+}
+
+// Cell grid of one wire around its bounding box lo[3], hi[3] (absolute A),
+// the fixed-point origin d.origin already set: cell edge >= rl (the list
+// radius with a guard), across the axis a margin of rl, along it half the
+// wire's extent plus rl at each end (room to double its length before an
+// atom leaves the grid).  False if an axis would need more than 1023 cells.
+bool plan_grid(WireDev& d, const double* lo, const double* hi, double rl) {
+  for (int k = 0; k < 3; ++k) {
+    const double margin = (k == 0 ? 0.5 * (hi[k] - lo[k]) : 0.0) + rl;
+    const double glo = lo[k] - d.origin[k] - margin, ghi = hi[k] - d.origin[k] + margin;
+    const double cells = std::floor((ghi - glo) / rl);
+    if (!(cells <= 1023.0)) return false;
+    const int n = std::max(1, (int)cells);
+    d.glo[k] = glo;
+    d.einv[k] = n / (ghi - glo);
+    d.nc[k] = n;
+  }
+  return true;
 }
 
 void fill_pair_consts(tbsma_ctx* c) {
@@ -435,9 +462,34 @@ tbsma_status enqueue_steps_baro(tbsma_ctx* c, cudaStream_t s, int n, double dt) 
   return TBSMA_OK;
 }
 
+// Optional per-phase timing of directly enqueued steps (tbsma_step_profile):
+// an event is recorded after each phase and tagged with the phase it closes.
+struct PhaseMarks {
+  tbsma_ctx* c;
+  std::vector<int> tag;  // tag[k]: the phase that ended at event k (-1: the start)
+  cudaError_t err = cudaSuccess;
+  void mark(cudaStream_t s, int phase) {
+    const size_t k = tag.size();
+    if (k >= c->prof_ev.size()) {
+      cudaEvent_t e = nullptr;
+      const cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) {
+        err = r;
+        return;
+      }
+      c->prof_ev.push_back(e);
+    }
+    const cudaError_t r = cudaEventRecord(c->prof_ev[k], s);
+    if (r != cudaSuccess) err = r;
+    tag.push_back(phase);
+  }
+};
+
 // n consecutive steps: first integrate with a half kick, the rest with a
 // merged full kick, and a closing half kick after the last force pass.
-tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
+// With `pm`, the list rebuild chain and the two pair passes are enqueued
+// one by one with an event after each phase (same kernels, same order).
+tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt, PhaseMarks* pm = nullptr) {
   if (barostat(c)) return enqueue_steps_baro(c, s, n, dt);
   const double hk = 0.5 * dt * c->inv_m;
   for (int k = 0; k < n; ++k) {
@@ -446,14 +498,27 @@ tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt) {
     if (nose_hoover(c)) nh_boundary(c, s, dt, k == 0 ? 0.0 : hk, k == 0 ? 2 : 3);
     if (k == 0) integrate<1>(c, s, dt);
     else integrate<2>(c, s, dt);
-    TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
-    TB_TRY(launch_pair<false>(c, s, c->prec));
+    if (!pm) {
+      TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
+      TB_TRY(launch_pair<false>(c, s, c->prec));
+      continue;
+    }
+    pm->mark(s, TBSMA_PHASE_INTEGRATE);
+    k_nl_plan<<<1, 1024, 0, s>>>(c->W, c->nw(), c->wd, 0, 1, c->step_counter, c->step_counter);
+    pm->mark(s, TBSMA_PHASE_PLAN);
+    TB_TRY(launch_rebuild(c, s));
+    pm->mark(s, TBSMA_PHASE_REBUILD);
+    TB_TRY(launch_one_pass(c, s, 1));
+    pm->mark(s, TBSMA_PHASE_DENSITY);
+    TB_TRY(launch_one_pass(c, s, 2));
+    pm->mark(s, TBSMA_PHASE_FORCE);
   }
   half_kick(c, s, hk);
   if (nose_hoover(c)) {  // the last step's end half step
     nh_boundary(c, s, dt, 0.0, 1);
     k_nh_scale<<<grid_for(c->N, 256), 256, 0, s>>>(c->N, c->v, c->meta, c->nh);
   }
+  if (pm) pm->mark(s, TBSMA_PHASE_KICK);
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
@@ -513,19 +578,135 @@ tbsma_status read_status(tbsma_ctx* c, std::vector<uint32_t>& st) {
   return TBSMA_OK;
 }
 
+// Replace the cell arrays by ones of `cells` cells (contents are not kept:
+// cells carry nothing from one list build to the next).  Drops the captured
+// graph, whose kernels hold the old pointers.
+tbsma_status realloc_cells(tbsma_ctx* c, int64_t cells) {
+  auto release = [&](void* p) {
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
+    cudaFree(p);
+  };
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  release(c->cell_count);
+  release(c->cell_atoms);
+  c->cell_count = nullptr;
+  c->cell_atoms = nullptr;
+  c->cells_alloc = 0;
+  TB_TRY(alloc(c, &c->cell_count, cells));
+  TB_TRY(alloc(c, &c->cell_atoms, (size_t)cells * kCellCap));
+  c->cells_alloc = cells;
+  return TBSMA_OK;
+}
+
+// Grow the cell grids of the wires whose status (st, just read) carries
+// kWireGridClamp or kWireCellOverflow: re-plan each around its current
+// bounding box (plan_grid, the fixed-point origin unchanged), give every
+// wire its new first cell, enlarge the cell arrays if needed (by at least
+// a quarter), clear the two bits (in st and on the device) and rebuild
+// those wires' lists.  Where a cell overflowed, the forces at the current
+// positions are recomputed as well (the list they came from missed atoms).
+// Poisoned (non-finite) wires keep their grid; their clamp bit is cleared.
+tbsma_status grow_grids(tbsma_ctx* c, std::vector<uint32_t>& st) {
+  const uint32_t grow_bits = kWireGridClamp | kWireCellOverflow;
+  std::vector<int> g;
+  bool overflowed = false;
+  for (int w = 0; w < c->W; ++w) {
+    if (!(st[w] & grow_bits)) continue;
+    if (st[w] & kWireNonFinite) {
+      st[w] &= ~kWireGridClamp;
+      continue;
+    }
+    g.push_back(w);
+    overflowed |= (st[w] & kWireCellOverflow) != 0;
+  }
+  if (!g.empty()) {
+    k_bbox<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wires_d, c->x, c->N, c->kind,
+                                                         c->bbox_d);
+    TB_CUDA(c, cudaGetLastError());
+    std::vector<double> bbox((size_t)c->W * 7);
+    TB_CUDA(c, cudaMemcpyAsync(bbox.data(), c->bbox_d, sizeof(double) * 7 * c->W,
+                               cudaMemcpyDeviceToHost, c->stream));
+    TB_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<WireDev> grids = c->wires_h;
+    for (int w : g) {
+      const double* lo = &bbox[(size_t)w * 7];
+      if (!(std::isfinite(lo[0]) && std::isfinite(lo[1]) && std::isfinite(lo[2]) &&
+            std::isfinite(lo[3]) && std::isfinite(lo[4]) && std::isfinite(lo[5])))
+        continue;  // non-finite since the status was read: left to the verdict
+      if (!plan_grid(grids[w], lo, lo + 3, c->cell_edge)) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "wire %d: its cell grid would need more than 1023 cells per axis", w);
+        return fail(c, TBSMA_EOVERFLOW, buf);
+      }
+    }
+    int64_t cells = 0;
+    for (int w = 0; w < c->W; ++w) {
+      grids[w].cell_base = cells;
+      cells += (int64_t)grids[w].nc[0] * grids[w].nc[1] * grids[w].nc[2];
+    }
+    if (cells > c->cells_alloc) TB_TRY(realloc_cells(c, std::max(cells, c->cells_alloc + c->cells_alloc / 4)));
+    c->wires_h = grids;
+    c->n_cells = cells;
+    TB_CUDA(c, cudaMemcpyAsync(c->wd, c->wires_h.data(), sizeof(WireDev) * c->W,
+                               cudaMemcpyHostToDevice, c->stream));
+    std::vector<int32_t> flag(c->W);
+    TB_CUDA(c, cudaMemcpyAsync(flag.data(), c->flag, sizeof(int32_t) * c->W, cudaMemcpyDeviceToHost,
+                               c->stream));
+    TB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int w : g) {
+      flag[w] = 1;
+      st[w] &= ~grow_bits;
+    }
+    TB_CUDA(c, cudaMemcpyAsync(c->flag, flag.data(), sizeof(int32_t) * c->W, cudaMemcpyHostToDevice,
+                               c->stream));
+  }
+  TB_CUDA(c, cudaMemcpyAsync(c->wire_status, st.data(), sizeof(uint32_t) * c->W,
+                             cudaMemcpyHostToDevice, c->stream));
+  if (!g.empty()) {
+    TB_TRY(launch_nl(c, c->stream, 0, 0, nullptr));
+    if (overflowed) TB_TRY(launch_pair<false>(c, c->stream, c->prec));
+  }
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));  // st (host) was read by the copy above
+  return TBSMA_OK;
+}
+
+// Read the wires' status words and grow the grids that need it.  Returns
+// whether some wire's cell had overflowed (its grid is grown now, but the
+// steps since its previous list build ran on a list that missed atoms).
+tbsma_status check_grids(tbsma_ctx* c, std::vector<uint32_t>& st, int& overflowed_wire) {
+  TB_TRY(read_status(c, st));
+  overflowed_wire = -1;
+  uint32_t grow = 0;
+  for (int w = 0; w < c->W; ++w) {
+    grow |= st[w] & (kWireGridClamp | kWireCellOverflow);
+    if ((st[w] & kWireCellOverflow) && overflowed_wire < 0) overflowed_wire = w;
+  }
+  if (grow) TB_TRY(grow_grids(c, st));
+  return TBSMA_OK;
+}
+
 tbsma_status status_verdict(tbsma_ctx* c) {
   std::vector<uint32_t> st;
-  TB_TRY(read_status(c, st));
+  int ofw = -1;
+  TB_TRY(check_grids(c, st, ofw));
   uint32_t any = 0;
   int first = -1;
   for (int w = 0; w < c->W; ++w) {
     any |= st[w];
     if (st[w] && first < 0) first = w;
   }
-  if (!any) return TBSMA_OK;
-  char buf[160];
+  char buf[224];
+  if (!any) {
+    if (ofw < 0) return TBSMA_OK;
+    snprintf(buf, sizeof buf,
+             "wire %d: a cell overflowed; its cell grid is grown and its list rebuilt, but the steps "
+             "since its previous list build used a list that missed atoms (repeat them from saved state)",
+             ofw);
+    return fail(c, TBSMA_EOVERFLOW, buf);
+  }
   snprintf(buf, sizeof buf, "wire %d status 0x%x (bits over all wires 0x%x)", first, st[first], any);
-  if (any & (kWireNbrOverflow | kWireCellOverflow)) return fail(c, TBSMA_EOVERFLOW, buf);
+  if (ofw >= 0 || (any & (kWireNbrOverflow | kWireCellOverflow))) return fail(c, TBSMA_EOVERFLOW, buf);
   return fail(c, TBSMA_EWIRE, buf);
 }
 
@@ -669,16 +850,14 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   if ((s = alloc(c, &(ptr), (n))) != TBSMA_OK) \
     return bail(s);
   // per-wire bounding boxes on the device (init only)
-  tbsma_wire* wires_d = nullptr;
-  double* bbox_d = nullptr;
-  ALLOC(wires_d, W);
-  ALLOC(bbox_d, (size_t)W * 7);
-  if (cudaMemcpyAsync(wires_d, wires, sizeof(tbsma_wire) * W, cudaMemcpyHostToDevice, c->stream) !=
+  ALLOC(c->wires_d, W);
+  ALLOC(c->bbox_d, (size_t)W * 7);
+  if (cudaMemcpyAsync(c->wires_d, wires, sizeof(tbsma_wire) * W, cudaMemcpyHostToDevice, c->stream) !=
       cudaSuccess)
     return bail(TBSMA_ECUDA);
-  k_bbox<<<std::min(W, 65535), 256, 0, c->stream>>>(W, wires_d, x, N, kind, bbox_d);
+  k_bbox<<<std::min(W, 65535), 256, 0, c->stream>>>(W, c->wires_d, x, N, kind, c->bbox_d);
   std::vector<double> bbox((size_t)W * 7);
-  if (cudaMemcpyAsync(bbox.data(), bbox_d, sizeof(double) * 7 * W, cudaMemcpyDeviceToHost,
+  if (cudaMemcpyAsync(bbox.data(), c->bbox_d, sizeof(double) * 7 * W, cudaMemcpyDeviceToHost,
                       c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(TBSMA_ECUDA);
@@ -686,6 +865,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   // per-wire cell grids: edge >= list radius (with a 1e-4 relative guard so
   // rounding in the cell coordinate never separates two atoms by two cells)
   const double rl = std::sqrt((double)c->rlist2) * 1.0001;
+  c->cell_edge = rl;
   c->wires_h.resize(W);
   int64_t cells = 0, slots = 0;
   for (int w = 0; w < W; ++w) {
@@ -707,21 +887,16 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       // origin on the 2^-26 grid, so that fixed_coord's offset is an exact integer
       d.origin[k] = std::nearbyint(0.5 * (lo + hi) * kFixedScale) / kFixedScale;
       d.ofixm[k] = kFixedMagic - d.origin[k] * kFixedScale;
-      // along the axis leave room for strain up to 1.0 (each end +L/2)
-      const double margin = (k == 0 ? 0.5 * (hi - lo) : 0.0) + rl;
-      const double glo = lo - d.origin[k] - margin, ghi = hi - d.origin[k] + margin;
-      const int n = std::max(1, (int)std::floor((ghi - glo) / rl));
-      if (n > 1023) return bail(fail(c, TBSMA_EINVAL, "wire too large for the cell grid (1023 cells per axis)"));
-      d.glo[k] = glo;
-      d.einv[k] = n / (ghi - glo);
-      d.nc[k] = n;
     }
+    if (!plan_grid(d, &bbox[w * 7], &bbox[w * 7 + 3], rl))
+      return bail(fail(c, TBSMA_EINVAL, "wire too large for the cell grid (1023 cells per axis)"));
     d.cell_base = cells;
     cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
     d.slot_base = slots;
     slots += (d.n + kSlotTile - 1) / kSlotTile * (int64_t)kSlotTile;
   }
   c->n_cells = cells;
+  c->cells_alloc = cells;
   c->NS = slots;
   const int64_t NS = slots;
 
@@ -755,6 +930,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);
+  ALLOC(c->rebuilt, 2);
   ALLOC(c->last_build, W);
   ALLOC(c->banked, W);
   ALLOC(c->wire_status, W);
@@ -772,6 +948,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
@@ -856,13 +1033,30 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
   TB_TRY(set_dt(c, dt_fs));
   const int chunk = (int)std::min<int64_t>(n_steps, kGraphChunk);
   if (!c->graph.exec || c->graph_dt != dt_fs || c->graph.steps != chunk) TB_TRY(capture(c, chunk, dt_fs));
-  int64_t left = n_steps;
-  while (left >= c->graph.steps) {
-    TB_CUDA(c, cudaGraphLaunch(c->graph.exec, c->stream));
-    left -= c->graph.steps;
+  int64_t left = n_steps, since_check = 0;
+  while (left > 0) {
+    if (left >= chunk) {
+      if (!c->graph.exec) TB_TRY(capture(c, chunk, dt_fs));  // dropped by a grid growth
+      TB_CUDA(c, cudaGraphLaunch(c->graph.exec, c->stream));
+      left -= chunk;
+      c->steps_done += chunk;
+      since_check += chunk;
+    } else {
+      TB_TRY(enqueue_steps(c, c->stream, (int)left, dt_fs));
+      c->steps_done += left;
+      left = 0;
+    }
+    // a long call looks at the status words every kGrowCheckSteps steps, so
+    // that a wire whose atoms leave its cell grid gets a larger grid before
+    // the clamped edge cells can overflow; a cell overflow ends the call
+    if (left > 0 && since_check >= kGrowCheckSteps) {
+      since_check = 0;
+      std::vector<uint32_t> st;
+      int ofw = -1;
+      TB_TRY(check_grids(c, st, ofw));
+      if (ofw >= 0) return status_verdict(c);
+    }
   }
-  if (left > 0) TB_TRY(enqueue_steps(c, c->stream, (int)left, dt_fs));
-  c->steps_done += n_steps;
   return status_verdict(c);
 }
 
@@ -879,6 +1073,8 @@ tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
   TB_CUDA(c, cudaGetLastError());
   TB_CUDA(c, cudaMemcpyAsync(out, c->obs_d, sizeof(tbsma_obs) * c->W, cudaMemcpyDeviceToHost, c->stream));
   TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  // the grid-clamp mark is not a fault, and status_verdict grows the grid now
+  for (int w = 0; w < c->W; ++w) out[w].status &= ~(int32_t)kWireGridClamp;
   return status_verdict(c);
 }
 
@@ -1184,6 +1380,45 @@ tbsma_status tbsma_run_pass(tbsma_ctx* c, int32_t pass, int32_t reps) {
   return TBSMA_OK;
 }
 
+tbsma_status tbsma_step_profile(tbsma_ctx* c, int64_t n_steps, double dt_fs, double* phase_ms) {
+  NvtxRange range_("tbsma_step_profile");
+  if (!c || !phase_ms) return TBSMA_EINVAL;
+  if (n_steps < 1 || n_steps > (1 << 20) || !(dt_fs > 0.0))
+    return fail(c, TBSMA_EINVAL, "n_steps must be in [1, 2^20] and dt > 0");
+  if (barostat(c)) return fail(c, TBSMA_EINVAL, "tbsma_step_profile does not cover the barostat's steps");
+  TB_TRY(set_dt(c, dt_fs));
+  for (int p = 0; p < TBSMA_N_PHASES; ++p) phase_ms[p] = 0.0;
+  PhaseMarks pm{c, {}, cudaSuccess};
+  pm.mark(c->stream, -1);
+  int64_t left = n_steps;
+  while (left > 0) {  // sequences of at most one graph chunk, as the graph replays run them
+    const int n = (int)std::min<int64_t>(left, kGraphChunk);
+    TB_TRY(enqueue_steps(c, c->stream, n, dt_fs, &pm));
+    left -= n;
+  }
+  if (pm.err != cudaSuccess) return cuda_fail(c, pm.err, "cudaEventRecord");
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t k = 1; k < pm.tag.size(); ++k) {
+    float ms = 0.f;
+    TB_CUDA(c, cudaEventElapsedTime(&ms, c->prof_ev[k - 1], c->prof_ev[k]));
+    phase_ms[pm.tag[k]] += ms;
+  }
+  c->steps_done += n_steps;
+  return status_verdict(c);
+}
+
+tbsma_status tbsma_get_rebuild_stats(tbsma_ctx* c, int64_t* out) {
+  if (!c || !out) return TBSMA_EINVAL;
+  int64_t h[3] = {0, 0, 0};
+  TB_CUDA(c, cudaMemcpyAsync(h, c->chains, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaMemcpyAsync(h + 1, c->rebuilt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = h[2];
+  return TBSMA_OK;
+}
+
 tbsma_status tbsma_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                                  void* cuda_stream) {
   if (n < 0 || (n > 0 && (!ctr || !key || !out))) return TBSMA_EINVAL;
@@ -1212,6 +1447,7 @@ void tbsma_destroy(tbsma_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   for (void* p : c->eam_allocs) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1232,11 +1468,6 @@ namespace {
 
 constexpr int kNoAllocMaxAtoms = TBSMA_NOALLOC_MAX_ATOMS;
 static __device__ __align__(256) double g_noalloc_inv[kNoAllocMaxAtoms];
-
-// Device address of g_noalloc_inv, looked up once per device with that
-// device current (in host code the symbol's name is only a host-side stand-in).
-constexpr int kNoAllocMaxDevices = 64;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 __global__ void k_noalloc_density(int n, const double* __restrict__ x, PairConsts pc,
                                   double* __restrict__ inv) {
@@ -1292,12 +1523,21 @@ extern "C" tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t
   if (!x || !f_out) return TBSMA_EINVAL;
   const tbsma_params& P = *params;
   if (!(P.r0 > 0 && P.r_cut > 0 && P.xi > 0 && P.A >= 0)) return TBSMA_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return TBSMA_ECUDA;
-  if (!g_noalloc_ptr[dev]) {
+  // A launch error that an earlier, unrelated call left pending is not ours
+  // to report or to clear: give up before launching anything.
+  if (cudaPeekAtLastError() != cudaSuccess) return TBSMA_ECUDA;
+  // The scratch array's device address, looked up on every call with the
+  // caller's device (and context) current: in host code the array's name is
+  // only a host-side stand-in, and the address differs per device and per
+  // context (after cudaDeviceReset the module is loaded again elsewhere).
+  // The lookup is a runtime query, cheap next to the n^2 kernels, and keeps
+  // no host-side state, so concurrent first calls from several host
+  // threads are safe.
+  double* inv = nullptr;
+  {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_inv) != cudaSuccess || !p) return TBSMA_ECUDA;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+    inv = static_cast<double*>(p);
   }
   PairConsts pc{};
   pc.rc2 = P.r_cut * P.r_cut;
@@ -1312,7 +1552,8 @@ extern "C" tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t
   const int block = 128;
   const unsigned grid = (unsigned)((n_atoms + block - 1) / block);
   // every inv slot the force pass reads is written by the density pass first
-  k_noalloc_density<<<grid, block, 0, s>>>(n_atoms, x, pc, g_noalloc_ptr[dev]);
-  k_noalloc_force<<<grid, block, 0, s>>>(n_atoms, x, pc, g_noalloc_ptr[dev], f_out);
+  k_noalloc_density<<<grid, block, 0, s>>>(n_atoms, x, pc, inv);
+  if (cudaGetLastError() != cudaSuccess) return TBSMA_ECUDA;
+  k_noalloc_force<<<grid, block, 0, s>>>(n_atoms, x, pc, inv, f_out);
   return cudaGetLastError() == cudaSuccess ? TBSMA_OK : TBSMA_ECUDA;
 }

@@ -24,6 +24,8 @@ STATUS_NAMES = {
     7: "ESTATE",
 }
 WIRE_NONFINITE, WIRE_NBR_OVERFLOW, WIRE_CELL_OVERFLOW, WIRE_RANGE = 1, 2, 4, 8
+WIRE_GRID_CLAMP = 16  # not a fault: the wire's cell grid is grown at the next status read
+PHASES = ("integrate", "plan", "rebuild", "density", "force", "kick")  # tbsma_step_profile
 
 
 class TbsmaError(RuntimeError):
@@ -144,6 +146,8 @@ SIGNATURES = [
     ("tbsma_get_neighbors", ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     ("tbsma_set_launch", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tbsma_run_pass", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("tbsma_step_profile", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P]),
+    ("tbsma_get_rebuild_stats", ctypes.c_int, [_P, _P]),
     ("tbsma_set_protocol", ctypes.c_int, [_P, _P]),
     ("tbsma_get_thermostat", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_get_barostat", ctypes.c_int, [_P, _P, _P]),
@@ -327,6 +331,23 @@ class Engine:
         self._check(lib().tbsma_get_rebuild_chains(self.ctx, ctypes.byref(n)),
                     "tbsma_get_rebuild_chains")
         return int(n.value)
+
+    def rebuild_stats(self) -> dict:
+        """List-build accounting since init (tbsma_get_rebuild_stats): chain
+        launches, wires rebuilt and atoms rebuilt."""
+        out = np.zeros(3, dtype=np.int64)
+        self._check(lib().tbsma_get_rebuild_stats(self.ctx, out.ctypes.data_as(ctypes.c_void_p)),
+                    "tbsma_get_rebuild_stats")
+        return {"chains": int(out[0]), "wires": int(out[1]), "atoms": int(out[2])}
+
+    def step_profile(self, n_steps: int, dt: float = 2.0) -> dict:
+        """n_steps steps enqueued directly with an event after each phase
+        (tbsma_step_profile): summed ms per phase."""
+        out = np.zeros(len(PHASES))
+        self._check(lib().tbsma_step_profile(self.ctx, int(n_steps), float(dt),
+                                             out.ctypes.data_as(ctypes.c_void_p)),
+                    "tbsma_step_profile")
+        return dict(zip(PHASES, (float(v) for v in out)))
 
     def set_launch(self, block_threads: int, window_atoms: int):
         """Pair-pass tile size (atoms per block) and shared-memory window (atoms)."""

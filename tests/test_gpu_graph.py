@@ -51,3 +51,29 @@ def test_graph_and_direct_steps_agree_bitwise(tb, prec):
     assert ra.sum() > 3  # the wires did rebuild
     # one chain per step, plus the two builds of init and the report's refresh
     assert ca == cb == 300 + 3
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_profiled_steps_equal_graph_steps(tb, prec):
+    """tbsma_step_profile enqueues the same kernels in the same order as the
+    graph replays, only with an event after each phase: 120 profiled steps
+    (sequences of 50, 50 and 20) equal 120 steps of one step call bit for
+    bit, with the same list builds; the phase times are positive where the
+    phase does work, and the list-build accounting counts the init's two
+    full builds of every wire."""
+    b = workload("tiny_batch")
+    out = []
+    for profiled in (False, True):
+        eng = tb.Engine(b, precision=prec)
+        rs = eng.rebuild_stats()
+        assert rs == {"chains": 2, "wires": 2 * b.n_wires, "atoms": 2 * b.n_atoms}
+        eng.init_velocities()
+        ph = eng.step_profile(120, 2.0) if profiled else eng.step(120, 2.0)
+        out.append((eng.positions(), eng.velocities(), eng.rebuild_stats(), ph))
+        eng.close()
+    (xa, va, ra, _), (xb, vb, rb, ph) = out
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    assert ra == rb and ra["chains"] == 2 + 120 and ra["wires"] > 2 * b.n_wires
+    assert set(ph) == {"integrate", "plan", "rebuild", "density", "force", "kick"}
+    assert all(v > 0.0 for v in ph.values())

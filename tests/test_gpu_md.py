@@ -103,3 +103,36 @@ def test_force_check_every_1000_steps_along_a_pull(tb):
     ob = eng.observables()
     assert ob["strain"][0] == pytest.approx(1e8 * 5000 * 2.0 * 1e-15, rel=1e-9)
     eng.close()
+
+
+@pytest.mark.parametrize("T", [10.0, 298.0])
+def test_nve_drift_over_one_ns_mixed(tb, T):
+    """The mixed integrator over 1 ns (500k steps) of NVE after 20 ps of
+    Langevin at T: its FP64 state takes FP32 increments whose velocity part
+    is rounded to nearest (an unbiased rounding; truncation would shrink
+    every position increment), and the linear drift of the total energy
+    per atom stays below 1e-4 eV/atom/ns."""
+    w, x = _relaxed_wire(tb, 2)
+    eq = Wire(x=x, kind=w.kind, diameter_nm=2.0, length_nm=6.0, L0=w.L0, temperature=T,
+              strain_rate=0.0, gamma=0.01, seed=9)
+    e_eq = tb.Engine(pack([eq]), precision="mixed")
+    e_eq.init_velocities()
+    e_eq.step(10000, 2.0)
+    x_eq, v_eq = e_eq.positions(), e_eq.velocities()
+    e_eq.close()
+    nve = Wire(x=x_eq, kind=w.kind, diameter_nm=2.0, length_nm=6.0, L0=w.L0, temperature=T,
+               strain_rate=0.0, gamma=0.0, seed=9)
+    eng = tb.Engine(pack([nve]), precision="mixed")
+    eng.upload(None, np.ascontiguousarray(v_eq.T).reshape(-1))
+    t_ps, e = [], []
+    for k in range(101):  # 1 ns in 5000-step blocks (10 ps)
+        if k:
+            eng.step(5000, 2.0)
+        ob = eng.observables()
+        t_ps.append(k * 10.0)
+        e.append((ob["e_pot"][0] + ob["e_kin"][0]) / w.n)
+    e = np.array(e)
+    slope = np.polyfit(np.array(t_ps) * 1e-3, e, 1)[0]  # eV/atom/ns
+    print(f"NVE drift mixed {T} K over 1 ns: {slope:.3e} eV/atom/ns, std {np.std(e):.2e} eV/atom")
+    assert abs(slope) < 1e-4, (T, slope)
+    eng.close()

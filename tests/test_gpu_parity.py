@@ -413,6 +413,41 @@ def test_full_size_batch_sampled_against_oracle(tb, orc):
     eng.close()
 
 
+def test_full_size_sweep_sampled_against_oracle(tb, orc):
+    """The bench workload, the 2048-wire sweep (55.8M atoms, D 2-4 nm, L 5-120
+    nm), jittered, in the bench's launch shape and list skin: every wire's
+    net force vanishes, and the smallest and the largest wire of each
+    diameter match the oracle atom by atom."""
+    from bench import LAUNCH, R_SKIN
+    from inputs.configs import WORKLOADS
+
+    specs = WORKLOADS["sweep2048"]()
+    b = workload("sweep2048")
+    b.x = jitter(b.x, 0.05, 23)
+    eng = tb.Engine(b, precision="mixed", params=tb.au_params(r_skin=R_SKIN))
+    eng.set_launch(*LAUNCH)
+    F32, _ = eng.forces(f32=True, f64=False)
+    F32 = F32.double().cpu().numpy()
+    eng.close()
+    for w in range(b.n_wires):
+        s = b.wire_slice(w)
+        net = np.abs(F32[s].sum(axis=0)).max()
+        assert net < 1e-6 * np.abs(F32[s]).sum()
+    picks = []
+    for d in (2.0, 3.0, 4.0):
+        ws = [w for w, sp in enumerate(specs) if sp.diameter_nm == d]
+        picks += [min(ws, key=lambda w: b.n[w]), max(ws, key=lambda w: b.n[w])]
+    for w in picks:
+        s = b.wire_slice(w)
+        ref = orc.tbsma(b.x[s], brute_max=0)
+        amb = ambiguous_atoms(orc, b.x[s], orc.AU.r_cut, 5e-6)
+        ok = np.ones(b.n[w], bool)
+        ok[amb] = False
+        d, fm, norm = force_errors(F32[s], ref.F)
+        assert np.max(d[ok] / ref.S[ok]) <= 1e-5
+        assert norm <= 1e-5
+
+
 def test_force_error_gate_on_thermalised_wires(tb, orc):
     """The mixed-precision force check (same positions, same list, same
     cutoff decisions) on 8 D3 x L40 wires after 1000 steps at 10 K, where

@@ -5,7 +5,9 @@ or a latency-critical loop that cannot afford a device-wide cudaMalloc).
 Its FP64 forces must equal those of the regular path (tbsma_compute_forces
 of an FP64 context) within the FP64 parity tolerance, on two calls in a row
 of different sizes, so that nothing left in its shared scratch array from
-one call leaks into the next.  This file is collected last on purpose.
+one call leaks into the next; the first call is also held against the FP64
+CPU oracle (Eq. 1-3 evaluated by brute force) with the parity tests'
+tolerance.  This file is collected last on purpose.
 """
 
 import ctypes
@@ -60,10 +62,10 @@ def _clear_of_cutoff(x, r_cut=5.8, band=1e-9):
     return not np.any(np.abs(d - r_cut) < band)
 
 
-def test_noalloc_forces_match_regular_path_twice(tb):
+def test_noalloc_forces_match_regular_path_twice(tb, orc):
     a = jitter(fcc_wire(2.0, 6.0).x, 0.05, seed=31)  # 1035 atoms
     b = jitter(fcc_wire(2.0, 3.5).x, 0.08, seed=32) + 100.0  # 621 atoms, elsewhere
-    for x in (a, b):
+    for k, x in enumerate((a, b)):
         assert _clear_of_cutoff(x)  # the two paths then see the same pair set
         got = _noalloc(tb, x)
         ref = _regular(tb, x)
@@ -72,6 +74,15 @@ def test_noalloc_forces_match_regular_path_twice(tb):
         # FP64 tolerance of the parity tests: only the summation order differs
         assert np.all(np.isfinite(got))
         assert np.all(d <= 1e-12 * fm + 1e-14)
+        if k == 0:
+            # and against the oracle: |dF_i| <= 1e-12 |F_i| where |F_i| is not
+            # tiny next to the atom's pair-force scale S_i, else <= 1e-12 S_i
+            o = orc.tbsma(x, brute_max=3000)
+            d = np.linalg.norm(got - o.F, axis=1)
+            fo = np.linalg.norm(o.F, axis=1)
+            big = fo >= 1e-6 * o.S
+            assert np.all(d[big] <= 1e-12 * fo[big])
+            assert np.all(d[~big] <= 1e-12 * o.S[~big])
 
 
 def test_noalloc_rejects_oversized_input(tb):
