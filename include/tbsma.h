@@ -417,8 +417,9 @@ tbsma_status tbsma_get_wire_status(tbsma_ctx* ctx, int32_t* status_host);
  * unused entries -1).  cap must equal tbsma_nbr_capacity(ctx). */
 int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
 
-/* Launch accounting: how many times the four kernels of the list-rebuild
- * chain (cell clear, bin, sort, build) were launched since tbsma_init: once
+/* Launch accounting: how many times the kernels of the list-rebuild chain
+ * (envelope, cell clear, bin, sort, cell build, and in MIXED contexts the
+ * slab build) were launched since tbsma_init: once
  * per step and per position refresh (they return at once when no wire is
  * flagged).  Synchronises.  Errors: EINVAL (null). */
 tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* ctx, int64_t* n);

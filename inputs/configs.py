@@ -91,6 +91,12 @@ def _sweep2048() -> list[WireSpec]:
     return out
 
 
+def _sweep144() -> list[WireSpec]:
+    """The first 144 trajectories of the sweep: one wire of every (D, L, T)
+    class (3.9M atoms), the small case of the sweep's kernel shapes."""
+    return _sweep2048()[:144]
+
+
 def _paper_table2() -> list[WireSpec]:
     """The paper's benchmark systems (Table 2, Results "TB-SMA benchmarks"):
     unstretched D 3.1 nm wires of length 20.4 k nm, k = 1..12 (8.9k-106k
@@ -120,6 +126,8 @@ WORKLOADS = {
     "ragged512": _ragged512,
     # 2048 trajectories over D {2,3,4} x 24 lengths 5..120 nm x T {10,298}
     "sweep2048": _sweep2048,
+    # one wire of each of the sweep's 144 classes (3.9M atoms): its small case
+    "sweep144": _sweep144,
     # the paper's Table 2 systems: D3.1 x L20.4k nm, k = 1..12, 10 K, no pull
     "paper_table2": _paper_table2,
     "tiny_batch": _tiny_batch,

@@ -26,6 +26,9 @@ struct NlWork {
   int32_t* wl_wire;     // [W] flagged wires
   int64_t* wl_cell;     // [W+1] prefix of their cell counts
   int64_t* wl_atom;     // [W+1] prefix of their atom counts
+  int64_t* wl_tile;     // [W+1] prefix of their tiles (kSlotTile consecutive atoms each)
+  uint8_t* mode;        // [W] build of the wire at this rebuild: 0 slab, 1 cells (k_nl_envelope)
+  float2* xenv;         // [N] along the atom order: prefix max and suffix min of x (k_nl_envelope)
   int32_t* n_flagged;   // [1]
   int32_t* n_rebuilds;  // [W]
   int64_t* chains;      // [1] launches of the rebuild chain (clear, bin, sort, build)
@@ -34,9 +37,14 @@ struct NlWork {
   int64_t* rebuilt;     // [2] wires and atoms whose lists were built, accumulated
 };
 
-// Shortest life (steps) of a wire's previous list for which its rebuilt
-// rows are put in bank-group order (see k_nl_build).
+// Shortest life (steps) of a wire's previous list for which the cell build
+// puts its rebuilt rows in bank-group order (see k_nl_build; the slab build
+// always does).
 constexpr int64_t kBankedInterval = 128;
+
+// Atoms per tile of the pair passes (see k_slot_order); the slab build
+// works on the same tiles.
+constexpr int kSlotTile = 256;
 
 // Binary search: largest k < nf with pre[k] <= idx.
 __device__ __forceinline__ int wl_find(const int64_t* pre, int nf, int64_t idx) {
@@ -61,34 +69,30 @@ __device__ __forceinline__ T warp_scan(T v) {
   return v;
 }
 
-// Exclusive block scan of three counters (blockDim.x = 1024: 32 warps);
-// returns the block totals in tot[3].
-__device__ __forceinline__ void block_scan3(int64_t& a, int64_t& b, int64_t& c, int64_t* tot) {
-  __shared__ int64_t s[3][32];
+// Exclusive block scan of four counters (blockDim.x = 1024: 32 warps);
+// returns the block totals in tot[4].
+__device__ __forceinline__ void block_scan4(int64_t (&v)[4], int64_t* tot) {
+  __shared__ int64_t s[4][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ia = warp_scan(a), ib = warp_scan(b), ic = warp_scan(c);
-  if (lane == 31) {
-    s[0][warp] = ia;
-    s[1][warp] = ib;
-    s[2][warp] = ic;
+  int64_t inc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    inc[q] = warp_scan(v[q]);
+    if (lane == 31) s[q][warp] = inc[q];
   }
   __syncthreads();
   if (warp == 0) {
-    const int64_t x = s[0][lane], y = s[1][lane], z = s[2][lane];
-    const int64_t sx = warp_scan(x), sy = warp_scan(y), sz = warp_scan(z);
-    s[0][lane] = sx - x;  // exclusive prefix of the warp totals
-    s[1][lane] = sy - y;
-    s[2][lane] = sz - z;
-    if (lane == 31) {
-      tot[0] = sx;
-      tot[1] = sy;
-      tot[2] = sz;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t x = s[q][lane];
+      const int64_t sx = warp_scan(x);
+      s[q][lane] = sx - x;  // exclusive prefix of the warp totals
+      if (lane == 31) tot[q] = sx;
     }
   }
   __syncthreads();
-  a = s[0][warp] + ia - a;
-  b = s[1][warp] + ib - b;
-  c = s[2][warp] + ic - c;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = s[q][warp] + inc[q] - v[q];
 }
 
 // One block of 1024 threads: compact flagged wires, clear their flags,
@@ -100,27 +104,31 @@ __global__ void __launch_bounds__(1024)
     k_nl_plan(int W, NlWork nw, const WireDev* __restrict__ wd, int force_all, int count_rebuild,
               int64_t* step_counter, const int64_t* __restrict__ steps_now) {
   const int64_t steps = steps_now[0];
-  __shared__ int64_t tot[3];
+  __shared__ int64_t tot[4];
   const int t = threadIdx.x;
   const int chunk = (W + 1023) / 1024;
   const int w0 = min(W, t * chunk), w1 = min(W, w0 + chunk);
-  int64_t cells = 0, atoms = 0, cnt = 0;
+  auto tiles_of = [](int n) { return (int64_t)((n + kSlotTile - 1) / kSlotTile); };
+  int64_t v[4] = {0, 0, 0, 0};  // cells, atoms, tiles, wires
   for (int w = w0; w < w1; ++w) {
     if (force_all || nw.flag[w]) {
-      ++cnt;
-      cells += (int64_t)wd[w].nc[0] * wd[w].nc[1] * wd[w].nc[2];
-      atoms += wd[w].n;
+      v[0] += (int64_t)wd[w].nc[0] * wd[w].nc[1] * wd[w].nc[2];
+      v[1] += wd[w].n;
+      v[2] += tiles_of(wd[w].n);
+      v[3] += 1;
     }
   }
-  int64_t c_pre = cells, a_pre = atoms, k = cnt;
-  block_scan3(c_pre, a_pre, k, tot);
+  block_scan4(v, tot);
+  int64_t c_pre = v[0], a_pre = v[1], t_pre = v[2], k = v[3];
   for (int w = w0; w < w1; ++w) {
     if (force_all || nw.flag[w]) {
       nw.wl_wire[k] = w;
       nw.wl_cell[k] = c_pre;
       nw.wl_atom[k] = a_pre;
+      nw.wl_tile[k] = t_pre;
       c_pre += (int64_t)wd[w].nc[0] * wd[w].nc[1] * wd[w].nc[2];
       a_pre += wd[w].n;
+      t_pre += tiles_of(wd[w].n);
       ++k;
       nw.flag[w] = 0;
       if (count_rebuild) nw.n_rebuilds[w] += 1;
@@ -131,10 +139,11 @@ __global__ void __launch_bounds__(1024)
     }
   }
   if (t == 0) {
-    const int nf = (int)tot[2];
+    const int nf = (int)tot[3];
     nw.n_flagged[0] = nf;
     nw.wl_cell[nf] = tot[0];
     nw.wl_atom[nf] = tot[1];
+    nw.wl_tile[nf] = tot[2];
     if (step_counter) step_counter[0] += 1;
     nw.chains[0] += 1;
     nw.rebuilt[0] += nf;
@@ -149,6 +158,7 @@ __global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* c
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = wl_find(nw.wl_cell, nf, idx);
+    if (nw.mode[nw.wl_wire[k]] == 0) continue;  // the slab build takes this wire
     const WireDev& w = wd[nw.wl_wire[k]];
     cell_count[w.cell_base + (idx - nw.wl_cell[k])] = 0;
   }
@@ -174,6 +184,7 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = wl_find(nw.wl_atom, nf, idx);
     const int wi = nw.wl_wire[k];
+    if (nw.mode[wi] == 0) continue;  // the slab build takes this wire
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (idx - nw.wl_atom[k]);
     bool out = false;
@@ -200,6 +211,7 @@ __global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32
   for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
        idx += warps) {
     const int k = wl_find(nw.wl_cell, nf, idx);
+    if (nw.mode[nw.wl_wire[k]] == 0) continue;  // warp-uniform (one cell per warp)
     const int64_t c = wd[nw.wl_wire[k]].cell_base + (idx - nw.wl_cell[k]);
     const int cnt = min(cell_count[c], kCellCap);
     const int32_t m = lane < cnt ? cell_atoms[c * kCellCap + lane] : INT32_MAX;
@@ -210,10 +222,15 @@ __global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32
   }
 }
 
-// Distance test of the list build on the packed positions (modular fixed
-// point: exact differences; FP64 copies in an FP64 context).
+// Distance test of the list builds on the packed positions: modular fixed
+// point in fixed-point units squared (2^-52 A^2; the differences are exact
+// and rounded once to FP32, and the power-of-two scale commutes with every
+// rounding, so comparing against r_list^2 * 2^52 decides exactly as the
+// same test in A^2 would); FP64 copies in an FP64 context, in A^2.
 __device__ __forceinline__ float build_d2(int4 a, int4 b) {
-  const float dx = fixed_diff(b.x, a.x), dy = fixed_diff(b.y, a.y), dz = fixed_diff(b.z, a.z);
+  const float dx = (float)(int)((unsigned)b.x - (unsigned)a.x);
+  const float dy = (float)(int)((unsigned)b.y - (unsigned)a.y);
+  const float dz = (float)(int)((unsigned)b.z - (unsigned)a.z);
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 __device__ __forceinline__ float build_d2(double4_32a a, double4_32a b) {
@@ -265,7 +282,8 @@ template <typename PosT>
 __global__ void __launch_bounds__(256)
     k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
                const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
-               const int32_t* __restrict__ slot_of, float rlist2, int16_t* __restrict__ nbr,
+               const int32_t* __restrict__ slot_of, float rlist2 /* in build_d2's units */,
+               int16_t* __restrict__ nbr,
                int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
                const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
                uint32_t* wire_status) {
@@ -281,6 +299,7 @@ __global__ void __launch_bounds__(256)
     const int64_t a = idx / kBuildQuad;
     const int k = wl_find(nw.wl_atom, nf, a);
     const int wi = nw.wl_wire[k];
+    if (nw.mode[wi] == 0) continue;  // quad-uniform: the slab build takes this wire
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (a - nw.wl_atom[k]);
     const int32_t ii = (int32_t)i;
@@ -388,6 +407,259 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------- slab build
+// Atoms keep their [100] order, so the neighbours of 32 consecutive atoms of
+// a wire lie in one contiguous index range.  k_nl_envelope bounds that range
+// for any positions: along the atom order it writes xenv[i] = (prefix max,
+// suffix min) of x (relative to the wire's origin, FP32).  For a group of
+// atoms whose x lie in [xmin, xmax], every neighbour j satisfies
+// xmin - R <= x_j <= xmax + R (R = list radius + guard), so j >= lo, the first
+// index whose prefix max reaches xmin - R, and j <= hi, the last index whose
+// suffix min is below xmax + R (both envelopes are monotone).  The range is
+// tight when the order is nearly sorted; its excess grows with the wire's
+// disorder D = max_i (prefix max - suffix min), so a wire with D above
+// max_disorder (or any wire of an FP64 context) takes the cell build instead
+// (mode 1).  One block per flagged wire.
+constexpr float kSlabGuard = 0.01f;  // A added to the list radius for the FP32 envelope
+__global__ void __launch_bounds__(256)
+    k_nl_envelope(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+                  int slab_ok, float max_disorder) {
+  __shared__ float s_mx[256], s_mn[256];
+  const int nf = nw.n_flagged[0];
+  const int t = threadIdx.x;
+  for (int k = blockIdx.x; k < nf; k += gridDim.x) {
+    const int wi = nw.wl_wire[k];
+    if (!slab_ok) {
+      if (t == 0) nw.mode[wi] = 1;
+      continue;
+    }
+    const WireDev& w = wd[wi];
+    const int n = w.n;
+    const double ox = w.origin[0];
+    const double* xw = x + w.offset;
+    float2* env = nw.xenv + w.offset;
+    const int chunk = (n + 255) / 256;
+    const int a0 = min(n, t * chunk), a1 = min(n, a0 + chunk);
+    float mx = -INFINITY, mn = INFINITY;
+    for (int a = a0; a < a1; ++a) {
+      const float v = (float)(xw[a] - ox);
+      mx = fmaxf(mx, v);
+      mn = fminf(mn, v);
+    }
+    // inclusive scans of the chunk extrema: max from the left, min from the right
+    s_mx[t] = mx;
+    s_mn[t] = mn;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      const float l = t >= o ? s_mx[t - o] : -INFINITY;
+      const float r = t + o < 256 ? s_mn[t + o] : INFINITY;
+      __syncthreads();
+      s_mx[t] = fmaxf(s_mx[t], l);
+      s_mn[t] = fminf(s_mn[t], r);
+      __syncthreads();
+    }
+    float run_mx = t > 0 ? s_mx[t - 1] : -INFINITY;   // max over the earlier chunks
+    float run_mn = t < 255 ? s_mn[t + 1] : INFINITY;  // min over the later chunks
+    __syncthreads();
+    for (int a = a0; a < a1; ++a) {
+      run_mx = fmaxf(run_mx, (float)(xw[a] - ox));
+      env[a].x = run_mx;
+    }
+    float dis = 0.f;
+    for (int a = a1 - 1; a >= a0; --a) {
+      run_mn = fminf(run_mn, (float)(xw[a] - ox));
+      env[a].y = run_mn;
+      dis = fmaxf(dis, env[a].x - run_mn);
+    }
+    // block max of the disorder
+    s_mx[t] = dis;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (t < o) s_mx[t] = fmaxf(s_mx[t], s_mx[t + o]);
+      __syncthreads();
+    }
+    if (t == 0) nw.mode[wi] = s_mx[0] <= max_disorder ? 0 : 1;
+    __syncthreads();
+  }
+}
+
+// First wire-relative index q <= top with env[q].x >= v (env[top].x >= v
+// holds), found by the warp in rounds of 32 probes (stride 16, then 1).
+__device__ __forceinline__ int slab_lo(const float2* env, int top, float v) {
+  const int lane = threadIdx.x & 31;
+  int step = 16;
+  for (;;) {
+    const int p = top - (lane + 1) * step;
+    const bool below = p < 0 || env[p].x < v;
+    const unsigned m = __ballot_sync(0xffffffffu, below);
+    if (m == 0) {
+      top -= 32 * step;  // every probe still reaches v
+      continue;
+    }
+    const int l = __ffs(m) - 1;
+    const int ok = top - l * step;  // the first index reaching v is in (ok - step, ok]
+    if (step == 1) return ok;
+    top = ok;
+    step = 1;
+  }
+}
+
+// Last wire-relative index q >= bot, q < n, with env[q].y <= v (env[bot].y
+// <= v holds), by the same search forward.
+__device__ __forceinline__ int slab_hi(const float2* env, int bot, int n, float v) {
+  const int lane = threadIdx.x & 31;
+  int step = 16;
+  for (;;) {
+    const int p = bot + (lane + 1) * step;
+    const bool above = p >= n || env[p].y > v;
+    const unsigned m = __ballot_sync(0xffffffffu, above);
+    if (m == 0) {
+      bot += 32 * step;
+      continue;
+    }
+    const int l = __ffs(m) - 1;
+    const int ok = bot + l * step;
+    if (step == 1) return ok;
+    bot = ok;
+    step = 1;
+  }
+}
+
+// The slab build (MIXED contexts, wires of mode 0): one block per tile of
+// kSlotTile consecutive atoms of a flagged wire, one warp per 32 atoms, one
+// atom per lane.  The warp bounds its candidates by the envelopes (slab_lo,
+// slab_hi) and walks them in index order with broadcast loads (every lane
+// reads the same candidate), each lane testing it against its own atom with
+// the cell build's distance test (build_d2 against the same r_list^2, so the
+// two builds accept the same pairs); accepted offsets go to the lane's
+// column of a shared-memory buffer in ascending j.  The row is then written
+// in bank-group order (see k_nl_build): the lane's entries are bucketed by
+// group (j - wire offset) mod 8, ascending within a group, and at list
+// position k the atom in pair-pass lane l = slot mod 8 takes the next entry
+// of group (k + l) mod 8 while it has one, else of the group with the most
+// entries left (the first such in the rotation from the preferred one); the
+// order is a function of the wire alone.  Rows are written as 8-byte groups
+// of four entries.  Also the index range [jmin, jmax] and the snapshot of
+// the packed position, as the cell build.
+__global__ void __launch_bounds__(256)
+    k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+                    const int32_t* __restrict__ slot_of, float rlist2u, float xrange,
+                    int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
+                    int2* __restrict__ jrange, const int4* __restrict__ xq, int4* __restrict__ xq_b,
+                    uint32_t* wire_status) {
+  extern __shared__ int16_t sA[];  // [cap][blockDim.x]: offsets j - i, ascending, by column
+  uint8_t* sB = reinterpret_cast<uint8_t*>(sA + (size_t)cap * blockDim.x);  // [cap][blockDim.x]
+  const int nf = nw.n_flagged[0];
+  if (nf == 0) return;
+  const int64_t tiles = nw.wl_tile[nf];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int B = blockDim.x;
+  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+    const int k = wl_find(nw.wl_tile, nf, tl);
+    const int wi = nw.wl_wire[k];
+    if (nw.mode[wi] != 0) continue;  // block-uniform
+    const WireDev& w = wd[wi];
+    const int n = w.n;
+    const int a = (int)(tl - nw.wl_tile[k]) * kSlotTile + tid;  // wire-relative atom
+    const int g0 = a - lane;                                    // the warp's first atom
+    if (g0 >= n) continue;                                      // warp-uniform
+    const bool valid = a < n;
+    const int64_t i = w.offset + (valid ? a : g0);
+    const int ii = (int)i;
+    const float2* env = nw.xenv + w.offset;
+    // the group's extent along the axis, then its candidate range
+    const float xf = (float)(x[i] - w.origin[0]);
+    float xmin = valid ? xf : INFINITY, xmax = valid ? xf : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+      xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    const int glast = min(g0 + 31, n - 1);
+    const int lo = slab_lo(env, g0, xmin - xrange);
+    const int hi = slab_hi(env, glast, n, xmax + xrange);
+    // candidates j in [lo, hi], four at a time, every lane reading the same ones
+    const int4 pi = xq[i];
+    int cnt = 0, jmin = INT_MAX, jmax = INT_MIN;
+    bool far = false;
+    auto test = [&](int j, int4 pj) {
+      const float d2 = build_d2(pi, pj);
+      if (!valid || j == ii || !(d2 <= rlist2u)) return;
+      if (j - ii > kMaxOffset || ii - j > kMaxOffset) {
+        far = true;  // not representable as an int16 offset: dropped, wire flagged
+        return;
+      }
+      if (cnt < cap) sA[cnt * B + tid] = (int16_t)(j - ii);
+      ++cnt;
+      jmin = min(jmin, j);
+      jmax = j;
+    };
+    const int jlo = (int)w.offset + lo, jhi = (int)w.offset + hi;
+    int j = jlo;
+    for (; j + 3 <= jhi; j += 4) {
+      const int4 q0 = __ldg(xq + j), q1 = __ldg(xq + j + 1), q2 = __ldg(xq + j + 2),
+                 q3 = __ldg(xq + j + 3);
+      test(j, q0);
+      test(j + 1, q1);
+      test(j + 2, q2);
+      test(j + 3, q3);
+    }
+    for (; j <= jhi; ++j) test(j, __ldg(xq + j));
+    if (!valid) continue;
+    if (far || cnt > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
+    const int nr = min(cnt, cap);
+    const int il = (int)(i - w.offset);
+    auto group = [&](int e) { return (il + sA[e * B + tid]) & 7; };
+    // bucket the entries by group (ascending within a group)
+    uint64_t T = 0;
+    for (int e = 0; e < nr; ++e) T += 1ull << (8 * group(e));
+    const uint64_t S = T * 0x0101010101010101ull - T;  // exclusive prefix of the 8 counts
+    uint64_t P = S;
+    for (int e = 0; e < nr; ++e) {
+      const int g = group(e);
+      sB[byte_of(P, g) * B + tid] = (uint8_t)e;
+      P += 1ull << (8 * g);
+    }
+    // emit in bank-group order, four entries per 8-byte store
+    const int64_t t = slot_of[i];
+    const int pl = (int)(t & 7);
+    uint64_t R = 0, rem = T;
+    uint32_t w0 = 0, w1 = 0;
+    uint2* rowg = reinterpret_cast<uint2*>(nbr);
+    for (int q = 0; q < nr; ++q) {
+      const int want = (q + pl) & 7;
+      int g = want;
+      if (byte_of(rem, g) == 0) {
+        int best = -1;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const int h = (want + d) & 7;
+          if (byte_of(rem, h) > best) {
+            best = byte_of(rem, h);
+            g = h;
+          }
+        }
+      }
+      const int e = sB[(byte_of(S, g) + byte_of(R, g)) * B + tid];
+      R += 1ull << (8 * g);
+      rem -= 1ull << (8 * g);
+      const uint32_t v = (uint16_t)sA[e * B + tid];
+      const int s4 = q & 3;
+      if (s4 == 0) w0 = v;
+      else if (s4 == 1) w0 |= v << 16;
+      else if (s4 == 2) w1 = v;
+      else w1 |= v << 16;
+      if (s4 == 3 || q == nr - 1) {
+        if (s4 < 2) w1 = 0;
+        rowg[nbr_group(t, q >> 2, cap)] = make_uint2(w0, w1);
+      }
+    }
+    n_nbr[t] = nr;
+    jrange[t] = make_int2(jmin, jmax);
+    xq_b[i] = pi;
+  }
+}
+
 // Row-major copy of the tiled lists (for the list accessor).
 // Either output may be null: counts[N] per atom, rows[N * cap] row-major.
 __global__ void k_list_rows(int64_t N, int cap, const int16_t* __restrict__ nbr,
@@ -427,7 +699,6 @@ __global__ void k_slot_init(int W, const WireDev* __restrict__ wd, int64_t NS,
 // so its neighbour-index window is unchanged.  The speed depends on this
 // order, and the list rows are ordered for the lane (slot mod 8) an atom gets
 // (k_nl_build); the lists are rebuilt after this kernel.
-constexpr int kSlotTile = 256;
 __global__ void __launch_bounds__(kSlotTile)
     k_slot_order(int64_t NS, const int32_t* __restrict__ n_nbr, int32_t* __restrict__ perm,
                  int32_t* __restrict__ slot_of) {

@@ -43,6 +43,11 @@ constexpr int kMinCap = 64;   // neighbour-list row length, bounds (list_capacit
 constexpr int kMaxCap = 128;
 constexpr int kMaxWindow = 4096; // largest shared-memory window of a pair-pass tile, atoms
 constexpr int kMaxEamSamples = 1 << 22;  // samples per EAM table
+// Largest disorder of a wire's atom order along the axis (max over atoms of
+// the prefix max minus the suffix min of x, A) for which it takes the slab
+// build: each A of disorder widens every slab by about a plane's worth of
+// atoms at each end; beyond this the cell build is cheaper.
+constexpr float kSlabDisorder = 4.0f;
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
@@ -101,6 +106,9 @@ struct tbsma_ctx {
   int32_t* wl_wire = nullptr;
   int64_t* wl_cell = nullptr;
   int64_t* wl_atom = nullptr;
+  int64_t* wl_tile = nullptr;
+  uint8_t* nl_mode = nullptr;  // per wire: 0 slab build, 1 cell build (k_nl_envelope)
+  float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (k_nl_envelope)
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
@@ -133,13 +141,28 @@ struct tbsma_ctx {
   bool eam_on = false;           // tabulated EAM instead of Eq. 1-3 (tbsma_set_eam)
   EamDev eam{};
   std::vector<void*> eam_allocs;  // the EAM tables (replaced by every tbsma_set_eam)
-  float rlist2 = 0.f;
+  float rlist2 = 0.f;   // list radius squared, A^2
+  float rlist2u = 0.f;  // the same in fixed-point units squared (x 2^52, exact)
+  float slab_range = 0.f;  // list radius plus the envelope guard, A (slab build)
   double half_skin2 = 0.0;
   double inv_m = 0.0;
 
   NlWork nw() const {
-    return NlWork{flag,   wl_wire,    wl_cell, wl_atom, n_flagged, n_rebuilds,
-                  chains, last_build, banked,  rebuilt};
+    NlWork w;
+    w.flag = flag;
+    w.wl_wire = wl_wire;
+    w.wl_cell = wl_cell;
+    w.wl_atom = wl_atom;
+    w.wl_tile = wl_tile;
+    w.mode = nl_mode;
+    w.xenv = xenv;
+    w.n_flagged = n_flagged;
+    w.n_rebuilds = n_rebuilds;
+    w.chains = chains;
+    w.last_build = last_build;
+    w.banked = banked;
+    w.rebuilt = rebuilt;
+    return w;
   }
 };
 
@@ -229,6 +252,8 @@ void fill_pair_consts(tbsma_ctx* c) {
   // displacement check can never drop a pair that reaches r_cut
   const double rl = P.r_cut + P.r_skin + 1e-3;
   c->rlist2 = (float)(rl * rl);
+  c->rlist2u = c->rlist2 * 4503599627370496.0f;  // x 2^52
+  c->slab_range = (float)rl + kSlabGuard;
   c->half_skin2 = 0.25 * P.r_skin * P.r_skin;
   c->inv_m = 1.0 / (P.mass * kMvv2e);
   // List row length: the fcc sites (density sqrt(2)/r0^3 for nearest-neighbour
@@ -277,9 +302,14 @@ tbsma_status launch_pack(tbsma_ctx* c, cudaStream_t s, int check) {
   return TBSMA_OK;
 }
 
-// The list rebuild of the wires the plan selected: clear their cells, bin,
-// sort each cell, build (each kernel returns at once when none is selected).
+// The list rebuild of the wires the plan selected (each kernel returns at
+// once when none is selected): envelopes and the choice of build per wire,
+// then the cell build (clear the cells, bin, sort each cell, build) of the
+// wires that need it, then the slab build of the others (MIXED contexts).
 tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
+  const bool mixed = c->prec == TBSMA_MIXED;
+  k_nl_envelope<<<(unsigned)(c->sm_count * 2), 256, 0, s>>>(c->nw(), c->wd, c->x, mixed ? 1 : 0,
+                                                            kSlabDisorder);
   const unsigned gs = (unsigned)(c->sm_count * 4);
   k_nl_clear<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->cell_count);
   k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
@@ -287,14 +317,19 @@ tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
   k_nl_sort<<<gs * 2, 256, 0, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms);
   const unsigned gb = (unsigned)(c->sm_count * 8);
   const size_t sbuf = (size_t)256 * c->cap * sizeof(int16_t);  // per-thread entry buffers
-  if (c->prec == TBSMA_MIXED)
+  if (mixed) {
     k_nl_build<int4><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
-                                           c->slot_of, c->rlist2, c->nbr, c->n_nbr, c->cap, c->jrange,
+                                           c->slot_of, c->rlist2u, c->nbr, c->n_nbr, c->cap, c->jrange,
                                            c->xq, c->xq_b, c->wire_status);
-  else
+    const size_t sslab = (size_t)256 * c->cap * (sizeof(int16_t) + sizeof(uint8_t));
+    k_nl_build_slab<<<(unsigned)(c->sm_count * 3), 256, sslab, s>>>(
+        c->nw(), c->wd, c->x, c->slot_of, c->rlist2u, c->slab_range, c->nbr, c->n_nbr, c->cap,
+        c->jrange, c->xq, c->xq_b, c->wire_status);
+  } else {
     k_nl_build<double4_32a><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
                                                   c->cell_of, c->slot_of, c->rlist2, c->nbr, c->n_nbr,
                                                   c->cap, c->jrange, c->xd, c->xd_b, c->wire_status);
+  }
   TB_CUDA(c, cudaGetLastError());
   return TBSMA_OK;
 }
@@ -841,8 +876,10 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       !smem_attr((const void*)k_force_f32<true, true>))
     return bail(TBSMA_ECUDA);
   const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
+  const int slab_max = 256 * kMaxCap * (int)(sizeof(int16_t) + sizeof(uint8_t));  // k_nl_build_slab's
   if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess)
+      cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_nl_build_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, slab_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
@@ -927,6 +964,9 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->wl_wire, W);
   ALLOC(c->wl_cell, W + 1);
   ALLOC(c->wl_atom, W + 1);
+  ALLOC(c->wl_tile, W + 1);
+  ALLOC(c->nl_mode, W);
+  ALLOC(c->xenv, N);
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);
@@ -951,6 +991,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->nl_mode, 1, W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->baro, 0, sizeof(BaroState) * W, st) == cudaSuccess;

@@ -167,6 +167,46 @@ def test_neighbor_lists_bracket_oracle_pairs(tb, orc):
     eng.close()
 
 
+def test_disordered_atom_order_takes_the_cell_build(tb, orc):
+    """One wire's atoms in random order: its envelopes along the atom order
+    are far apart, so the library builds its lists through the cell grid
+    instead of the slab scan.  Both builds decide each pair by the same test,
+    so that wire's lists hold the same atoms as those of the same wire in
+    [100] order (a slab build), its lists bracket the oracle's pairs, and its
+    forces match the oracle's."""
+    b = _jittered_batch(0.05, 29)
+    w = 1
+    s = b.wire_slice(w)
+    p = np.random.default_rng(4).permutation(int(b.n[w]))
+    b2 = _jittered_batch(0.05, 29)
+    b2.x[s] = b.x[s][p]
+    b2.kind[s] = b.kind[s][p]
+    o = int(b.offset[w])
+    rows = []
+    for bb in (b, b2):
+        eng = tb.Engine(bb, precision="mixed")
+        n, nb = eng.neighbors()
+        F32, _ = eng.forces(f32=True, f64=False)
+        rows.append((n.cpu().numpy(), nb.cpu().numpy(), F32.double().cpu().numpy()))
+        eng.close()
+    (n1, nb1, _), (n2, nb2, F2) = rows
+    for k in range(int(b.n[w])):
+        got = {int(p[j - o]) for j in nb2[o + k, :n2[o + k]]}
+        ref = set((nb1[o + p[k], :n1[o + p[k]]] - o).tolist())
+        assert got == ref
+    r_list = orc.AU.r_cut + orc.R_SKIN + 1e-3
+    s_in, n_in = orc.pairs(b2.x[s], r_list - 1e-4)
+    for k in range(int(b.n[w])):
+        assert set(n_in[s_in[k]:s_in[k + 1]].tolist()) <= set((nb2[o + k, :n2[o + k]] - o).tolist())
+    ref = orc.tbsma(b2.x[s], brute_max=3000)
+    amb = ambiguous_atoms(orc, b2.x[s], orc.AU.r_cut, 5e-6)
+    ok = np.ones(int(b.n[w]), bool)
+    ok[amb] = False
+    d, fm, norm = force_errors(F2[s], ref.F)
+    assert np.max(d[ok] / ref.S[ok]) <= 1e-5
+    assert norm <= 1e-5
+
+
 # --------------------------------------------------------- initial state
 def test_init_velocities_match_oracle(tb, orc):
     b = workload("tiny_batch")
