@@ -51,7 +51,7 @@ GRAPH_CHUNK = 50  # steps per captured graph (library constant)
 # than at 0.29 A (measured on this workload: 751.6 -> 700.6 us per step).
 R_SKIN = 0.40
 KERNELS_PER_STEP = 4  # integrate, plan, density, force (+ the rebuild chain when it runs)
-KERNELS_PER_CHAIN = 6  # envelope, cell clear, bin, sort, cell build, slab build: counted by the library
+KERNELS_PER_CHAIN = 7  # two envelope passes, cell clear, bin, sort, cell build, slab build (per plan)
 OBS_EVERY = 1000  # per-wire observables reported every OBS_EVERY steps inside the timed region
 KERNELS_PER_OBS = 5  # pack, plan, density + force (with energies), reduce (+ a rebuild chain)
 METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"

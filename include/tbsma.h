@@ -418,8 +418,8 @@ tbsma_status tbsma_get_wire_status(tbsma_ctx* ctx, int32_t* status_host);
 int32_t tbsma_nbr_capacity(const tbsma_ctx* ctx);
 
 /* Launch accounting: how many times the kernels of the list-rebuild chain
- * (envelope, cell clear, bin, sort, cell build, and in MIXED contexts the
- * slab build) were launched since tbsma_init: once
+ * (cell clear, bin, sort, cell build, and in MIXED contexts the two envelope
+ * passes and the slab build) were launched since tbsma_init: once
  * per step and per position refresh (they return at once when no wire is
  * flagged).  Synchronises.  Errors: EINVAL (null). */
 tbsma_status tbsma_get_rebuild_chains(tbsma_ctx* ctx, int64_t* n);

@@ -27,8 +27,11 @@ struct NlWork {
   int64_t* wl_cell;     // [W+1] prefix of their cell counts
   int64_t* wl_atom;     // [W+1] prefix of their atom counts
   int64_t* wl_tile;     // [W+1] prefix of their tiles (kSlotTile consecutive atoms each)
-  uint8_t* mode;        // [W] build of the wire at this rebuild: 0 slab, 1 cells (k_nl_envelope)
-  float2* xenv;         // [N] along the atom order: prefix max and suffix min of x (k_nl_envelope)
+  float2* xenv;         // [N] along the atom order: prefix max and suffix min of x (envelopes)
+  float2* tenv;         // [NS / kSlotTile] per tile: max and min of x (envelopes)
+  uint32_t* wdis;       // [W] disorder of the atom order along x, A (FP32 bits; envelopes)
+  int slab_ok;          // the context may use the slab build (MIXED)
+  float max_disorder;   // largest disorder for which a wire takes the slab build, A
   int32_t* n_flagged;   // [1]
   int32_t* n_rebuilds;  // [W]
   int64_t* chains;      // [1] launches of the rebuild chain (clear, bin, sort, build)
@@ -45,6 +48,12 @@ constexpr int64_t kBankedInterval = 128;
 // Atoms per tile of the pair passes (see k_slot_order); the slab build
 // works on the same tiles.
 constexpr int kSlotTile = 256;
+
+// Whether wire w takes the slab build at this rebuild (its disorder, from
+// k_nl_env_merge, small enough; NaN positions give a NaN disorder: cells).
+__device__ __forceinline__ bool use_slab(const NlWork& nw, int w) {
+  return nw.slab_ok && __uint_as_float(nw.wdis[w]) <= nw.max_disorder;
+}
 
 // Binary search: largest k < nf with pre[k] <= idx.
 __device__ __forceinline__ int wl_find(const int64_t* pre, int nf, int64_t idx) {
@@ -158,7 +167,7 @@ __global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* c
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = wl_find(nw.wl_cell, nf, idx);
-    if (nw.mode[nw.wl_wire[k]] == 0) continue;  // the slab build takes this wire
+    if (use_slab(nw, nw.wl_wire[k])) continue;  // the slab build takes this wire
     const WireDev& w = wd[nw.wl_wire[k]];
     cell_count[w.cell_base + (idx - nw.wl_cell[k])] = 0;
   }
@@ -184,7 +193,7 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = wl_find(nw.wl_atom, nf, idx);
     const int wi = nw.wl_wire[k];
-    if (nw.mode[wi] == 0) continue;  // the slab build takes this wire
+    if (use_slab(nw, wi)) continue;  // the slab build takes this wire
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (idx - nw.wl_atom[k]);
     bool out = false;
@@ -211,7 +220,7 @@ __global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32
   for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
        idx += warps) {
     const int k = wl_find(nw.wl_cell, nf, idx);
-    if (nw.mode[nw.wl_wire[k]] == 0) continue;  // warp-uniform (one cell per warp)
+    if (use_slab(nw, nw.wl_wire[k])) continue;  // warp-uniform (one cell per warp)
     const int64_t c = wd[nw.wl_wire[k]].cell_base + (idx - nw.wl_cell[k]);
     const int cnt = min(cell_count[c], kCellCap);
     const int32_t m = lane < cnt ? cell_atoms[c * kCellCap + lane] : INT32_MAX;
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(256)
     const int64_t a = idx / kBuildQuad;
     const int k = wl_find(nw.wl_atom, nf, a);
     const int wi = nw.wl_wire[k];
-    if (nw.mode[wi] == 0) continue;  // quad-uniform: the slab build takes this wire
+    if (use_slab(nw, wi)) continue;  // quad-uniform: the slab build takes this wire
     const WireDev& w = wd[wi];
     const int64_t i = w.offset + (a - nw.wl_atom[k]);
     const int32_t ii = (int32_t)i;
@@ -409,77 +418,125 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------- slab build
 // Atoms keep their [100] order, so the neighbours of 32 consecutive atoms of
-// a wire lie in one contiguous index range.  k_nl_envelope bounds that range
-// for any positions: along the atom order it writes xenv[i] = (prefix max,
-// suffix min) of x (relative to the wire's origin, FP32).  For a group of
-// atoms whose x lie in [xmin, xmax], every neighbour j satisfies
-// xmin - R <= x_j <= xmax + R (R = list radius + guard), so j >= lo, the first
-// index whose prefix max reaches xmin - R, and j <= hi, the last index whose
-// suffix min is below xmax + R (both envelopes are monotone).  The range is
-// tight when the order is nearly sorted; its excess grows with the wire's
-// disorder D = max_i (prefix max - suffix min), so a wire with D above
-// max_disorder (or any wire of an FP64 context) takes the cell build instead
-// (mode 1).  One block per flagged wire.
+// a wire lie in one contiguous index range.  The envelopes bound that range
+// for any positions: along the atom order, xenv[i] = (prefix max, suffix
+// min) of x relative to the wire's origin (FP32).  For a group of atoms whose
+// x lie in [xmin, xmax], every neighbour j satisfies xmin - R <= x_j <= xmax
+// + R (R = list radius + guard), so j >= lo, the first index whose prefix max
+// reaches xmin - R, and j <= hi, the last index whose suffix min is below
+// xmax + R (both envelopes are monotone).  The range is tight when the order
+// is nearly sorted; its excess grows with the wire's disorder D = max_i
+// (prefix max - suffix min), so a wire with D above max_disorder (or any
+// wire of an FP64 context) takes the cell build instead.  Two passes over
+// the flagged wires' tiles, each fully parallel: k_nl_env_tiles scans each
+// tile alone, k_nl_env_merge folds in the extrema of the wire's other tiles.
 constexpr float kSlabGuard = 0.01f;  // A added to the list radius for the FP32 envelope
-__global__ void __launch_bounds__(256)
-    k_nl_envelope(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-                  int slab_ok, float max_disorder) {
-  __shared__ float s_mx[256], s_mn[256];
+
+// Block-wide inclusive max-scan from the left and min-scan from the right of
+// (mx, mn) over the kSlotTile threads, and the block's max and min.
+__device__ __forceinline__ void tile_scans(float& mx, float& mn, float& bmx, float& bmn) {
+  __shared__ float s_mx[kSlotTile / 32], s_mn[kSlotTile / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(0xffffffffu, mx, o);
+    const float d = __shfl_down_sync(0xffffffffu, mn, o);
+    if (lane >= o) mx = fmaxf(mx, u);
+    if (lane + o < 32) mn = fminf(mn, d);
+  }
+  if (lane == 31) s_mx[warp] = mx;  // the warp's max
+  if (lane == 0) s_mn[warp] = mn;   // the warp's min
+  __syncthreads();
+  float before = -INFINITY, after = INFINITY;
+  bmx = -INFINITY;
+  bmn = INFINITY;
+#pragma unroll
+  for (int q = 0; q < kSlotTile / 32; ++q) {
+    if (q < warp) before = fmaxf(before, s_mx[q]);
+    if (q > warp) after = fminf(after, s_mn[q]);
+    bmx = fmaxf(bmx, s_mx[q]);
+    bmn = fminf(bmn, s_mn[q]);
+  }
+  mx = fmaxf(mx, before);
+  mn = fminf(mn, after);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSlotTile)
+    k_nl_env_tiles(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x) {
   const int nf = nw.n_flagged[0];
-  const int t = threadIdx.x;
-  for (int k = blockIdx.x; k < nf; k += gridDim.x) {
+  if (nf == 0 || !nw.slab_ok) return;
+  const int64_t tiles = nw.wl_tile[nf];
+  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+    const int k = wl_find(nw.wl_tile, nf, tl);
     const int wi = nw.wl_wire[k];
-    if (!slab_ok) {
-      if (t == 0) nw.mode[wi] = 1;
-      continue;
-    }
     const WireDev& w = wd[wi];
-    const int n = w.n;
-    const double ox = w.origin[0];
-    const double* xw = x + w.offset;
-    float2* env = nw.xenv + w.offset;
-    const int chunk = (n + 255) / 256;
-    const int a0 = min(n, t * chunk), a1 = min(n, a0 + chunk);
-    float mx = -INFINITY, mn = INFINITY;
-    for (int a = a0; a < a1; ++a) {
-      const float v = (float)(xw[a] - ox);
-      mx = fmaxf(mx, v);
-      mn = fminf(mn, v);
+    const int kt = (int)(tl - nw.wl_tile[k]);  // tile of the wire
+    const int a = kt * kSlotTile + threadIdx.x;
+    const bool valid = a < w.n;
+    const float v = valid ? (float)(x[w.offset + a] - w.origin[0]) : 0.f;
+    float mx = valid ? v : -INFINITY, mn = valid ? v : INFINITY, bmx, bmn;
+    tile_scans(mx, mn, bmx, bmn);
+    if (valid) nw.xenv[w.offset + a] = make_float2(mx, mn);
+    if (threadIdx.x == 0) {
+      nw.tenv[w.slot_base / kSlotTile + kt] = make_float2(bmx, bmn);
+      if (kt == 0) nw.wdis[wi] = 0u;
     }
-    // inclusive scans of the chunk extrema: max from the left, min from the right
-    s_mx[t] = mx;
-    s_mn[t] = mn;
+  }
+}
+
+__global__ void __launch_bounds__(kSlotTile)
+    k_nl_env_merge(NlWork nw, const WireDev* __restrict__ wd) {
+  __shared__ float s_red[2][kSlotTile / 32];
+  const int nf = nw.n_flagged[0];
+  if (nf == 0 || !nw.slab_ok) return;
+  const int64_t tiles = nw.wl_tile[nf];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+    const int k = wl_find(nw.wl_tile, nf, tl);
+    const int wi = nw.wl_wire[k];
+    const WireDev& w = wd[wi];
+    const int kt = (int)(tl - nw.wl_tile[k]);
+    const int nt = (w.n + kSlotTile - 1) / kSlotTile;
+    const float2* te = nw.tenv + w.slot_base / kSlotTile;
+    // max over the wire's earlier tiles, min over its later tiles
+    float before = -INFINITY, after = INFINITY;
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+      const float2 e = te[q];
+      if (q < kt) before = fmaxf(before, e.x);
+      if (q > kt) after = fminf(after, e.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      before = fmaxf(before, __shfl_xor_sync(0xffffffffu, before, o));
+      after = fminf(after, __shfl_xor_sync(0xffffffffu, after, o));
+    }
+    if (lane == 0) {
+      s_red[0][warp] = before;
+      s_red[1][warp] = after;
+    }
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
-      const float l = t >= o ? s_mx[t - o] : -INFINITY;
-      const float r = t + o < 256 ? s_mn[t + o] : INFINITY;
-      __syncthreads();
-      s_mx[t] = fmaxf(s_mx[t], l);
-      s_mn[t] = fminf(s_mn[t], r);
-      __syncthreads();
+    before = -INFINITY;
+    after = INFINITY;
+#pragma unroll
+    for (int q = 0; q < kSlotTile / 32; ++q) {
+      before = fmaxf(before, s_red[0][q]);
+      after = fminf(after, s_red[1][q]);
     }
-    float run_mx = t > 0 ? s_mx[t - 1] : -INFINITY;   // max over the earlier chunks
-    float run_mn = t < 255 ? s_mn[t + 1] : INFINITY;  // min over the later chunks
     __syncthreads();
-    for (int a = a0; a < a1; ++a) {
-      run_mx = fmaxf(run_mx, (float)(xw[a] - ox));
-      env[a].x = run_mx;
-    }
+    const int a = kt * kSlotTile + threadIdx.x;
     float dis = 0.f;
-    for (int a = a1 - 1; a >= a0; --a) {
-      run_mn = fminf(run_mn, (float)(xw[a] - ox));
-      env[a].y = run_mn;
-      dis = fmaxf(dis, env[a].x - run_mn);
+    if (a < w.n) {
+      float2 e = nw.xenv[w.offset + a];
+      e.x = fmaxf(e.x, before);
+      e.y = fminf(e.y, after);
+      nw.xenv[w.offset + a] = e;
+      dis = e.x - e.y;  // NaN positions: NaN, which fmaxf below does not drop into 0
+      if (!(dis == dis)) dis = INFINITY;
     }
-    // block max of the disorder
-    s_mx[t] = dis;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (t < o) s_mx[t] = fmaxf(s_mx[t], s_mx[t + o]);
-      __syncthreads();
-    }
-    if (t == 0) nw.mode[wi] = s_mx[0] <= max_disorder ? 0 : 1;
-    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dis = fmaxf(dis, __shfl_xor_sync(0xffffffffu, dis, o));
+    if (lane == 0 && dis > 0.f) atomicMax(nw.wdis + wi, __float_as_uint(dis));
   }
 }
 
@@ -525,39 +582,45 @@ __device__ __forceinline__ int slab_hi(const float2* env, int bot, int n, float 
   }
 }
 
-// The slab build (MIXED contexts, wires of mode 0): one block per tile of
-// kSlotTile consecutive atoms of a flagged wire, one warp per 32 atoms, one
-// atom per lane.  The warp bounds its candidates by the envelopes (slab_lo,
-// slab_hi) and walks them in index order with broadcast loads (every lane
-// reads the same candidate), each lane testing it against its own atom with
-// the cell build's distance test (build_d2 against the same r_list^2, so the
-// two builds accept the same pairs); accepted offsets go to the lane's
-// column of a shared-memory buffer in ascending j.  The row is then written
-// in bank-group order (see k_nl_build): the lane's entries are bucketed by
+// The slab build (MIXED contexts, wires whose disorder allows it): one block
+// per tile of kSlotTile consecutive atoms of a flagged wire, one warp per 32
+// atoms, one atom per lane.  The warp bounds its candidates by the envelopes
+// (slab_lo, slab_hi) and walks them in index order with broadcast loads
+// (every lane reads the same candidate), each lane testing it against its
+// own atom with the cell build's distance test (build_d2 against the same
+// r_list^2, so the two builds accept the same pairs).  The test is
+// branch-free: each lane collects the outcomes of 32 consecutive candidates
+// as the bits of a mask, then appends the set bits to its column of a
+// shared-memory buffer as offsets j - i; the atom itself (offset 0, d2 = 0)
+// is accepted too and dropped afterwards, so the loop needs no j != i test.
+// The row is then written in
+// bank-group order (see k_nl_build): the lane's entries are bucketed by
 // group (j - wire offset) mod 8, ascending within a group, and at list
 // position k the atom in pair-pass lane l = slot mod 8 takes the next entry
 // of group (k + l) mod 8 while it has one, else of the group with the most
 // entries left (the first such in the rotation from the preferred one); the
 // order is a function of the wire alone.  Rows are written as 8-byte groups
 // of four entries.  Also the index range [jmin, jmax] and the snapshot of
-// the packed position, as the cell build.
+// the packed position, as the cell build.  The entry buffer has room for
+// cap + kSlabSlack entries per lane (cap neighbours and the atom itself).
+constexpr int kSlabSlack = 1;
 __global__ void __launch_bounds__(256)
     k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
                     const int32_t* __restrict__ slot_of, float rlist2u, float xrange,
                     int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
                     int2* __restrict__ jrange, const int4* __restrict__ xq, int4* __restrict__ xq_b,
                     uint32_t* wire_status) {
-  extern __shared__ int16_t sA[];  // [cap][blockDim.x]: offsets j - i, ascending, by column
-  uint8_t* sB = reinterpret_cast<uint8_t*>(sA + (size_t)cap * blockDim.x);  // [cap][blockDim.x]
+  extern __shared__ int16_t sA[];  // [cap + kSlabSlack][blockDim.x]: offsets, ascending, by column
+  const int B = blockDim.x;
+  uint8_t* sB = reinterpret_cast<uint8_t*>(sA + (size_t)(cap + kSlabSlack) * B);  // [cap][B]
   const int nf = nw.n_flagged[0];
-  if (nf == 0) return;
+  if (nf == 0 || !nw.slab_ok) return;
   const int64_t tiles = nw.wl_tile[nf];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int B = blockDim.x;
   for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
     const int k = wl_find(nw.wl_tile, nf, tl);
     const int wi = nw.wl_wire[k];
-    if (nw.mode[wi] != 0) continue;  // block-uniform
+    if (!use_slab(nw, wi)) continue;  // block-uniform
     const WireDev& w = wd[wi];
     const int n = w.n;
     const int a = (int)(tl - nw.wl_tile[k]) * kSlotTile + tid;  // wire-relative atom
@@ -577,39 +640,62 @@ __global__ void __launch_bounds__(256)
     }
     const int glast = min(g0 + 31, n - 1);
     const int lo = slab_lo(env, g0, xmin - xrange);
-    const int hi = slab_hi(env, glast, n, xmax + xrange);
+    int hi = slab_hi(env, glast, n, xmax + xrange);
+    if (hi - lo > kMaxOffset) {  // offsets would not fit the int16 entries
+      if (lane == 0) atomicOr(&wire_status[wi], kWireNbrOverflow);
+      hi = lo + kMaxOffset;
+    }
     // candidates j in [lo, hi], four at a time, every lane reading the same ones
     const int4 pi = xq[i];
-    int cnt = 0, jmin = INT_MAX, jmax = INT_MIN;
-    bool far = false;
-    auto test = [&](int j, int4 pj) {
-      const float d2 = build_d2(pi, pj);
-      if (!valid || j == ii || !(d2 <= rlist2u)) return;
-      if (j - ii > kMaxOffset || ii - j > kMaxOffset) {
-        far = true;  // not representable as an int16 offset: dropped, wire flagged
-        return;
-      }
-      if (cnt < cap) sA[cnt * B + tid] = (int16_t)(j - ii);
-      ++cnt;
-      jmin = min(jmin, j);
-      jmax = j;
-    };
+    // every lane tests every candidate, 32 at a time into an acceptance mask
+    // (bit u: candidate j0 + u), whose set bits are then appended to the
+    // lane's column as offsets j - i: rows 0..cap hold the first cap + 1
+    // accepted entries (cap neighbours and the atom itself)
+    int n_all = 0;
     const int jlo = (int)w.offset + lo, jhi = (int)w.offset + hi;
-    int j = jlo;
-    for (; j + 3 <= jhi; j += 4) {
-      const int4 q0 = __ldg(xq + j), q1 = __ldg(xq + j + 1), q2 = __ldg(xq + j + 2),
-                 q3 = __ldg(xq + j + 3);
-      test(j, q0);
-      test(j + 1, q1);
-      test(j + 2, q2);
-      test(j + 3, q3);
+    auto flush = [&](uint32_t m, int off0) {
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if (n_all <= cap) sA[n_all * B + tid] = (int16_t)(off0 + b);
+        ++n_all;
+      }
+    };
+    for (int j0 = jlo; j0 <= jhi; j0 += 32) {
+      uint32_t m = 0;
+      const int cnt32 = min(32, jhi - j0 + 1);
+      if (cnt32 == 32) {
+#pragma unroll
+        for (int u = 0; u < 32; u += 4) {
+          const int4 q0 = __ldg(xq + j0 + u), q1 = __ldg(xq + j0 + u + 1),
+                     q2 = __ldg(xq + j0 + u + 2), q3 = __ldg(xq + j0 + u + 3);
+          if (build_d2(pi, q0) <= rlist2u) m |= 1u << u;
+          if (build_d2(pi, q1) <= rlist2u) m |= 2u << u;
+          if (build_d2(pi, q2) <= rlist2u) m |= 4u << u;
+          if (build_d2(pi, q3) <= rlist2u) m |= 8u << u;
+        }
+      } else {
+        for (int u = 0; u < cnt32; ++u)
+          if (build_d2(pi, __ldg(xq + j0 + u)) <= rlist2u) m |= 1u << u;
+      }
+      flush(m, j0 - ii);
     }
-    for (; j <= jhi; ++j) test(j, __ldg(xq + j));
     if (!valid) continue;
-    if (far || cnt > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
+    const bool ovf = n_all > cap + 1;
+    n_all = min(n_all, cap + 1);  // accepted and stored, the atom itself included (if it fit)
+    // drop the atom itself: offsets ascend, so it follows the negative ones
+    int self = n_all;
+    for (int e = 0; e < n_all; ++e)
+      if (sA[e * B + tid] == 0) {
+        self = e;
+        break;
+      }
+    const int cnt = n_all - (self < n_all ? 1 : 0);
+    if (ovf || cnt > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
     const int nr = min(cnt, cap);
+    auto entry = [&](int e) { return sA[(e < self ? e : e + 1) * B + tid]; };  // e-th without self
     const int il = (int)(i - w.offset);
-    auto group = [&](int e) { return (il + sA[e * B + tid]) & 7; };
+    auto group = [&](int e) { return (il + entry(e)) & 7; };
     // bucket the entries by group (ascending within a group)
     uint64_t T = 0;
     for (int e = 0; e < nr; ++e) T += 1ull << (8 * group(e));
@@ -643,7 +729,7 @@ __global__ void __launch_bounds__(256)
       const int e = sB[(byte_of(S, g) + byte_of(R, g)) * B + tid];
       R += 1ull << (8 * g);
       rem -= 1ull << (8 * g);
-      const uint32_t v = (uint16_t)sA[e * B + tid];
+      const uint32_t v = (uint16_t)entry(e);
       const int s4 = q & 3;
       if (s4 == 0) w0 = v;
       else if (s4 == 1) w0 |= v << 16;
@@ -655,7 +741,7 @@ __global__ void __launch_bounds__(256)
       }
     }
     n_nbr[t] = nr;
-    jrange[t] = make_int2(jmin, jmax);
+    jrange[t] = nr > 0 ? make_int2(ii + entry(0), ii + entry(nr - 1)) : make_int2(INT_MAX, INT_MIN);
     xq_b[i] = pi;
   }
 }

@@ -107,8 +107,9 @@ struct tbsma_ctx {
   int64_t* wl_cell = nullptr;
   int64_t* wl_atom = nullptr;
   int64_t* wl_tile = nullptr;
-  uint8_t* nl_mode = nullptr;  // per wire: 0 slab build, 1 cell build (k_nl_envelope)
-  float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (k_nl_envelope)
+  float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (slab-build envelopes)
+  float2* tenv = nullptr;      // per tile: max / min of x (slab-build envelopes)
+  uint32_t* wdis = nullptr;    // per wire: disorder of the atom order along x (FP32 bits)
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
@@ -154,8 +155,11 @@ struct tbsma_ctx {
     w.wl_cell = wl_cell;
     w.wl_atom = wl_atom;
     w.wl_tile = wl_tile;
-    w.mode = nl_mode;
     w.xenv = xenv;
+    w.tenv = tenv;
+    w.wdis = wdis;
+    w.slab_ok = prec == TBSMA_MIXED ? 1 : 0;
+    w.max_disorder = kSlabDisorder;
     w.n_flagged = n_flagged;
     w.n_rebuilds = n_rebuilds;
     w.chains = chains;
@@ -308,8 +312,10 @@ tbsma_status launch_pack(tbsma_ctx* c, cudaStream_t s, int check) {
 // wires that need it, then the slab build of the others (MIXED contexts).
 tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
   const bool mixed = c->prec == TBSMA_MIXED;
-  k_nl_envelope<<<(unsigned)(c->sm_count * 2), 256, 0, s>>>(c->nw(), c->wd, c->x, mixed ? 1 : 0,
-                                                            kSlabDisorder);
+  if (mixed) {
+    k_nl_env_tiles<<<(unsigned)(c->sm_count * 8), kSlotTile, 0, s>>>(c->nw(), c->wd, c->x);
+    k_nl_env_merge<<<(unsigned)(c->sm_count * 8), kSlotTile, 0, s>>>(c->nw(), c->wd);
+  }
   const unsigned gs = (unsigned)(c->sm_count * 4);
   k_nl_clear<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->cell_count);
   k_nl_bin<<<gs, 256, 0, s>>>(c->nw(), c->wd, c->x, c->N, c->cell_count, c->cell_atoms,
@@ -321,7 +327,7 @@ tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
     k_nl_build<int4><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms, c->cell_of,
                                            c->slot_of, c->rlist2u, c->nbr, c->n_nbr, c->cap, c->jrange,
                                            c->xq, c->xq_b, c->wire_status);
-    const size_t sslab = (size_t)256 * c->cap * (sizeof(int16_t) + sizeof(uint8_t));
+    const size_t sslab = (size_t)256 * ((c->cap + kSlabSlack) * sizeof(int16_t) + c->cap * sizeof(uint8_t));
     k_nl_build_slab<<<(unsigned)(c->sm_count * 3), 256, sslab, s>>>(
         c->nw(), c->wd, c->x, c->slot_of, c->rlist2u, c->slab_range, c->nbr, c->n_nbr, c->cap,
         c->jrange, c->xq, c->xq_b, c->wire_status);
@@ -876,7 +882,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       !smem_attr((const void*)k_force_f32<true, true>))
     return bail(TBSMA_ECUDA);
   const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
-  const int slab_max = 256 * kMaxCap * (int)(sizeof(int16_t) + sizeof(uint8_t));  // k_nl_build_slab's
+  const int slab_max = 256 * ((kMaxCap + kSlabSlack) * (int)sizeof(int16_t) + kMaxCap);  // k_nl_build_slab's
   if (cudaFuncSetAttribute(k_nl_build<int4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_nl_build_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, slab_max) != cudaSuccess)
@@ -965,8 +971,9 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->wl_cell, W + 1);
   ALLOC(c->wl_atom, W + 1);
   ALLOC(c->wl_tile, W + 1);
-  ALLOC(c->nl_mode, W);
   ALLOC(c->xenv, N);
+  ALLOC(c->tenv, (size_t)(NS / kSlotTile));
+  ALLOC(c->wdis, W);
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);
@@ -991,7 +998,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(c->nl_mode, 1, W, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->wdis, 0xff, sizeof(uint32_t) * W, st) == cudaSuccess;  // NaN: cells
   ok = ok && cudaMemsetAsync(c->wire_status, 0, sizeof(uint32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->nh, 0, sizeof(NhState) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->baro, 0, sizeof(BaroState) * W, st) == cudaSuccess;
