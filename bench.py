@@ -78,6 +78,14 @@ def parse():
                         "sample the TB-SMA functions (every leg, the oracle's included)")
     p.add_argument("--table2", action="store_true",
                    help="context: steps/s of the paper's Table 2 wires, each alone, 10 and 298 K")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                   help="arithmetic of the timed context (fp64: the plain FP64 path)")
+    p.add_argument("--run-log", default=None,
+                   help="time the run through runlog.run_logged into this JSON-lines file: "
+                        "observables every 1000 steps and the mixed-vs-FP64 force check at each")
+    p.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
+                   help="graph replays or the persistent step kernel (auto: persistent where "
+                        "the context can run it)")
     return p.parse_args()
 
 
@@ -572,12 +580,13 @@ def run_ours(args):
     batch = build(specs)
     N, W = batch.n_atoms, batch.n_wires
     params = tb.au_params(r_skin=R_SKIN)
-    eng = tb.Engine(batch, precision="mixed", params=params)
+    eng = tb.Engine(batch, precision=args.precision, params=params)
     eam = args.potential == "eam"
     if eam:
         eng.set_eam(**au_eam_tables())
     launch = LAUNCH
     eng.set_launch(*launch)
+    persist_blocks = eng.set_step_mode(args.step_mode)
     eng.init_velocities()
     # the input recipe: equilibrate from the lattice start (untimed), so that
     # surface relaxation is over and list rebuilds come at their steady rate
@@ -605,10 +614,18 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.mark()
+    log = None
+    if args.run_log:
+        from paper_1311_3890_b300.runlog import RunLog, run_logged
+
+        log = RunLog(args.run_log, workload=args.workload, precision=args.precision)
     ev0.record()
-    for k in _chunks(args.steps):  # the job: steps with per-wire observables every OBS_EVERY
-        eng.step(k, 2.0)
-        ob = eng.observables()
+    if log is not None:  # the job through the run logger: reports and force checks every 1000
+        ob = run_logged(eng, args.steps, log, 2.0, report_every=OBS_EVERY, check_every=1000)
+    else:
+        for k in _chunks(args.steps):  # the job: steps with per-wire observables every OBS_EVERY
+            eng.step(k, 2.0)
+            ob = eng.observables()
     ev1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -646,10 +663,12 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    roof = pass_rooflines(eng, res[2], res[1], ck, eam=eam)
+    roof = pass_rooflines(eng, res[2], res[1], ck, eam=eam) if args.precision == "mixed" else None
     cfg = {"workload": args.workload, "atoms_per_gpu": N, "dt_fs": 2.0}
     cfg.update(workload_config(specs))
-    cfg.update({"precision": "mixed",
+    cfg.update({"precision": args.precision,
+                "step_mode": ("persistent step kernel (%d blocks)" % persist_blocks
+                              if persist_blocks else "graph replays of 50 steps"),
                 "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
                 "equilibration_steps": args.equil, "observables_every": OBS_EVERY,
                 "r_skin_A": R_SKIN, "tile_atoms": launch[0], "window_atoms": launch[1],
@@ -658,7 +677,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "mixed f32 pair / f64 state",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed f32 pair / f64 state" if args.precision == "mixed" else "f64",
         "data": "synthetic", "config": cfg,
         "roofline": roof,
         "clocks": ck,
@@ -672,6 +692,7 @@ def run_ours(args):
             "rebuilt_atoms_per_atom_step": (rs1["atoms"] - rs0["atoms"]) / (N * args.steps),
             "reports": len(_chunks(args.steps)),
         },
+        "run_log": None,
         "split": {
             "steps": split_steps,
             "how": "the steps after the timed window, enqueued directly with a CUDA event after "
@@ -683,6 +704,16 @@ def run_ours(args):
             "rebuilt_atoms": rs2["atoms"] - rs1["atoms"],
         },
     }
+
+    if log is not None:
+        from paper_1311_3890_b300.runlog import read_log
+
+        log.close()
+        recs = [r for r in read_log(args.run_log) if r["kind"] == "force_check"]
+        line["run_log"] = {
+            "path": args.run_log, "force_checks": len(recs),
+            "max_err_scaled": max((max(r["max_err_scaled"]) for r in recs), default=None),
+            "norm_err": max((max(r["norm_err"]) for r in recs), default=None)}
 
     if not args.no_extras and rank == 0:
         # end to end through the public API: pinned host state in, K steps in

@@ -308,10 +308,35 @@ typedef struct {
 tbsma_status tbsma_wire_topology(tbsma_ctx* ctx, tbsma_topology* out, int32_t* labels);
 
 /* Test hook for failure detection: the bound of every union-find walk of
- * tbsma_wire_topology (default 1048576 steps).  A bound too small for the
- * graph makes the call give up: status 2 and TBSMA_ETIMEOUT, with the
- * context still usable.  Errors: EINVAL (steps < 1). */
+ * tbsma_wire_topology (default 1048576 steps), and of every wait of the
+ * persistent step kernel at a grid barrier (4 (steps - 1) polls; 1 makes
+ * every block that is not the last to arrive give up at once).  A bound too
+ * small for the graph makes tbsma_wire_topology give up: status 2 and
+ * TBSMA_ETIMEOUT; a barrier wait that gives up ends the step kernel in every
+ * block and tbsma_step_nvt_pull returns TBSMA_ETIMEOUT (the wires' state
+ * is then part-way through a step: restore it before going on).  The
+ * context stays usable.  Errors: EINVAL (steps < 1). */
 tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
+
+/* How tbsma_step_nvt_pull runs the steps.
+ *   TBSMA_STEPS_AUTO        the persistent step kernel when the context can
+ *                           run it, else graph replays (default);
+ *   TBSMA_STEPS_GRAPH       always replays of captured step graphs;
+ *   TBSMA_STEPS_PERSISTENT  the persistent step kernel (tbsma_step_nvt_pull
+ *                           returns EINVAL if the context cannot run it).
+ * The persistent step kernel runs a call's steps (up to 1000 per launch) in
+ * one cooperative launch, one block per 256-atom tile, its blocks meeting at
+ * bounded grid-wide barriers between the phases of a step: the same
+ * kernels' code per atom and per tile, so bitwise the same trajectories as
+ * the graph replays, without a launch per phase.  It serves small contexts:
+ * MIXED, the default protocol (Langevin, continuous pull), 256-atom tiles
+ * (tbsma_set_launch), and every tile of the batch resident on the GPU at
+ * once.  blocks (host, nullable) receives the blocks it would use in this
+ * context (0: it cannot run it).  Errors: EINVAL (unknown mode). */
+#define TBSMA_STEPS_AUTO 0
+#define TBSMA_STEPS_GRAPH 1
+#define TBSMA_STEPS_PERSISTENT 2
+tbsma_status tbsma_set_step_mode(tbsma_ctx* ctx, int32_t mode, int32_t* blocks);
 
 /* Tabulated embedded-atom method (EAM), the general form of the two-stage
  * many-body force the paper builds TB-SMA on (Introduction; Methods,

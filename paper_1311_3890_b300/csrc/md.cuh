@@ -332,21 +332,20 @@ __device__ __forceinline__ float narrow(double d) {
 // displacement check is integer.
 // 40 registers (6 blocks per SM): a streaming kernel needs the warps to keep
 // enough loads in flight (measured 19 us per step faster than at 56 registers)
+// (The step of atom i, step the 0-based step index; any_flag, if not null,
+// is set too when a wire is flagged.  The kernel runs one atom per thread,
+// the persistent step kernel strides its threads over the atoms.)
 template <int KICK, bool PROTO>
-__global__ void __launch_bounds__(256, 6)
-    k_integrate_mixed(int64_t N, double* __restrict__ x, double* __restrict__ v,
-                      const float* __restrict__ f32, const uint32_t* __restrict__ meta,
-                      const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk,
-                      float hd, const int64_t* __restrict__ step_counter, int4* __restrict__ xq,
-                      const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
-                      uint32_t* wire_status, double* d_grip, ProtoDev proto,
-                      const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__device__ __forceinline__ void integrate_mixed_atom(
+    int64_t i, long long step, int64_t N, double* __restrict__ x, double* __restrict__ v,
+    const float* __restrict__ f32, const uint32_t* __restrict__ meta,
+    const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk, float hd,
+    int4* __restrict__ xq, const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
+    int32_t* any_flag, uint32_t* wire_status, double* d_grip, const ProtoDev& proto,
+    const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
   const uint32_t m = meta[i];
   const uint32_t wi = meta_wire(m), kind = meta_kind(m);
   const WireDev& w = wd[wi];
-  const long long step = step_counter[0];
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
   if (PROTO && proto.baro) {  // S(dt/2) before the drift (B changes v only)
     const double bc = baro[wi].c;
@@ -421,7 +420,26 @@ __global__ void __launch_bounds__(256, 6)
   xq[i] = q;
   const int4 b = xq_b[i];
   const float ex = fixed_diff(q.x, b.x), ey = fixed_diff(q.y, b.y), ez = fixed_diff(q.z, b.z);
-  if (ex * ex + ey * ey + ez * ez > half_skin2) flag[wi] = 1;
+  if (ex * ex + ey * ey + ez * ez > half_skin2) {
+    flag[wi] = 1;
+    if (any_flag) *any_flag = 1;
+  }
+}
+
+template <int KICK, bool PROTO>
+__global__ void __launch_bounds__(256, 6)
+    k_integrate_mixed(int64_t N, double* __restrict__ x, double* __restrict__ v,
+                      const float* __restrict__ f32, const uint32_t* __restrict__ meta,
+                      const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk,
+                      float hd, const int64_t* __restrict__ step_counter, int4* __restrict__ xq,
+                      const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
+                      uint32_t* wire_status, double* d_grip, ProtoDev proto,
+                      const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  integrate_mixed_atom<KICK, PROTO>(i, step_counter[0], N, x, v, f32, meta, wd, wdyn, hk, hd, xq,
+                                    xq_b, half_skin2, flag, nullptr, wire_status, d_grip, proto, nh,
+                                    baro);
 }
 
 // Block per wire: the Nosé–Hoover half steps at a step boundary (Methods,
@@ -584,15 +602,24 @@ __global__ void __launch_bounds__(256)
 
 // Closing half kick of the last step of a sequence.
 template <int PREC>
-__global__ void k_half_kick(int64_t N, double* __restrict__ v, const float* __restrict__ f32,
-                            const double* __restrict__ f64, const uint32_t* __restrict__ meta,
-                            double hk) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N || meta_kind(meta[i]) != 0) return;
+__device__ __forceinline__ void half_kick_atom(int64_t i, int64_t N, double* __restrict__ v,
+                                               const float* __restrict__ f32,
+                                               const double* __restrict__ f64,
+                                               const uint32_t* __restrict__ meta, double hk) {
+  if (meta_kind(meta[i]) != 0) return;
   for (int d = 0; d < 3; ++d) {
     const double f = PREC == TBSMA_MIXED ? (double)f32[d * N + i] : f64[d * N + i];
     v[d * N + i] += hk * f;
   }
+}
+
+template <int PREC>
+__global__ void k_half_kick(int64_t N, double* __restrict__ v, const float* __restrict__ f32,
+                            const double* __restrict__ f64, const uint32_t* __restrict__ meta,
+                            double hk) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  half_kick_atom<PREC>(i, N, v, f32, f64, meta, hk);
 }
 
 // Block per wire: initial velocities (Philox tag 1), mobile COM removed,

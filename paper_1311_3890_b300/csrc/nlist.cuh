@@ -78,8 +78,8 @@ __device__ __forceinline__ T warp_scan(T v) {
   return v;
 }
 
-// Exclusive block scan of four counters (blockDim.x = 1024: 32 warps);
-// returns the block totals in tot[4].
+// Exclusive block scan of four counters (blockDim.x a multiple of 32, at
+// most 1024); returns the block totals in tot[4].
 __device__ __forceinline__ void block_scan4(int64_t (&v)[4], int64_t* tot) {
   __shared__ int64_t s[4][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -91,9 +91,10 @@ __device__ __forceinline__ void block_scan4(int64_t (&v)[4], int64_t* tot) {
   }
   __syncthreads();
   if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t x = s[q][lane];
+      const int64_t x = lane < nw ? s[q][lane] : 0;
       const int64_t sx = warp_scan(x);
       s[q][lane] = sx - x;  // exclusive prefix of the warp totals
       if (lane == 31) tot[q] = sx;
@@ -104,18 +105,17 @@ __device__ __forceinline__ void block_scan4(int64_t (&v)[4], int64_t* tot) {
   for (int q = 0; q < 4; ++q) v[q] = s[q][warp] + inc[q] - v[q];
 }
 
-// One block of 1024 threads: compact flagged wires, clear their flags,
-// count the rebuild, and (in the step loop) advance the step counter.
-// (Skipping the rest of the chain through a conditional graph node when no
-// wire is flagged measured 5 us per step slower than launching its kernels,
-// which return at once.)
-__global__ void __launch_bounds__(1024)
-    k_nl_plan(int W, NlWork nw, const WireDev* __restrict__ wd, int force_all, int count_rebuild,
-              int64_t* step_counter, const int64_t* __restrict__ steps_now) {
-  const int64_t steps = steps_now[0];
+// One block: compact flagged wires, clear their flags, count the rebuild,
+// and (in the step loop) advance the step counter; `steps` is the step
+// count at this plan.  (Skipping the rest of the chain through a
+// conditional graph node when no wire is flagged measured 5 us per step
+// slower than launching its kernels, which return at once.)
+__device__ __forceinline__ void nl_plan_body(int W, NlWork nw, const WireDev* __restrict__ wd,
+                                             int force_all, int count_rebuild,
+                                             int64_t* step_counter, int64_t steps) {
   __shared__ int64_t tot[4];
   const int t = threadIdx.x;
-  const int chunk = (W + 1023) / 1024;
+  const int chunk = (W + (int)blockDim.x - 1) / (int)blockDim.x;
   const int w0 = min(W, t * chunk), w1 = min(W, w0 + chunk);
   auto tiles_of = [](int n) { return (int64_t)((n + kSlotTile - 1) / kSlotTile); };
   int64_t v[4] = {0, 0, 0, 0};  // cells, atoms, tiles, wires
@@ -160,7 +160,14 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-__global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* cell_count) {
+__global__ void __launch_bounds__(1024)
+    k_nl_plan(int W, NlWork nw, const WireDev* __restrict__ wd, int force_all, int count_rebuild,
+              int64_t* step_counter, const int64_t* __restrict__ steps_now) {
+  nl_plan_body(W, nw, wd, force_all, count_rebuild, step_counter, steps_now[0]);
+}
+
+__device__ __forceinline__ void nl_clear_body(NlWork nw, const WireDev* __restrict__ wd,
+                                              int32_t* cell_count) {
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
   const int64_t total = nw.wl_cell[nf];
@@ -171,6 +178,9 @@ __global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* c
     const WireDev& w = wd[nw.wl_wire[k]];
     cell_count[w.cell_base + (idx - nw.wl_cell[k])] = 0;
   }
+}
+__global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* cell_count) {
+  nl_clear_body(nw, wd, cell_count);
 }
 
 // Cell coordinate along one axis, clamped into the grid; `out` is set when
@@ -183,9 +193,10 @@ __device__ __forceinline__ int cell_coord(double rel, double lo, double einv, in
 
 // Bin the atoms of flagged wires (positions from the caller's FP64 array).
 // The atom's cell coordinates are kept (packed cx << 20 | cy << 10 | cz) for the build.
-__global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-                         int64_t N, int32_t* cell_count, int32_t* cell_atoms, int32_t* cell_of,
-                         uint32_t* wire_status) {
+__device__ __forceinline__ void nl_bin_body(NlWork nw, const WireDev* __restrict__ wd,
+                                            const double* __restrict__ x, int64_t N,
+                                            int32_t* cell_count, int32_t* cell_atoms,
+                                            int32_t* cell_of, uint32_t* wire_status) {
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
   const int64_t total = nw.wl_atom[nf];
@@ -208,10 +219,15 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
     else atomicOr(&wire_status[wi], kWireCellOverflow);
   }
 }
+__global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+                         int64_t N, int32_t* cell_count, int32_t* cell_atoms, int32_t* cell_of,
+                         uint32_t* wire_status) {
+  nl_bin_body(nw, wd, x, N, cell_count, cell_atoms, cell_of, wire_status);
+}
 
 // Warp per flagged cell: sort its members ascending (rank by counting).
-__global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32_t* cell_count,
-                          int32_t* cell_atoms) {
+__device__ __forceinline__ void nl_sort_body(NlWork nw, const WireDev* __restrict__ wd,
+                                             const int32_t* cell_count, int32_t* cell_atoms) {
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
   const int64_t total = nw.wl_cell[nf];
@@ -229,6 +245,10 @@ __global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32
     __syncwarp();
     if (lane < cnt) cell_atoms[c * kCellCap + rank] = m;
   }
+}
+__global__ void k_nl_sort(NlWork nw, const WireDev* __restrict__ wd, const int32_t* cell_count,
+                          int32_t* cell_atoms) {
+  nl_sort_body(nw, wd, cell_count, cell_atoms);
 }
 
 // Distance test of the list builds on the packed positions: modular fixed
@@ -288,14 +308,12 @@ __device__ __forceinline__ int byte_of(uint64_t v, int g) { return (int)((v >> (
 // that rebuilds more often (298 K) keeps the rows in quad order.
 constexpr int kBuildQuad = 4;
 template <typename PosT>
-__global__ void __launch_bounds__(256)
-    k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
-               const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
-               const int32_t* __restrict__ slot_of, float rlist2 /* in build_d2's units */,
-               int16_t* __restrict__ nbr,
-               int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
-               const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
-               uint32_t* wire_status) {
+__device__ __forceinline__ void nl_build_body(
+    NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
+    const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
+    const int32_t* __restrict__ slot_of, float rlist2 /* in build_d2's units */,
+    int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
+    const PosT* __restrict__ pos, PosT* __restrict__ pos_build, uint32_t* wire_status) {
   extern __shared__ int16_t sbuf[];  // [cap][blockDim.x]: entry e of thread x at e * blockDim.x + x
   const int nf = nw.n_flagged[0];
   if (nf == 0) return;
@@ -415,6 +433,17 @@ __global__ void __launch_bounds__(256)
     }
   }
 }
+template <typename PosT>
+__global__ void __launch_bounds__(256)
+    k_nl_build(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ cell_count,
+               const int32_t* __restrict__ cell_atoms, const int32_t* __restrict__ cell_of,
+               const int32_t* __restrict__ slot_of, float rlist2, int16_t* __restrict__ nbr,
+               int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
+               const PosT* __restrict__ pos, PosT* __restrict__ pos_build,
+               uint32_t* wire_status) {
+  nl_build_body<PosT>(nw, wd, cell_count, cell_atoms, cell_of, slot_of, rlist2, nbr, n_nbr, cap,
+                      jrange, pos, pos_build, wire_status);
+}
 
 // ---------------------------------------------------------------- slab build
 // Atoms keep their [100] order, so the neighbours of 32 consecutive atoms of
@@ -462,8 +491,8 @@ __device__ __forceinline__ void tile_scans(float& mx, float& mn, float& bmx, flo
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSlotTile)
-    k_nl_env_tiles(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x) {
+__device__ __forceinline__ void nl_env_tiles_body(NlWork nw, const WireDev* __restrict__ wd,
+                                                  const double* __restrict__ x) {
   const int nf = nw.n_flagged[0];
   if (nf == 0 || !nw.slab_ok) return;
   const int64_t tiles = nw.wl_tile[nf];
@@ -484,9 +513,12 @@ __global__ void __launch_bounds__(kSlotTile)
     }
   }
 }
-
 __global__ void __launch_bounds__(kSlotTile)
-    k_nl_env_merge(NlWork nw, const WireDev* __restrict__ wd) {
+    k_nl_env_tiles(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x) {
+  nl_env_tiles_body(nw, wd, x);
+}
+
+__device__ __forceinline__ void nl_env_merge_body(NlWork nw, const WireDev* __restrict__ wd) {
   __shared__ float s_red[2][kSlotTile / 32];
   const int nf = nw.n_flagged[0];
   if (nf == 0 || !nw.slab_ok) return;
@@ -538,6 +570,9 @@ __global__ void __launch_bounds__(kSlotTile)
     for (int o = 16; o > 0; o >>= 1) dis = fmaxf(dis, __shfl_xor_sync(0xffffffffu, dis, o));
     if (lane == 0 && dis > 0.f) atomicMax(nw.wdis + wi, __float_as_uint(dis));
   }
+}
+__global__ void __launch_bounds__(kSlotTile) k_nl_env_merge(NlWork nw, const WireDev* __restrict__ wd) {
+  nl_env_merge_body(nw, wd);
 }
 
 // First wire-relative index q <= top with env[q].x >= v (env[top].x >= v
@@ -604,12 +639,11 @@ __device__ __forceinline__ int slab_hi(const float2* env, int bot, int n, float 
 // the packed position, as the cell build.  The entry buffer has room for
 // cap + kSlabSlack entries per lane (cap neighbours and the atom itself).
 constexpr int kSlabSlack = 1;
-__global__ void __launch_bounds__(256)
-    k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-                    const int32_t* __restrict__ slot_of, float rlist2u, float xrange,
-                    int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
-                    int2* __restrict__ jrange, const int4* __restrict__ xq, int4* __restrict__ xq_b,
-                    uint32_t* wire_status) {
+__device__ __forceinline__ void nl_build_slab_body(
+    NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+    const int32_t* __restrict__ slot_of, float rlist2u, float xrange, int16_t* __restrict__ nbr,
+    int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange, const int4* __restrict__ xq,
+    int4* __restrict__ xq_b, uint32_t* wire_status) {
   extern __shared__ int16_t sA[];  // [cap + kSlabSlack][blockDim.x]: offsets, ascending, by column
   const int B = blockDim.x;
   uint8_t* sB = reinterpret_cast<uint8_t*>(sA + (size_t)(cap + kSlabSlack) * B);  // [cap][B]
@@ -744,6 +778,15 @@ __global__ void __launch_bounds__(256)
     jrange[t] = nr > 0 ? make_int2(ii + entry(0), ii + entry(nr - 1)) : make_int2(INT_MAX, INT_MIN);
     xq_b[i] = pi;
   }
+}
+__global__ void __launch_bounds__(256)
+    k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
+                    const int32_t* __restrict__ slot_of, float rlist2u, float xrange,
+                    int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
+                    int2* __restrict__ jrange, const int4* __restrict__ xq, int4* __restrict__ xq_b,
+                    uint32_t* wire_status) {
+  nl_build_slab_body(nw, wd, x, slot_of, rlist2u, xrange, nbr, n_nbr, cap, jrange, xq, xq_b,
+                     wire_status);
 }
 
 // Row-major copy of the tiled lists (for the list accessor).

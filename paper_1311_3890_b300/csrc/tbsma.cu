@@ -22,6 +22,7 @@
 #include "nlist.cuh"
 #include "pair.cuh"
 #include "topo.cuh"
+#include "persist.cuh"
 
 using namespace tbsma;
 
@@ -29,6 +30,7 @@ namespace {
 
 constexpr int kGraphChunk = 50;  // steps per captured graph
 constexpr int64_t kGrowCheckSteps = 1000;  // steps between cell-grid checks inside one step call
+static_assert(kGrowCheckSteps % kGraphChunk == 0, "grid checks fall on kick-sequence boundaries");
 
 // An NVTX range over one library call, for timeline tools (nsys): the
 // header-only NVTX3 API does nothing unless a tool is attached.  Inside the
@@ -127,7 +129,10 @@ struct tbsma_ctx {
   int* uf_parent = nullptr;         // union-find of the topology call (allocated on first use)
   uint32_t* uf_err = nullptr;
   tbsma_topology* topo_d = nullptr;
-  int wait_limit = kUfSteps;        // bound of the topology's union-find walks
+  int wait_limit = kUfSteps;        // bound of the topology's union-find walks and barrier waits
+  int step_mode = TBSMA_STEPS_AUTO;  // graph replays or the persistent step kernel
+  unsigned* bar = nullptr;           // [3] grid barrier of the persistent step kernel
+  int32_t* any_flag = nullptr;       // [2] some wire flagged in a step of this parity
   tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
   double* d_grip = nullptr;
   int64_t* step_counter = nullptr;
@@ -611,6 +616,96 @@ tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
   return TBSMA_OK;
 }
 
+// ------------------------------------------------ persistent step kernel
+// Dynamic shared memory of the persistent step kernel: the largest of the
+// pair passes' window and the two builds' buffers.
+size_t persist_smem(const tbsma_ctx* c) {
+  const size_t window = (size_t)c->wcap * sizeof(int4);
+  const size_t cell = (size_t)256 * c->cap * sizeof(int16_t);
+  const size_t slab = (size_t)256 * ((c->cap + kSlabSlack) * sizeof(int16_t) + c->cap);
+  return std::max(window, std::max(cell, slab));
+}
+
+// Blocks of the persistent step kernel for this context, 0 if it cannot run
+// it: MIXED, the default protocol, 256-atom tiles, and every tile of the
+// batch resident at once (one block per tile, at most the co-resident
+// blocks of a cooperative launch).
+int persist_blocks(tbsma_ctx* c) {
+  if (c->prec != TBSMA_MIXED || protocol_mode(c) || c->block != 256) return 0;
+  int per_sm = 0;
+  const void* fn = c->eam_on ? (const void*)k_steps_persistent<true> : (const void*)k_steps_persistent<false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, persist_smem(c)) != cudaSuccess)
+    return 0;
+  const int64_t tiles = c->NS / 256;
+  const int64_t most = (int64_t)per_sm * c->sm_count;
+  if (tiles < 1 || tiles > most) return 0;
+  return (int)tiles;
+}
+
+// n steps in one cooperative launch of the persistent step kernel (the
+// caller has checked persist_blocks > 0 and set dt).  Same steps, kicks and
+// step counts as enqueue_steps.
+tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double dt) {
+  PersistArgs a;
+  a.N = c->N;
+  a.NS = c->NS;
+  a.W = c->W;
+  a.x = c->x;
+  a.v = c->v;
+  a.f32 = c->f32;
+  a.meta = c->meta;
+  a.wd = c->wd;
+  a.wdyn = c->wdyn;
+  a.hk_open = (float)(0.5 * dt * c->inv_m);
+  a.hk_full = (float)(dt * c->inv_m);
+  a.hd = (float)(0.5 * dt);
+  a.hk_close = 0.5 * dt * c->inv_m;
+  a.xq = c->xq;
+  a.xq_b = c->xq_b;
+  a.half_skin2 = (float)c->half_skin2;
+  a.flag = c->flag;
+  a.any_flag = c->any_flag;
+  a.wire_status = c->wire_status;
+  a.d_grip = c->d_grip;
+  a.step_counter = c->step_counter;
+  a.nw = c->nw();
+  a.cell_count = c->cell_count;
+  a.cell_atoms = c->cell_atoms;
+  a.cell_of = c->cell_of;
+  a.slot_of = c->slot_of;
+  a.rlist2u = c->rlist2u;
+  a.slab_range = c->slab_range;
+  a.nbr = c->nbr;
+  a.n_nbr = c->n_nbr;
+  a.cap = c->cap;
+  a.jrange = c->jrange;
+  a.perm = c->perm;
+  a.wcap = c->wcap;
+  a.pc = c->pc;
+  a.eam = c->eam;
+  a.step0 = c->steps_done;
+  a.n_steps = n;
+  a.seq = seq;
+  a.bar = GridBarrier{c->bar, c->bar + 1, c->bar + 2,
+                      (unsigned)std::max(0, c->wait_limit - 1) * 4u};
+  TB_CUDA(c, cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), c->stream));
+  TB_CUDA(c, cudaMemsetAsync(c->any_flag, 0, 2 * sizeof(int32_t), c->stream));
+  void* args[] = {&a};
+  const void* fn = c->eam_on ? (const void*)k_steps_persistent<true> : (const void*)k_steps_persistent<false>;
+  TB_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), args,
+                                         persist_smem(c), c->stream));
+  return TBSMA_OK;
+}
+
+// The persistent kernel's barrier error word: ETIMEOUT if a wait gave up.
+tbsma_status persist_verdict(tbsma_ctx* c) {
+  unsigned err = 0;
+  TB_CUDA(c, cudaMemcpyAsync(&err, c->bar + 2, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+  TB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (err) return fail(c, TBSMA_ETIMEOUT, "a grid barrier of the persistent step kernel gave up");
+  return TBSMA_OK;
+}
+
 tbsma_status read_status(tbsma_ctx* c, std::vector<uint32_t>& st) {
   st.resize(c->W);
   TB_CUDA(c, cudaMemcpyAsync(st.data(), c->wire_status, sizeof(uint32_t) * c->W,
@@ -887,6 +982,10 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_nl_build_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, slab_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
+  const int persist_max = std::max(std::max(smem_max, sbuf_max), slab_max);
+  if (cudaFuncSetAttribute(k_steps_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
 #define ALLOC(ptr, n)                          \
@@ -978,6 +1077,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);
   ALLOC(c->rebuilt, 2);
+  ALLOC(c->bar, 3);
+  ALLOC(c->any_flag, 2);
   ALLOC(c->last_build, W);
   ALLOC(c->banked, W);
   ALLOC(c->wire_status, W);
@@ -996,6 +1097,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->any_flag, 0, 2 * sizeof(int32_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wdis, 0xff, sizeof(uint32_t) * W, st) == cudaSuccess;  // NaN: cells
@@ -1079,6 +1182,29 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
   if (n_steps < 0 || !(dt_fs > 0.0)) return fail(c, TBSMA_EINVAL, "n_steps < 0 or dt <= 0");
   if (n_steps == 0) return TBSMA_OK;
   TB_TRY(set_dt(c, dt_fs));
+  const int pblocks = c->step_mode == TBSMA_STEPS_GRAPH ? 0 : persist_blocks(c);
+  if (c->step_mode == TBSMA_STEPS_PERSISTENT && pblocks == 0)
+    return fail(c, TBSMA_EINVAL, "this context cannot run the persistent step kernel");
+  if (pblocks > 0) {
+    // kick sequences as the graph path runs them: min(n_steps, kGraphChunk)
+    // steps each (kGrowCheckSteps is a multiple of kGraphChunk)
+    const int seq = (int)std::min<int64_t>(n_steps, kGraphChunk);
+    int64_t left = n_steps;
+    while (left > 0) {
+      const int n = (int)std::min<int64_t>(left, kGrowCheckSteps);
+      TB_TRY(launch_persistent(c, pblocks, n, seq, dt_fs));
+      left -= n;
+      c->steps_done += n;
+      TB_TRY(persist_verdict(c));
+      if (left > 0) {
+        std::vector<uint32_t> st;
+        int ofw = -1;
+        TB_TRY(check_grids(c, st, ofw));
+        if (ofw >= 0) return status_verdict(c);
+      }
+    }
+    return status_verdict(c);
+  }
   const int chunk = (int)std::min<int64_t>(n_steps, kGraphChunk);
   if (!c->graph.exec || c->graph_dt != dt_fs || c->graph.steps != chunk) TB_TRY(capture(c, chunk, dt_fs));
   int64_t left = n_steps, since_check = 0;
@@ -1344,6 +1470,15 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* c, int32_t steps) {
   if (!c) return TBSMA_EINVAL;
   if (steps < 1) return fail(c, TBSMA_EINVAL, "the wait limit must be >= 1");
   c->wait_limit = steps;
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_set_step_mode(tbsma_ctx* c, int32_t mode, int32_t* blocks) {
+  if (!c) return TBSMA_EINVAL;
+  if (mode != TBSMA_STEPS_AUTO && mode != TBSMA_STEPS_GRAPH && mode != TBSMA_STEPS_PERSISTENT)
+    return fail(c, TBSMA_EINVAL, "unknown step mode");
+  c->step_mode = mode;
+  if (blocks) *blocks = mode == TBSMA_STEPS_GRAPH ? 0 : persist_blocks(c);
   return TBSMA_OK;
 }
 

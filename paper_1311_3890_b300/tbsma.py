@@ -128,6 +128,7 @@ class EamC(ctypes.Structure):
 THERMOSTATS = {"langevin": 0, "nose_hoover": 1}
 BARO_MODULUS = 100.0 / 160.21766208  # 100 GPa in eV/A^3: the barostat's reference modulus
 PULLS = {"continuous": 0, "stepwise": 1}
+STEP_MODES = {"auto": 0, "graph": 1, "persistent": 2}
 
 SIGNATURES = [
     ("tbsma_init", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
@@ -155,6 +156,7 @@ SIGNATURES = [
     ("tbsma_eam_cubics", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("tbsma_set_step_mode", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("tbsma_restore_state", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
@@ -437,6 +439,15 @@ class Engine:
     def set_wait_limit(self, steps: int):
         """Bound of the topology's union-find walks (a failure-detection test hook)."""
         self._check(lib().tbsma_set_wait_limit(self.ctx, int(steps)), "tbsma_set_wait_limit")
+
+    def set_step_mode(self, mode: str = "auto") -> int:
+        """How steps run (tbsma_set_step_mode): "auto", "graph" or
+        "persistent"; returns the blocks the persistent step kernel would use
+        in this context (0: it cannot run it)."""
+        b = ctypes.c_int32(0)
+        self._check(lib().tbsma_set_step_mode(self.ctx, STEP_MODES[mode], ctypes.byref(b)),
+                    "tbsma_set_step_mode")
+        return int(b.value)
 
     def save(self, path: str):
         """Checkpoint into directory `path` (tbsma_save_state): header.json and

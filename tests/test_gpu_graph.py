@@ -37,6 +37,7 @@ def test_graph_and_direct_steps_agree_bitwise(tb, prec):
     out = []
     for split in ([50, 25] * 4, [75] * 4):
         eng = tb.Engine(b, precision=prec)
+        eng.set_step_mode("graph")
         eng.init_velocities()
         for n in split:
             eng.step(n, 2.0)
@@ -65,6 +66,7 @@ def test_profiled_steps_equal_graph_steps(tb, prec):
     out = []
     for profiled in (False, True):
         eng = tb.Engine(b, precision=prec)
+        eng.set_step_mode("graph")
         rs = eng.rebuild_stats()
         assert rs == {"chains": 2, "wires": 2 * b.n_wires, "atoms": 2 * b.n_atoms}
         eng.init_velocities()
@@ -77,3 +79,82 @@ def test_profiled_steps_equal_graph_steps(tb, prec):
     assert ra == rb and ra["chains"] == 2 + 120 and ra["wires"] > 2 * b.n_wires
     assert set(ph) == {"integrate", "plan", "rebuild", "density", "force", "kick"}
     assert all(v > 0.0 for v in ph.values())
+
+
+def test_persistent_step_kernel_equals_graph_replays(tb):
+    """The persistent step kernel (one cooperative launch per call, grid
+    barriers between the phases) runs the graph path's code per atom and
+    per tile: 300 steps of the tiny batch (10 K and 298 K wires, pulled,
+    with list rebuilds) in calls of 50 and 25 steps give bitwise the
+    positions, velocities, rebuild counts and list-build accounting of
+    graph replays, and the observables after them agree."""
+    b = workload("tiny_batch")
+    out = []
+    for mode in ("graph", "persistent"):
+        eng = tb.Engine(b, precision="mixed")
+        blocks = eng.set_step_mode(mode)
+        if mode == "persistent":
+            assert blocks == int(np.sum((b.n + 255) // 256))  # one block per tile
+        eng.init_velocities()
+        for n in [50, 25] * 4:
+            eng.step(n, 2.0)
+        ob = eng.observables()
+        out.append((eng.positions(), eng.velocities(), ob, eng.rebuild_stats()))
+        eng.close()
+    (xa, va, oa, ra), (xb, vb, ob, rb) = out
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(oa["n_rebuilds"], ob["n_rebuilds"])
+    assert oa["n_rebuilds"].sum() > 3  # the wires did rebuild
+    assert ra == rb
+    for k in ("e_pot", "e_kin", "sigma_xx", "strain"):
+        np.testing.assert_array_equal(oa[k], ob[k])
+
+
+def test_persistent_barrier_gives_up_and_context_recovers(tb, tmp_path):
+    """Failure detection of the persistent step kernel without a fault: with
+    the wait limit at 1 every block that is not the last to reach a grid
+    barrier gives up at once, every block leaves, and the step call returns
+    TBSMA_ETIMEOUT.  With the limit restored, the same context resumes from
+    a checkpoint and continues bit for bit as a context that never timed
+    out."""
+    b = workload("tiny_batch")
+    eng = tb.Engine(b, precision="mixed")
+    assert eng.set_step_mode("persistent") > 1
+    eng.init_velocities()
+    eng.step(100, 2.0)
+    ck = str(tmp_path / "ck")
+    eng.save(ck)
+    eng.set_wait_limit(1)
+    with pytest.raises(tb.TbsmaError) as e:
+        eng.step(20, 2.0)
+    assert e.value.status == 5  # TBSMA_ETIMEOUT
+    eng.set_wait_limit(1 << 20)
+    eng.load(ck)
+    eng.step(100, 2.0)
+    x1, v1 = eng.positions(), eng.velocities()
+    eng.close()
+    ref = tb.Engine(b, precision="mixed")
+    ref.set_step_mode("persistent")
+    ref.load(ck)
+    ref.step(100, 2.0)
+    np.testing.assert_array_equal(ref.positions(), x1)
+    np.testing.assert_array_equal(ref.velocities(), v1)
+    ref.close()
+
+
+def test_persistent_mode_is_refused_where_it_cannot_run(tb):
+    """FP64 contexts and the paper's protocol mode run graph replays; asking
+    them for the persistent step kernel is an EINVAL at the step call."""
+    b = workload("tiny_batch")
+    eng = tb.Engine(b, precision="fp64")
+    assert eng.set_step_mode("persistent") == 0
+    with pytest.raises(tb.TbsmaError) as e:
+        eng.step(5, 2.0)
+    assert e.value.status == 1
+    eng.close()
+    eng = tb.Engine(b, precision="mixed")
+    eng.set_protocol()
+    assert eng.set_step_mode("auto") == 0
+    eng.step(5, 2.0)  # graph replays
+    eng.close()
