@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--run-log", default=None,
                    help="time the run through runlog.run_logged into this JSON-lines file: "
                         "observables every 1000 steps and the mixed-vs-FP64 force check at each")
+    p.add_argument("--lanes", type=int, default=1, choices=[1, 4],
+                   help="threads per atom in the pair passes (bitwise the same results)")
     p.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                    help="graph replays or the persistent step kernel (auto: persistent where "
                         "the context can run it)")
@@ -586,6 +588,7 @@ def run_ours(args):
         eng.set_eam(**au_eam_tables())
     launch = LAUNCH
     eng.set_launch(*launch)
+    eng.set_pair_lanes(args.lanes)
     persist_blocks = eng.set_step_mode(args.step_mode)
     eng.init_velocities()
     # the input recipe: equilibrate from the lattice start (untimed), so that
@@ -621,7 +624,8 @@ def run_ours(args):
         log = RunLog(args.run_log, workload=args.workload, precision=args.precision)
     ev0.record()
     if log is not None:  # the job through the run logger: reports and force checks every 1000
-        ob = run_logged(eng, args.steps, log, 2.0, report_every=OBS_EVERY, check_every=1000)
+        # a report every 1000 steps, and the force check at every report
+        ob = run_logged(eng, args.steps, log, 2.0, report_every=OBS_EVERY, check_every=1)
     else:
         for k in _chunks(args.steps):  # the job: steps with per-wire observables every OBS_EVERY
             eng.step(k, 2.0)
@@ -672,6 +676,7 @@ def run_ours(args):
                 "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
                 "equilibration_steps": args.equil, "observables_every": OBS_EVERY,
                 "r_skin_A": R_SKIN, "tile_atoms": launch[0], "window_atoms": launch[1],
+                "pair_lanes": args.lanes,
                 "launch": "autotuned" if args.autotune else "fixed",
                 "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"})
     line = {

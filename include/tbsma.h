@@ -333,6 +333,15 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
  * (tbsma_set_launch), and every tile of the batch resident on the GPU at
  * once.  blocks (host, nullable) receives the blocks it would use in this
  * context (0: it cannot run it).  Errors: EINVAL (unknown mode). */
+/* Threads per atom in the MIXED pair passes, graph replays and the
+ * persistent step kernel alike: 1 (default; one thread walks the atom's
+ * list) or 4 (four threads per atom, each evaluating one entry of every
+ * group of four, the terms added in list order through shuffles: bitwise
+ * the same forces and energies).  Measured on a B300, 4 is slower both on
+ * large batches and on a lone 17k-atom wire; it is kept because it is
+ * exact.  Invalidates captured graphs.  Errors: EINVAL (other values). */
+tbsma_status tbsma_set_pair_lanes(tbsma_ctx* ctx, int32_t lanes);
+
 #define TBSMA_STEPS_AUTO 0
 #define TBSMA_STEPS_GRAPH 1
 #define TBSMA_STEPS_PERSISTENT 2

@@ -108,11 +108,11 @@ struct PersistArgs {
   GridBarrier bar;
 };
 
-template <bool EAM>
+template <bool EAM, int LANES>
 __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t ntiles = a.NS / blockDim.x;
+  const int64_t ntiles = a.NS * LANES / blockDim.x;  // pair-pass tiles of blockDim / LANES atoms
   const ProtoDev proto{};
   for (int k = 0; k < a.n_steps; ++k) {
     const long long step = a.step0 + k;
@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
     }
     // density pass, force pass
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-      density_f32_tile<false, EAM>(tile, a.NS, a.xq, a.nbr, a.n_nbr, a.perm, a.jrange, a.cap,
+      density_f32_tile<false, EAM, LANES>(tile, a.NS, a.xq, a.nbr, a.n_nbr, a.perm, a.jrange, a.cap,
                                    a.wcap, a.pc, nullptr, a.eam);
     if (!grid_sync(a.bar)) return;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-      force_f32_tile<false, EAM>(tile, a.NS, a.xq, a.nbr, a.n_nbr, a.perm, a.jrange, a.cap, a.wcap,
+      force_f32_tile<false, EAM, LANES>(tile, a.NS, a.xq, a.nbr, a.n_nbr, a.perm, a.jrange, a.cap, a.wcap,
                                  a.pc, a.f32, a.f32 + a.N, a.f32 + 2 * a.N, nullptr, nullptr,
                                  nullptr, nullptr, a.eam);
     if (!grid_sync(a.bar)) return;

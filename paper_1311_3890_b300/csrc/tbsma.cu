@@ -131,6 +131,7 @@ struct tbsma_ctx {
   tbsma_topology* topo_d = nullptr;
   int wait_limit = kUfSteps;        // bound of the topology's union-find walks and barrier waits
   int step_mode = TBSMA_STEPS_AUTO;  // graph replays or the persistent step kernel
+  int lanes = 1;  // threads per atom in the MIXED pair passes: 1 or 4
   unsigned* bar = nullptr;           // [3] grid barrier of the persistent step kernel
   int32_t* any_flag = nullptr;       // [2] some wire flagged in a step of this parity
   tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
@@ -352,24 +353,35 @@ tbsma_status launch_nl(tbsma_ctx* c, cudaStream_t s, int force_all, int count_re
   return launch_rebuild(c, s);
 }
 
-template <bool OBS, bool EAM>
+template <bool OBS, bool EAM, int LANES>
 void pair_f32_pot(tbsma_ctx* c, cudaStream_t s, int which) {
-  const unsigned g = grid_for(c->NS, c->block);
+  const unsigned g = grid_for(c->NS * LANES, c->block);
   const size_t smem = (size_t)c->wcap * sizeof(int4);
   if (which & 1)
-    k_density_f32<OBS, EAM><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange,
-                                                      c->cap, c->wcap, c->pc, c->e_band, c->eam);
+    k_density_f32<OBS, EAM, LANES><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm,
+                                                             c->jrange, c->cap, c->wcap, c->pc,
+                                                             c->e_band, c->eam);
   if (which & 2)
-    k_force_f32<OBS, EAM><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm, c->jrange,
-                                                    c->cap, c->wcap, c->pc, c->f32, c->f32 + c->N,
-                                                    c->f32 + 2 * c->N, c->e_band, c->e_atom,
-                                                    c->w_atom, c->s_atom, c->eam);
+    k_force_f32<OBS, EAM, LANES><<<g, c->block, smem, s>>>(c->NS, c->xq, c->nbr, c->n_nbr, c->perm,
+                                                           c->jrange, c->cap, c->wcap, c->pc, c->f32,
+                                                           c->f32 + c->N, c->f32 + 2 * c->N,
+                                                           c->e_band, c->e_atom, c->w_atom, c->s_atom,
+                                                           c->eam);
 }
+
+// Threads per atom of the MIXED pair passes.
+int graph_lanes(const tbsma_ctx* c) { return c->lanes == 4 ? 4 : 1; }
 
 template <bool OBS>
 void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
-  if (c->eam_on) pair_f32_pot<OBS, true>(c, s, which);
-  else pair_f32_pot<OBS, false>(c, s, which);
+  const bool four = graph_lanes(c) == 4;
+  if (c->eam_on) {
+    if (four) pair_f32_pot<OBS, true, 4>(c, s, which);
+    else pair_f32_pot<OBS, true, 1>(c, s, which);
+  } else {
+    if (four) pair_f32_pot<OBS, false, 4>(c, s, which);
+    else pair_f32_pot<OBS, false, 1>(c, s, which);
+  }
 }
 
 template <bool OBS, bool DECIDE32, bool EAM>
@@ -630,16 +642,26 @@ size_t persist_smem(const tbsma_ctx* c) {
 // it: MIXED, the default protocol, 256-atom tiles, and every tile of the
 // batch resident at once (one block per tile, at most the co-resident
 // blocks of a cooperative launch).
+// Threads per atom of the persistent kernel's pair passes.
+int persist_lanes(const tbsma_ctx* c) { return c->lanes == 4 ? 4 : 1; }
+
+const void* persist_fn(const tbsma_ctx* c) {
+  if (persist_lanes(c) == 4)
+    return c->eam_on ? (const void*)k_steps_persistent<true, 4> : (const void*)k_steps_persistent<false, 4>;
+  return c->eam_on ? (const void*)k_steps_persistent<true, 1> : (const void*)k_steps_persistent<false, 1>;
+}
+
 int persist_blocks(tbsma_ctx* c) {
   if (c->prec != TBSMA_MIXED || protocol_mode(c) || c->block != 256) return 0;
   int per_sm = 0;
-  const void* fn = c->eam_on ? (const void*)k_steps_persistent<true> : (const void*)k_steps_persistent<false>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, persist_smem(c)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_fn(c), 256, persist_smem(c)) !=
+      cudaSuccess)
     return 0;
   const int64_t tiles = c->NS / 256;
   const int64_t most = (int64_t)per_sm * c->sm_count;
   if (tiles < 1 || tiles > most) return 0;
-  return (int)tiles;
+  // one block per tile of the pair passes (256 / lanes atoms), as many as fit
+  return (int)std::min<int64_t>(tiles * persist_lanes(c), most);
 }
 
 // n steps in one cooperative launch of the persistent step kernel (the
@@ -691,8 +713,7 @@ tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double 
   TB_CUDA(c, cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), c->stream));
   TB_CUDA(c, cudaMemsetAsync(c->any_flag, 0, 2 * sizeof(int32_t), c->stream));
   void* args[] = {&a};
-  const void* fn = c->eam_on ? (const void*)k_steps_persistent<true> : (const void*)k_steps_persistent<false>;
-  TB_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), args,
+  TB_CUDA(c, cudaLaunchCooperativeKernel(persist_fn(c), dim3((unsigned)blocks), dim3(256), args,
                                          persist_smem(c), c->stream));
   return TBSMA_OK;
 }
@@ -967,14 +988,22 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   const auto smem_attr = [&](const void* k) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) == cudaSuccess;
   };
-  if (!smem_attr((const void*)k_density_f32<false, false>) ||
-      !smem_attr((const void*)k_density_f32<true, false>) ||
-      !smem_attr((const void*)k_force_f32<false, false>) ||
-      !smem_attr((const void*)k_force_f32<true, false>) ||
-      !smem_attr((const void*)k_density_f32<false, true>) ||
-      !smem_attr((const void*)k_density_f32<true, true>) ||
-      !smem_attr((const void*)k_force_f32<false, true>) ||
-      !smem_attr((const void*)k_force_f32<true, true>))
+  if (!smem_attr((const void*)k_density_f32<false, false, 1>) ||
+      !smem_attr((const void*)k_density_f32<true, false, 1>) ||
+      !smem_attr((const void*)k_force_f32<false, false, 1>) ||
+      !smem_attr((const void*)k_force_f32<true, false, 1>) ||
+      !smem_attr((const void*)k_density_f32<false, true, 1>) ||
+      !smem_attr((const void*)k_density_f32<true, true, 1>) ||
+      !smem_attr((const void*)k_force_f32<false, true, 1>) ||
+      !smem_attr((const void*)k_force_f32<true, true, 1>) ||
+      !smem_attr((const void*)k_density_f32<false, false, 4>) ||
+      !smem_attr((const void*)k_density_f32<true, false, 4>) ||
+      !smem_attr((const void*)k_force_f32<false, false, 4>) ||
+      !smem_attr((const void*)k_force_f32<true, false, 4>) ||
+      !smem_attr((const void*)k_density_f32<false, true, 4>) ||
+      !smem_attr((const void*)k_density_f32<true, true, 4>) ||
+      !smem_attr((const void*)k_force_f32<false, true, 4>) ||
+      !smem_attr((const void*)k_force_f32<true, true, 4>))
     return bail(TBSMA_ECUDA);
   const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
   const int slab_max = 256 * ((kMaxCap + kSlabSlack) * (int)sizeof(int16_t) + kMaxCap);  // k_nl_build_slab's
@@ -983,8 +1012,10 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       cudaFuncSetAttribute(k_nl_build_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, slab_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int persist_max = std::max(std::max(smem_max, sbuf_max), slab_max);
-  if (cudaFuncSetAttribute(k_steps_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_steps_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_steps_persistent<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
@@ -1470,6 +1501,14 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* c, int32_t steps) {
   if (!c) return TBSMA_EINVAL;
   if (steps < 1) return fail(c, TBSMA_EINVAL, "the wait limit must be >= 1");
   c->wait_limit = steps;
+  return TBSMA_OK;
+}
+
+tbsma_status tbsma_set_pair_lanes(tbsma_ctx* c, int32_t lanes) {
+  if (!c) return TBSMA_EINVAL;
+  if (lanes != 1 && lanes != 4) return fail(c, TBSMA_EINVAL, "lanes must be 1 or 4");
+  c->lanes = lanes;
+  drop_graph(c);
   return TBSMA_OK;
 }
 

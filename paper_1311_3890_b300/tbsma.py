@@ -157,6 +157,7 @@ SIGNATURES = [
     ("tbsma_wire_topology", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tbsma_set_step_mode", ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    ("tbsma_set_pair_lanes", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tbsma_save_state", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("tbsma_restore_state", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     ("tbsma_philox4x32_10", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
@@ -448,6 +449,11 @@ class Engine:
         self._check(lib().tbsma_set_step_mode(self.ctx, STEP_MODES[mode], ctypes.byref(b)),
                     "tbsma_set_step_mode")
         return int(b.value)
+
+    def set_pair_lanes(self, lanes: int = 1):
+        """Threads per atom in the MIXED pair passes (tbsma_set_pair_lanes):
+        1 (default) or 4 (bitwise the same results)."""
+        self._check(lib().tbsma_set_pair_lanes(self.ctx, int(lanes)), "tbsma_set_pair_lanes")
 
     def save(self, path: str):
         """Checkpoint into directory `path` (tbsma_save_state): header.json and

@@ -81,7 +81,8 @@ def test_profiled_steps_equal_graph_steps(tb, prec):
     assert all(v > 0.0 for v in ph.values())
 
 
-def test_persistent_step_kernel_equals_graph_replays(tb):
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_persistent_step_kernel_equals_graph_replays(tb, lanes):
     """The persistent step kernel (one cooperative launch per call, grid
     barriers between the phases) runs the graph path's code per atom and
     per tile: 300 steps of the tiny batch (10 K and 298 K wires, pulled,
@@ -92,9 +93,11 @@ def test_persistent_step_kernel_equals_graph_replays(tb):
     out = []
     for mode in ("graph", "persistent"):
         eng = tb.Engine(b, precision="mixed")
-        blocks = eng.set_step_mode(mode)
         if mode == "persistent":
-            assert blocks == int(np.sum((b.n + 255) // 256))  # one block per tile
+            eng.set_pair_lanes(lanes)
+        blocks = eng.set_step_mode(mode)
+        if mode == "persistent":  # one block per pair-pass tile of 256 / lanes atoms
+            assert blocks == lanes * int(np.sum((b.n + 255) // 256))
         eng.init_velocities()
         for n in [50, 25] * 4:
             eng.step(n, 2.0)
@@ -158,3 +161,27 @@ def test_persistent_mode_is_refused_where_it_cannot_run(tb):
     assert eng.set_step_mode("auto") == 0
     eng.step(5, 2.0)  # graph replays
     eng.close()
+
+
+def test_four_lanes_per_atom_give_bitwise_the_same_results(tb):
+    """The pair passes with four threads per atom (each evaluating one entry
+    of every group of four, the terms added in list order through shuffles)
+    give bitwise the forces, energies and virials of one thread per atom, on
+    a jittered tiny batch in both launch shapes, and the same trajectory."""
+    from inputs import jitter
+
+    b = workload("tiny_batch")
+    b.x = jitter(b.x, 0.06, 41)
+    out = []
+    for lanes in (1, 4):
+        eng = tb.Engine(b, precision="mixed")
+        eng.set_step_mode("graph")
+        eng.set_pair_lanes(lanes)
+        F32, _ = eng.forces(f32=True, f64=False)
+        e, w = eng.atom_energies()
+        eng.init_velocities()
+        eng.step(120, 2.0)
+        out.append((F32.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy(), eng.positions()))
+        eng.close()
+    for a, c in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, c)
