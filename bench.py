@@ -431,10 +431,10 @@ FORCE_IMPL_MODEL = {"fp32_in": 21, "fp32_skin": 7, "mufu_in": 3, "bytes_out": 12
 # MUFU 1; skin entries as above.
 EAM_MODEL = {"fp32_in": 25, "fp32_skin": 7, "mufu_in": 1, "bytes_out": 12}
 # DRAM bytes (read + write) per atom of one force-pass launch from an ncu
-# capture of the current kernel on a smaller case of the same workload,
-# scaled by the atom count (the traffic is per atom); None until the
-# current kernel has been captured.
-FORCE_TRAFFIC_B_PER_ATOM = None
+# capture of the current kernel on a smaller case of the same workload
+# (sweep144: 528.27 MB read + 42.81 MB written for 3,971,388 atoms), scaled
+# by the atom count (the traffic is per atom); None once the kernel changes.
+FORCE_TRAFFIC_B_PER_ATOM = 143.8
 
 
 def au_eam_tables(d_r=0.002, d_rho=0.005, rho_max=120.0, r_cut=5.8):
@@ -505,9 +505,10 @@ def roofline_of(N, n_c, n_s, ms, sms, mhz, hbm_gbs, model=PASS_MODEL["force"]):
     return bound
 
 
-def pass_rooflines(eng, ms_force, ms_density, clocks, eam=False):
+def pass_rooflines(eng, ms_force, ms_density, clocks, eam=False, captured=True):
     """The force pass's roofline (the dominant kernel), with the density
-    pass's beside it."""
+    pass's beside it.  `captured`: the force kernel runs in the launch shape
+    and lane count its DRAM traffic was captured with."""
     import torch
 
     n_c, n_s = _list_census(eng)
@@ -516,7 +517,8 @@ def pass_rooflines(eng, ms_force, ms_density, clocks, eam=False):
     sms, mhz = props.multi_processor_count, clocks.get("sm_mhz") or 2032.0
     force_model = EAM_MODEL if eam else PASS_MODEL["force"]
     bound = roofline_of(eng.N, n_c, n_s, ms_force, sms, mhz, hbm, model=force_model)
-    traffic = None if (eam or FORCE_TRAFFIC_B_PER_ATOM is None) else FORCE_TRAFFIC_B_PER_ATOM * eng.N
+    traffic = (None if (eam or not captured or FORCE_TRAFFIC_B_PER_ATOM is None)
+               else FORCE_TRAFFIC_B_PER_ATOM * eng.N)
     bound.update({
         "kernel": "k_force_f32<EAM>" if eam else "k_force_f32",
         "model": ("EAM: 25 FP32 + 1 MUFU per in-cutoff entry, 7 FP32 per skin entry" if eam else
@@ -667,7 +669,9 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    roof = pass_rooflines(eng, res[2], res[1], ck, eam=eam) if args.precision == "mixed" else None
+    captured = tuple(launch) == LAUNCH and args.lanes == 1 and args.workload in ("sweep2048", "sweep144")
+    roof = (pass_rooflines(eng, res[2], res[1], ck, eam=eam, captured=captured)
+            if args.precision == "mixed" else None)
     cfg = {"workload": args.workload, "atoms_per_gpu": N, "dt_fs": 2.0}
     cfg.update(workload_config(specs))
     cfg.update({"precision": args.precision,

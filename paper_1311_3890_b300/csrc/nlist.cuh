@@ -30,6 +30,9 @@ struct NlWork {
   float2* xenv;         // [N] along the atom order: prefix max and suffix min of x (envelopes)
   float2* tenv;         // [NS / kSlotTile] per tile: max and min of x (envelopes)
   uint32_t* wdis;       // [W] disorder of the atom order along x, A (FP32 bits; envelopes)
+  float4* xf;           // [3 NS / 4] slab-build candidates: per group of four slots, x, y, z
+                        // (four FP32 coordinates relative to the wire's origin each)
+  int64_t N;            // atoms (the stride of the position planes)
   int slab_ok;          // the context may use the slab build (MIXED)
   float max_disorder;   // largest disorder for which a wire takes the slab build, A
   int32_t* n_flagged;   // [1]
@@ -460,6 +463,15 @@ __global__ void __launch_bounds__(256)
 // the flagged wires' tiles, each fully parallel: k_nl_env_tiles scans each
 // tile alone, k_nl_env_merge folds in the extrema of the wire's other tiles.
 constexpr float kSlabGuard = 0.01f;  // A added to the list radius for the FP32 envelope
+// The slab build tests candidates on FP32 coordinates relative to the
+// wire's origin.  Within kSlabMaxCoord of it a coordinate is off by at most
+// half an ulp of 2048 A (1.2e-4 A), a coordinate difference by 2.4e-4 A and
+// a distance by 4.3e-4 A: inside the 1e-3 A guard the list radius carries,
+// so no pair that can reach r_cut before the next rebuild is dropped.  Wires
+// reaching farther (410 nm) take the cell build (exact fixed-point
+// differences).
+constexpr float kSlabMaxCoord = 2048.f;
+constexpr float kSlabFar = 1e30f;  // padding slots' x: d^2 overflows to +inf, never accepted
 
 // Block-wide inclusive max-scan from the left and min-scan from the right of
 // (mx, mn) over the kSlotTile threads, and the block's max and min.
@@ -503,8 +515,21 @@ __device__ __forceinline__ void nl_env_tiles_body(NlWork nw, const WireDev* __re
     const int kt = (int)(tl - nw.wl_tile[k]);  // tile of the wire
     const int a = kt * kSlotTile + threadIdx.x;
     const bool valid = a < w.n;
-    const float v = valid ? (float)(x[w.offset + a] - w.origin[0]) : 0.f;
-    float mx = valid ? v : -INFINITY, mn = valid ? v : INFINITY, bmx, bmn;
+    const int64_t i = w.offset + a;
+    const float v = valid ? (float)(x[i] - w.origin[0]) : 0.f;
+    const float vy = valid ? (float)(x[nw.N + i] - w.origin[1]) : 0.f;
+    const float vz = valid ? (float)(x[2 * nw.N + i] - w.origin[2]) : 0.f;
+    // the slab build's candidate coordinates (padding slots: far away, never
+    // accepted); an atom beyond kSlabMaxCoord of the origin (or not finite)
+    // gives its wire an infinite disorder, hence the cell build
+    float* xf = reinterpret_cast<float*>(nw.xf + 3 * ((w.slot_base + a) >> 2)) + (a & 3);
+    xf[0] = valid ? v : kSlabFar;
+    xf[4] = vy;
+    xf[8] = vz;
+    const bool far =
+        valid && !(fabsf(v) <= kSlabMaxCoord && fabsf(vy) <= kSlabMaxCoord && fabsf(vz) <= kSlabMaxCoord);
+    float mx = valid ? (far ? INFINITY : v) : -INFINITY, mn = valid ? (far ? -INFINITY : v) : INFINITY;
+    float bmx, bmn;
     tile_scans(mx, mn, bmx, bmn);
     if (valid) nw.xenv[w.offset + a] = make_float2(mx, mn);
     if (threadIdx.x == 0) {
@@ -622,8 +647,10 @@ __device__ __forceinline__ int slab_hi(const float2* env, int bot, int n, float 
 // atoms, one atom per lane.  The warp bounds its candidates by the envelopes
 // (slab_lo, slab_hi) and walks them in index order with broadcast loads
 // (every lane reads the same candidate), each lane testing it against its
-// own atom with the cell build's distance test (build_d2 against the same
-// r_list^2, so the two builds accept the same pairs).  The test is
+// own atom: d^2 <= r_list^2 on the FP32 coordinates k_nl_env_tiles stored
+// (relative to the wire's origin; the cell build takes exact fixed-point
+// differences instead, and the two can disagree only on pairs within
+// 4.3e-4 A of r_list, inside its 1e-3 A guard).  The test is
 // branch-free: each lane collects the outcomes of 32 consecutive candidates
 // as the bits of a mask, then appends the set bits to its column of a
 // shared-memory buffer as offsets j - i; the atom itself (offset 0, d2 = 0)
@@ -640,8 +667,8 @@ __device__ __forceinline__ int slab_hi(const float2* env, int bot, int n, float 
 // cap + kSlabSlack entries per lane (cap neighbours and the atom itself).
 constexpr int kSlabSlack = 1;
 __device__ __forceinline__ void nl_build_slab_body(
-    NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-    const int32_t* __restrict__ slot_of, float rlist2u, float xrange, int16_t* __restrict__ nbr,
+    NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ slot_of, float rlist2,
+    float xrange, int16_t* __restrict__ nbr,
     int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange, const int4* __restrict__ xq,
     int4* __restrict__ xq_b, uint32_t* wire_status) {
   extern __shared__ int16_t sA[];  // [cap + kSlabSlack][blockDim.x]: offsets, ascending, by column
@@ -664,9 +691,13 @@ __device__ __forceinline__ void nl_build_slab_body(
     const int64_t i = w.offset + (valid ? a : g0);
     const int ii = (int)i;
     const float2* env = nw.xenv + w.offset;
+    // the atom's FP32 coordinates, as its candidates carry them
+    const float4* G = nw.xf + 3 * (w.slot_base >> 2);  // the wire's groups of four slots
+    const int ai = valid ? a : g0;
+    const float* own = reinterpret_cast<const float*>(G + 3 * (ai >> 2)) + (ai & 3);
+    const float px = own[0], py = own[4], pz = own[8];
     // the group's extent along the axis, then its candidate range
-    const float xf = (float)(x[i] - w.origin[0]);
-    float xmin = valid ? xf : INFINITY, xmax = valid ? xf : -INFINITY;
+    float xmin = valid ? px : INFINITY, xmax = valid ? px : -INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
@@ -675,18 +706,20 @@ __device__ __forceinline__ void nl_build_slab_body(
     const int glast = min(g0 + 31, n - 1);
     const int lo = slab_lo(env, g0, xmin - xrange);
     int hi = slab_hi(env, glast, n, xmax + xrange);
-    if (hi - lo > kMaxOffset) {  // offsets would not fit the int16 entries
+    if (hi - lo > kMaxOffset - 3) {  // offsets would not fit the int16 entries
       if (lane == 0) atomicOr(&wire_status[wi], kWireNbrOverflow);
-      hi = lo + kMaxOffset;
+      hi = lo + kMaxOffset - 3;
     }
-    // candidates j in [lo, hi], four at a time, every lane reading the same ones
     const int4 pi = xq[i];
-    // every lane tests every candidate, 32 at a time into an acceptance mask
-    // (bit u: candidate j0 + u), whose set bits are then appended to the
-    // lane's column as offsets j - i: rows 0..cap hold the first cap + 1
-    // accepted entries (cap neighbours and the atom itself)
+    // every lane tests every candidate j in [lo, hi] (widened to whole groups
+    // of four: the extra ones lie beyond the slab and fail the test), 32 at a
+    // time into an acceptance mask (bit u: candidate j0 + u), whose set bits
+    // are then appended to the lane's column as offsets j - i: rows 0..cap
+    // hold the first cap + 1 accepted entries (cap neighbours and the atom
+    // itself).  A group is three broadcast 16-byte loads (x, y, z of four
+    // candidates), its differences and squared distances two FP32 pairs per
+    // instruction.
     int n_all = 0;
-    const int jlo = (int)w.offset + lo, jhi = (int)w.offset + hi;
     auto flush = [&](uint32_t m, int off0) {
       while (m) {
         const int b = __ffs(m) - 1;
@@ -695,24 +728,31 @@ __device__ __forceinline__ void nl_build_slab_body(
         ++n_all;
       }
     };
-    for (int j0 = jlo; j0 <= jhi; j0 += 32) {
+    const float2 nx = make_float2(-px, -px), ny = make_float2(-py, -py), nz = make_float2(-pz, -pz);
+    auto test4 = [&](const float4* q, uint32_t bit, uint32_t& m) {
+      const float4 X = __ldg(q), Y = __ldg(q + 1), Z = __ldg(q + 2);
+      const float2 dx0 = __fadd2_rn(make_float2(X.x, X.y), nx), dx1 = __fadd2_rn(make_float2(X.z, X.w), nx);
+      const float2 dy0 = __fadd2_rn(make_float2(Y.x, Y.y), ny), dy1 = __fadd2_rn(make_float2(Y.z, Y.w), ny);
+      const float2 dz0 = __fadd2_rn(make_float2(Z.x, Z.y), nz), dz1 = __fadd2_rn(make_float2(Z.z, Z.w), nz);
+      const float2 d0 = __ffma2_rn(dz0, dz0, __ffma2_rn(dy0, dy0, __fmul2_rn(dx0, dx0)));
+      const float2 d1 = __ffma2_rn(dz1, dz1, __ffma2_rn(dy1, dy1, __fmul2_rn(dx1, dx1)));
+      if (d0.x <= rlist2) m |= bit;
+      if (d0.y <= rlist2) m |= bit << 1;
+      if (d1.x <= rlist2) m |= bit << 2;
+      if (d1.y <= rlist2) m |= bit << 3;
+    };
+    const int alo = lo & ~3, ahi = hi | 3;
+    for (int j0 = alo; j0 <= ahi; j0 += 32) {
       uint32_t m = 0;
-      const int cnt32 = min(32, jhi - j0 + 1);
-      if (cnt32 == 32) {
+      const float4* q = G + 3 * (j0 >> 2);
+      const int ng = min(8, (ahi - j0 + 1) >> 2);  // groups in this batch of 32
+      if (ng == 8) {
 #pragma unroll
-        for (int u = 0; u < 32; u += 4) {
-          const int4 q0 = __ldg(xq + j0 + u), q1 = __ldg(xq + j0 + u + 1),
-                     q2 = __ldg(xq + j0 + u + 2), q3 = __ldg(xq + j0 + u + 3);
-          if (build_d2(pi, q0) <= rlist2u) m |= 1u << u;
-          if (build_d2(pi, q1) <= rlist2u) m |= 2u << u;
-          if (build_d2(pi, q2) <= rlist2u) m |= 4u << u;
-          if (build_d2(pi, q3) <= rlist2u) m |= 8u << u;
-        }
+        for (int g = 0; g < 8; ++g) test4(q + 3 * g, 1u << (4 * g), m);
       } else {
-        for (int u = 0; u < cnt32; ++u)
-          if (build_d2(pi, __ldg(xq + j0 + u)) <= rlist2u) m |= 1u << u;
+        for (int g = 0; g < ng; ++g) test4(q + 3 * g, 1u << (4 * g), m);
       }
-      flush(m, j0 - ii);
+      flush(m, (int)w.offset + j0 - ii);
     }
     if (!valid) continue;
     const bool ovf = n_all > cap + 1;
@@ -780,12 +820,11 @@ __device__ __forceinline__ void nl_build_slab_body(
   }
 }
 __global__ void __launch_bounds__(256)
-    k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const double* __restrict__ x,
-                    const int32_t* __restrict__ slot_of, float rlist2u, float xrange,
-                    int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap,
-                    int2* __restrict__ jrange, const int4* __restrict__ xq, int4* __restrict__ xq_b,
-                    uint32_t* wire_status) {
-  nl_build_slab_body(nw, wd, x, slot_of, rlist2u, xrange, nbr, n_nbr, cap, jrange, xq, xq_b,
+    k_nl_build_slab(NlWork nw, const WireDev* __restrict__ wd, const int32_t* __restrict__ slot_of,
+                    float rlist2, float xrange, int16_t* __restrict__ nbr,
+                    int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
+                    const int4* __restrict__ xq, int4* __restrict__ xq_b, uint32_t* wire_status) {
+  nl_build_slab_body(nw, wd, slot_of, rlist2, xrange, nbr, n_nbr, cap, jrange, xq, xq_b,
                      wire_status);
 }
 

@@ -93,7 +93,7 @@ struct PersistArgs {
   int32_t* cell_atoms;
   int32_t* cell_of;
   const int32_t* slot_of;
-  float rlist2u, slab_range;
+  float rlist2u, rlist2, slab_range;  // list radius^2 in fixed-point units^2 and in A^2
   int16_t* nbr;
   int32_t* n_nbr;
   int cap;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
       if (!grid_sync(a.bar)) return;
       nl_build_body<int4>(a.nw, a.wd, a.cell_count, a.cell_atoms, a.cell_of, a.slot_of, a.rlist2u,
                           a.nbr, a.n_nbr, a.cap, a.jrange, a.xq, a.xq_b, a.wire_status);
-      nl_build_slab_body(a.nw, a.wd, a.x, a.slot_of, a.rlist2u, a.slab_range, a.nbr, a.n_nbr, a.cap,
+      nl_build_slab_body(a.nw, a.wd, a.slot_of, a.rlist2, a.slab_range, a.nbr, a.n_nbr, a.cap,
                          a.jrange, a.xq, a.xq_b, a.wire_status);
       if (!grid_sync(a.bar)) return;
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -112,6 +112,7 @@ struct tbsma_ctx {
   float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (slab-build envelopes)
   float2* tenv = nullptr;      // per tile: max / min of x (slab-build envelopes)
   uint32_t* wdis = nullptr;    // per wire: disorder of the atom order along x (FP32 bits)
+  float4* xf = nullptr;        // per group of four slots: FP32 x, y, z (slab-build candidates)
   int32_t* n_flagged = nullptr;
   int32_t* n_rebuilds = nullptr;
   int64_t* chains = nullptr;  // launches of the rebuild chain (launch accounting)
@@ -164,6 +165,8 @@ struct tbsma_ctx {
     w.xenv = xenv;
     w.tenv = tenv;
     w.wdis = wdis;
+    w.xf = xf;
+    w.N = N;
     w.slab_ok = prec == TBSMA_MIXED ? 1 : 0;
     w.max_disorder = kSlabDisorder;
     w.n_flagged = n_flagged;
@@ -335,7 +338,7 @@ tbsma_status launch_rebuild(tbsma_ctx* c, cudaStream_t s) {
                                            c->xq, c->xq_b, c->wire_status);
     const size_t sslab = (size_t)256 * ((c->cap + kSlabSlack) * sizeof(int16_t) + c->cap * sizeof(uint8_t));
     k_nl_build_slab<<<(unsigned)(c->sm_count * 3), 256, sslab, s>>>(
-        c->nw(), c->wd, c->x, c->slot_of, c->rlist2u, c->slab_range, c->nbr, c->n_nbr, c->cap,
+        c->nw(), c->wd, c->slot_of, c->rlist2, c->slab_range, c->nbr, c->n_nbr, c->cap,
         c->jrange, c->xq, c->xq_b, c->wire_status);
   } else {
     k_nl_build<double4_32a><<<gb, 256, sbuf, s>>>(c->nw(), c->wd, c->cell_count, c->cell_atoms,
@@ -696,6 +699,7 @@ tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double 
   a.cell_of = c->cell_of;
   a.slot_of = c->slot_of;
   a.rlist2u = c->rlist2u;
+  a.rlist2 = c->rlist2;
   a.slab_range = c->slab_range;
   a.nbr = c->nbr;
   a.n_nbr = c->n_nbr;
@@ -1104,6 +1108,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->xenv, N);
   ALLOC(c->tenv, (size_t)(NS / kSlotTile));
   ALLOC(c->wdis, W);
+  if (c->prec == TBSMA_MIXED) ALLOC(c->xf, (size_t)(NS / 4) * 3);  // slab-build candidates
   ALLOC(c->n_flagged, 1);
   ALLOC(c->n_rebuilds, W);
   ALLOC(c->chains, 1);

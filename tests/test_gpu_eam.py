@@ -181,6 +181,43 @@ def test_eam_md_matches_oracle_short_horizon(tb, orc, prec, xtol, vtol):
     eng.close()
 
 
+@pytest.mark.parametrize("prec,xtol,vtol", [("fp64", 1e-9, 1e-11), ("mixed", 2e-5, 2e-6)])
+def test_eam_langevin_pull_matches_oracle(tb, orc, prec, xtol, vtol):
+    """200 steps of the tiny batch on the EAM with the default protocol on:
+    Langevin at 10 and 298 K (Philox normals drawn per atom and step) and
+    the grips pulled at 1e9 1/s, against the oracle's BAOAB on its EAM
+    (same seeds, same draws).  Positions, velocities, strain, potential
+    energy, temperature and stress, as for TB-SMA."""
+    T = tbsma_sampled()
+    pot = orc.EamPotential(orc.EamTables(**T))
+    b = workload("tiny_batch")
+    eng = tb.Engine(b, precision=prec)
+    eng.set_eam(**T)
+    eng.init_velocities()
+    v0 = eng.velocities()
+    eng.step(200, 2.0)
+    x, v = eng.positions(), eng.velocities()
+    ob = eng.observables()
+    for w in range(b.n_wires):
+        s = b.wire_slice(w)
+        st = orc.WireState(x=b.x[s].copy(), v=v0[s].copy(), kind=b.kind[s], L0=float(b.L0[w]),
+                           strain_rate=float(b.strain_rate[w]),
+                           temperature=float(b.temperature[w]), gamma=float(b.gamma[w]),
+                           seed=int(b.seed[w]))
+        orc.md_steps(st, 200, 2.0, pot=pot, brute_max=3000)
+        assert np.max(np.abs(x[s] - st.x)) < xtol
+        assert np.max(np.abs(v[s] - st.v)) < vtol
+        o = orc.observables(st, pot=pot, brute_max=3000)
+        assert o.strain > 0.0
+        assert ob["strain"][w] == pytest.approx(o.strain, rel=1e-12)
+        assert ob["e_pot"][w] == pytest.approx(o.e_pot, rel=1e-8 if prec == "fp64" else 1e-6)
+        assert ob["temp"][w] == pytest.approx(o.temp, rel=1e-6 if prec == "fp64" else 1e-3)
+        assert ob["sigma_xx"][w] == pytest.approx(o.sigma_xx, rel=1e-5, abs=1e-7)
+        assert ob["n_rebuilds"][w] == st.n_rebuild
+    assert ob["temp"][1] > 50.0  # the 298 K wire was thermalised by the draws
+    eng.close()
+
+
 def test_set_eam_rejects_bad_tables(tb):
     T = synthetic()
     eng = tb.Engine(workload("tiny_batch"), precision="mixed")
