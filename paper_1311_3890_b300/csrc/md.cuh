@@ -338,7 +338,7 @@ __device__ __forceinline__ float narrow(double d) {
 template <int KICK, bool PROTO>
 __device__ __forceinline__ void integrate_mixed_atom(
     int64_t i, long long step, int64_t N, double* __restrict__ x, double* __restrict__ v,
-    const float* __restrict__ f32, const uint32_t* __restrict__ meta,
+    float3 F, const uint32_t* __restrict__ meta,
     const WireDev* __restrict__ wd, const WireDyn* __restrict__ wdyn, float hk, float hd,
     int4* __restrict__ xq, const int4* __restrict__ xq_b, float half_skin2, int32_t* flag,
     int32_t* any_flag, uint32_t* wire_status, double* d_grip, const ProtoDev& proto,
@@ -360,7 +360,7 @@ __device__ __forceinline__ void integrate_mixed_atom(
       // Nosé–Hoover: v' = s (v + a) + b with a the closing half kick (KICK = 2)
       // and b the opening one; increments (s - 1)(v + a) + a + b in FP32,
       // drift dt v'.  hk is the half kick here.
-      const float bx = hk * f32[i], by = hk * f32[N + i], bz = hk * f32[2 * N + i];
+      const float bx = hk * F.x, by = hk * F.y, bz = hk * F.z;
       const float ax = KICK == 2 ? bx : 0.f, ay = KICK == 2 ? by : 0.f, az = KICK == 2 ? bz : 0.f;
       const float sm1 = nh[wi].sm1f;
       const float cx = narrow(vx) + ax, cy = narrow(vy) + ay, cz = narrow(vz) + az;
@@ -376,7 +376,7 @@ __device__ __forceinline__ void integrate_mixed_atom(
       float c2sig = wdyn[wi].c2sigf;
       if (PROTO && proto.ramp > 0 && w.temperature > 0.0)
         c2sig *= sqrtf((float)(target_temperature(proto, w.temperature, step) / w.temperature));
-      const float dvx = hk * f32[i], dvy = hk * f32[N + i], dvz = hk * f32[2 * N + i];
+      const float dvx = hk * F.x, dvy = hk * F.y, dvz = hk * F.z;
       const float v1x = narrow(vx) + dvx, v1y = narrow(vy) + dvy, v1z = narrow(vz) + dvz;
       float Dx = 0.f, Dy = 0.f, Dz = 0.f;
       if (c2sig != 0.f) {
@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(256, 6)
                       const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  integrate_mixed_atom<KICK, PROTO>(i, step_counter[0], N, x, v, f32, meta, wd, wdyn, hk, hd, xq,
+  integrate_mixed_atom<KICK, PROTO>(i, step_counter[0], N, x, v,
+                                    make_float3(f32[i], f32[N + i], f32[2 * N + i]), meta, wd, wdyn,
+                                    hk, hd, xq,
                                     xq_b, half_skin2, flag, nullptr, wire_status, d_grip, proto, nh,
                                     baro);
 }
@@ -598,6 +600,17 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) baro[w] = b;
     __syncthreads();
   }
+}
+
+// Closing half kick of the last step of a sequence, MIXED, with the atom's
+// FP32 force at hand.
+__device__ __forceinline__ void half_kick_atom_f(int64_t i, int64_t N, double* __restrict__ v,
+                                                 float3 F, const uint32_t* __restrict__ meta,
+                                                 double hk) {
+  if (meta_kind(meta[i]) != 0) return;
+  v[i] += hk * (double)F.x;
+  v[N + i] += hk * (double)F.y;
+  v[2 * N + i] += hk * (double)F.z;
 }
 
 // Closing half kick of the last step of a sequence.

@@ -719,12 +719,22 @@ __device__ __forceinline__ void nl_build_slab_body(
     // itself).  A group is three broadcast 16-byte loads (x, y, z of four
     // candidates), its differences and squared distances two FP32 pairs per
     // instruction.
-    int n_all = 0;
+    // Also counted on the way: the accepted entries before the atom's own
+    // (negative offsets: the own entry's index), and the stored entries per
+    // bank group (eight byte counters; the own entry excluded).
+    const int il = (int)(i - w.offset);
+    int n_all = 0, n_neg = 0;
+    uint64_t T = 0;
     auto flush = [&](uint32_t m, int off0) {
+      n_neg += __popc(off0 >= 0 ? 0u : off0 <= -32 ? m : m & ((1u << -off0) - 1u));
       while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        if (n_all <= cap) sA[n_all * B + tid] = (int16_t)(off0 + b);
+        const int off = off0 + b;
+        if (n_all <= cap) {
+          sA[n_all * B + tid] = (int16_t)off;
+          if (off != 0) T += 1ull << (8 * ((il + off) & 7));
+        }
         ++n_all;
       }
     };
@@ -758,21 +768,19 @@ __device__ __forceinline__ void nl_build_slab_body(
     const bool ovf = n_all > cap + 1;
     n_all = min(n_all, cap + 1);  // accepted and stored, the atom itself included (if it fit)
     // drop the atom itself: offsets ascend, so it follows the negative ones
-    int self = n_all;
-    for (int e = 0; e < n_all; ++e)
-      if (sA[e * B + tid] == 0) {
-        self = e;
-        break;
-      }
+    // (its index is n_neg; n_all when it was not stored)
+    const int self = min(n_neg, n_all);
     const int cnt = n_all - (self < n_all ? 1 : 0);
     if (ovf || cnt > cap) atomicOr(&wire_status[wi], kWireNbrOverflow);
     const int nr = min(cnt, cap);
     auto entry = [&](int e) { return sA[(e < self ? e : e + 1) * B + tid]; };  // e-th without self
-    const int il = (int)(i - w.offset);
     auto group = [&](int e) { return (il + entry(e)) & 7; };
-    // bucket the entries by group (ascending within a group)
-    uint64_t T = 0;
-    for (int e = 0; e < nr; ++e) T += 1ull << (8 * group(e));
+    // bucket the entries by group (ascending within a group); the counts
+    // came with the scan unless the row overflowed (then only nr of them)
+    if (cnt > nr) {
+      T = 0;
+      for (int e = 0; e < nr; ++e) T += 1ull << (8 * group(e));
+    }
     const uint64_t S = T * 0x0101010101010101ull - T;  // exclusive prefix of the 8 counts
     uint64_t P = S;
     for (int e = 0; e < nr; ++e) {

@@ -109,6 +109,7 @@ struct tbsma_ctx {
   int64_t* wl_cell = nullptr;
   int64_t* wl_atom = nullptr;
   int64_t* wl_tile = nullptr;
+  int4* xq2 = nullptr;         // second position buffer of the persistent step kernel
   float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (slab-build envelopes)
   float2* tenv = nullptr;      // per tile: max / min of x (slab-build envelopes)
   uint32_t* wdis = nullptr;    // per wire: disorder of the atom order along x (FP32 bits)
@@ -633,9 +634,10 @@ tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
 
 // ------------------------------------------------ persistent step kernel
 // Dynamic shared memory of the persistent step kernel: the largest of the
-// pair passes' window and the two builds' buffers.
+// pair passes' window with the tile cache and the two builds' buffers.
 size_t persist_smem(const tbsma_ctx* c) {
-  const size_t window = (size_t)c->wcap * sizeof(int4);
+  const int slots = 256 / (c->lanes == 4 ? 4 : 1);
+  const size_t window = (size_t)c->wcap * sizeof(int4) + tile_cache_bytes(c->cap, slots);
   const size_t cell = (size_t)256 * c->cap * sizeof(int16_t);
   const size_t slab = (size_t)256 * ((c->cap + kSlabSlack) * sizeof(int16_t) + c->cap);
   return std::max(window, std::max(cell, slab));
@@ -671,6 +673,7 @@ int persist_blocks(tbsma_ctx* c) {
 // caller has checked persist_blocks > 0 and set dt).  Same steps, kicks and
 // step counts as enqueue_steps.
 tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double dt) {
+  if (!c->xq2) TB_TRY(alloc(c, &c->xq2, (size_t)c->N));  // the kernel's second position buffer
   PersistArgs a;
   a.N = c->N;
   a.NS = c->NS;
@@ -686,6 +689,7 @@ tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double 
   a.hd = (float)(0.5 * dt);
   a.hk_close = 0.5 * dt * c->inv_m;
   a.xq = c->xq;
+  a.xq2 = c->xq2;
   a.xq_b = c->xq_b;
   a.half_skin2 = (float)c->half_skin2;
   a.flag = c->flag;
@@ -1015,7 +1019,14 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       cudaFuncSetAttribute(k_nl_build<double4_32a>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_nl_build_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, slab_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
-  const int persist_max = std::max(std::max(smem_max, sbuf_max), slab_max);
+  // the persistent kernel: the largest window with its tile cache, or a
+  // build's buffers, up to what a block may opt in to (a context whose
+  // shape needs more runs graph replays: persist_blocks finds no room)
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return bail(TBSMA_ECUDA);
+  const int persist_max = std::min(
+      optin, std::max(std::max(smem_max + (int)tile_cache_bytes(kMaxCap, 256), sbuf_max), slab_max));
   if (cudaFuncSetAttribute(k_steps_persistent<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
