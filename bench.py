@@ -773,9 +773,10 @@ TABLE2_298K = [2286, 1507, 1141, 897, 717, 616, 550, 484, 409, 354, 330, 300]
 
 def run_table2(args):
     """Each Table 2 wire alone in its own mixed-precision context (as the
-    paper ran one system per GPU), 64-atom tiles to spread a small wire over
-    the SMs, the library default list skin: steps/s over the timed steps
-    after the warm-up, at 10 K and at 298 K.  Context only, one JSON line."""
+    paper ran one system per GPU), in the default step mode (the persistent
+    step kernel where the wire's tiles fit the GPU at once, which all twelve
+    do), the library default list skin: steps/s over the timed steps after
+    the warm-up, at 10 K and at 298 K.  Context only, one JSON line."""
     import torch
 
     from inputs.configs import WireSpec, build
@@ -789,7 +790,7 @@ def run_table2(args):
         for T in (10.0, 298.0):
             batch = build([WireSpec(3.1, 20.4 * k, T, 0.0, k)])
             eng = tb.Engine(batch, precision="mixed")
-            eng.set_launch(64, 1280)
+            row[f"persistent_blocks_{int(T)}K"] = eng.set_step_mode("auto")
             eng.init_velocities()
             eng.step(warm, 2.0)
             eng.step(min(50, steps), 2.0)  # capture the graph outside the timed region

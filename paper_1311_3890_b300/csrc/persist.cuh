@@ -31,12 +31,14 @@ namespace tbsma {
 
 // State of the grid barrier (device memory, zeroed before each launch):
 // the arrival count and the error word.  The count only grows within a
-// launch: the k-th barrier is passed once it reaches k * gridDim.x, so an
-// arrival is one fire-and-forget add and a wait is a poll of one word (no
-// reset by the last block, no second word to flip).
+// launch: the k-th barrier is passed once its low word reaches
+// k * gridDim.x, so an arrival is one atomic add and a wait is a poll of one
+// word (no reset by the last block, no second word to flip).  Its high word
+// counts the arrivals of blocks that flagged a list rebuild, so the barrier
+// after an integrate also tells every block whether any atom crossed half
+// the skin (no separate flag word to read after it).
 struct GridBarrier {
-  unsigned* count;
-  unsigned* gen;  // unused (kept zero)
+  unsigned long long* count;
   unsigned* err;
   unsigned limit;  // polls before giving up
 };
@@ -44,24 +46,37 @@ struct GridBarrier {
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
 
 // Polls a wait spins before it starts to sleep between polls.
 constexpr unsigned kSpinPolls = 256;
 
 // All blocks of the grid meet here; `target` is the block's running count of
 // arrivals expected so far (advanced by gridDim.x per barrier, starting at
-// 0).  Returns false when the barrier gave up (this block's wait ran out, or
+// 0).  `flag` (shared memory, or null): set by any thread of the block that
+// flagged a rebuild since the last barrier; it is read and cleared here, and
+// `flagged` receives the launch's running count of flagging arrivals.
+// Returns false when the barrier gave up (this block's wait ran out, or
 // another block's did and set the error word): the caller leaves.
-__device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& target) {
-  __shared__ unsigned s_ok;
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& target,
+                                          int32_t* flag = nullptr, unsigned* flagged = nullptr) {
+  __shared__ unsigned s_ok, s_flagged;
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
     unsigned ok = 1;
+    unsigned long long add = 1;
+    if (flag && *flag) {
+      add += 1ull << 32;
+      *flag = 0;
+    }
     __threadfence();  // the block's writes (ordered by the block barrier) before the arrival
-    atomicAdd(b.count, 1u);
+    atomicAdd(b.count, add);
     unsigned polls = 0;
-    while ((int)(ld_volatile(b.count) - target) < 0) {
+    unsigned long long c;
+    while ((int)((unsigned)(c = ld_volatile(b.count)) - target) < 0) {
       if (polls++ >= b.limit || ld_volatile(b.err)) {
         atomicOr(b.err, 1u);
         ok = 0;
@@ -71,8 +86,10 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& target
     }
     __threadfence();  // the other blocks' writes before this block's next reads
     s_ok = ok;
+    s_flagged = (unsigned)(c >> 32);
   }
   __syncthreads();
+  if (flagged) *flagged = s_flagged;
   return s_ok != 0;
 }
 
@@ -93,7 +110,6 @@ struct PersistArgs {
   int4* xq_b;
   float half_skin2;
   int32_t* flag;
-  int32_t* any_flag;  // [2]: some wire flagged in a step of this parity
   uint32_t* wire_status;
   double* d_grip;
   int64_t* step_counter;
@@ -180,6 +196,10 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
     tile_cache_fill<LANES>(blockIdx.x, a.nbr, a.n_nbr, a.perm, a.jrange, a.cap, a.wcap);
   const ProtoDev proto{};
   unsigned bt = 0;  // barrier target
+  __shared__ int32_t s_any;  // some atom of this block flagged a rebuild since the last barrier
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  unsigned flagged = 0, flagged_before = 0;  // flagging arrivals so far, and at the last step
   // The positions of step k go to one of two buffers, the last step's to
   // a.xq (the context's) and earlier ones alternately to a.xq2 and a.xq: an
   // atom's next step is integrated while other blocks may still read this
@@ -190,16 +210,16 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
   for (int64_t i = gtid; i < a.N; i += nthreads)
     integrate_mixed_atom<1, false>(
         i, a.step0, a.N, a.x, a.v, make_float3(a.f32[i], a.f32[a.N + i], a.f32[2 * a.N + i]),
-        a.meta, a.wd, a.wdyn, a.hk_open, a.hd, xq_of(0), a.xq_b, a.half_skin2, a.flag,
-        a.any_flag + (a.step0 & 1), a.wire_status, a.d_grip, proto, nullptr, nullptr);
-  if (!grid_sync(a.bar, bt)) return;
+        a.meta, a.wd, a.wdyn, a.hk_open, a.hd, xq_of(0), a.xq_b, a.half_skin2, a.flag, &s_any,
+        a.wire_status, a.d_grip, proto, nullptr, nullptr);
+  if (!grid_sync(a.bar, bt, &s_any, &flagged)) return;
   for (int k = 0; k < a.n_steps; ++k) {
     const long long step = a.step0 + k;
     int4* xq = xq_of(k);
-    // list rebuild of the flagged wires (every block sees the same flag word:
-    // it was written before the barrier and is cleared only a step later)
-    const bool rebuild = ld_volatile(reinterpret_cast<const unsigned*>(a.any_flag + (step & 1))) != 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.any_flag[(step + 1) & 1] = 0;
+    // list rebuild of the flagged wires (every block read the same count of
+    // flagging arrivals at the barrier after this step's integrate)
+    const bool rebuild = flagged != flagged_before;
+    flagged_before = flagged;
     if (rebuild) {
       if (blockIdx.x == 0) nl_plan_body(a.W, a.nw, a.wd, 0, 1, nullptr, step);
       if (!grid_sync(a.bar, bt)) return;
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
     const bool close = (k + 1) % a.seq == 0 || k + 1 == a.n_steps;
     const bool more = k + 1 < a.n_steps;
     int4* xq_next = xq_of(k + 1);
-    int32_t* any_next = a.any_flag + ((step + 1) & 1);
+    int32_t* any_next = &s_any;
     const StepEpilogue epi{a.N,     a.x,          a.v,         a.meta,  a.wd,     a.wdyn,
                            a.hk_open, a.hk_full,  a.hd,        a.hk_close, a.xq_b, a.half_skin2,
                            a.flag,  a.wire_status, a.d_grip,   step + 1, close,    more,
@@ -259,13 +279,9 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
                                           a.wcap, a.pc, a.f32, a.f32 + a.N, a.f32 + 2 * a.N, nullptr,
                                           nullptr, nullptr, nullptr, a.eam, epi);
     }
-    if (!grid_sync(a.bar, bt)) return;
+    if (!grid_sync(a.bar, bt, &s_any, &flagged)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.step_counter[0] = a.step0 + a.n_steps;
-    a.any_flag[0] = 0;
-    a.any_flag[1] = 0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.step_counter[0] = a.step0 + a.n_steps;
 }
 
 }  // namespace tbsma

@@ -134,8 +134,7 @@ struct tbsma_ctx {
   int wait_limit = kUfSteps;        // bound of the topology's union-find walks and barrier waits
   int step_mode = TBSMA_STEPS_AUTO;  // graph replays or the persistent step kernel
   int lanes = 1;  // threads per atom in the MIXED pair passes: 1 or 4
-  unsigned* bar = nullptr;           // [3] grid barrier of the persistent step kernel
-  int32_t* any_flag = nullptr;       // [2] some wire flagged in a step of this parity
+  unsigned* bar = nullptr;           // [3] persistent kernel barrier: 64-bit arrival count, error word
   tbsma_protocol proto{};           // paper protocol mode (default: Langevin, continuous pull)
   double* d_grip = nullptr;
   int64_t* step_counter = nullptr;
@@ -144,6 +143,8 @@ struct tbsma_ctx {
 
   std::vector<WireDev> wires_h;
   Graph graph;
+  cudaGraphExec_t obs_graph = nullptr;  // a report's re-pack, rebuild and passes (launch_captured)
+  cudaGraphExec_t fc_graph = nullptr;   // the force check's
   double graph_dt = -1.0;
 
   PairConsts pc{};
@@ -390,7 +391,7 @@ void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
 
 template <bool OBS, bool DECIDE32, bool EAM>
 void pair_f64_pot(tbsma_ctx* c, cudaStream_t s, int which) {
-  const unsigned g = grid_for(c->NS, c->block);
+  const unsigned g = grid_for(c->NS * kLanes64, c->block);  // a warp per atom
   if (which & 1)
     k_density_f64<OBS, DECIDE32, EAM><<<g, c->block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
                                                               c->perm, c->cap, c->pc, c->inv64,
@@ -589,6 +590,37 @@ void drop_graph(tbsma_ctx* c) {
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   c->graph = Graph{};
   c->graph_dt = -1.0;
+  for (cudaGraphExec_t* g : {&c->obs_graph, &c->fc_graph})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+}
+
+// Launch the kernels `enqueue` puts on a stream as one graph, captured on
+// first use and kept until drop_graph (a report's dozen short launches cost
+// more than their work on a small context).
+template <class F>
+tbsma_status launch_captured(tbsma_ctx* c, cudaGraphExec_t& exec, F enqueue) {
+  if (!exec) {
+    cudaGraph_t g = nullptr;
+    TB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const tbsma_status st = enqueue(c->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != TBSMA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      exec = nullptr;
+      return cuda_fail(c, ei, "cudaGraphInstantiate");
+    }
+  }
+  TB_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  return TBSMA_OK;
 }
 
 tbsma_status set_dt(tbsma_ctx* c, double dt) {
@@ -693,7 +725,6 @@ tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double 
   a.xq_b = c->xq_b;
   a.half_skin2 = (float)c->half_skin2;
   a.flag = c->flag;
-  a.any_flag = c->any_flag;
   a.wire_status = c->wire_status;
   a.d_grip = c->d_grip;
   a.step_counter = c->step_counter;
@@ -716,10 +747,9 @@ tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double 
   a.step0 = c->steps_done;
   a.n_steps = n;
   a.seq = seq;
-  a.bar = GridBarrier{c->bar, c->bar + 1, c->bar + 2,
+  a.bar = GridBarrier{reinterpret_cast<unsigned long long*>(c->bar), c->bar + 2,
                       (unsigned)std::max(0, c->wait_limit - 1) * 4u};
   TB_CUDA(c, cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), c->stream));
-  TB_CUDA(c, cudaMemsetAsync(c->any_flag, 0, 2 * sizeof(int32_t), c->stream));
   void* args[] = {&a};
   TB_CUDA(c, cudaLaunchCooperativeKernel(persist_fn(c), dim3((unsigned)blocks), dim3(256), args,
                                          persist_smem(c), c->stream));
@@ -1125,7 +1155,6 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->chains, 1);
   ALLOC(c->rebuilt, 2);
   ALLOC(c->bar, 3);
-  ALLOC(c->any_flag, 2);
   ALLOC(c->last_build, W);
   ALLOC(c->banked, W);
   ALLOC(c->wire_status, W);
@@ -1145,7 +1174,6 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), st) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(c->any_flag, 0, 2 * sizeof(int32_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->banked, 0, W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->wdis, 0xff, sizeof(uint32_t) * W, st) == cudaSuccess;  // NaN: cells
@@ -1284,8 +1312,12 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
 tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
   NvtxRange range_("tbsma_reduce_observables");
   if (!c || !out) return TBSMA_EINVAL;
-  TB_TRY(refresh(c, 0));
-  TB_TRY(launch_pair<true>(c, c->stream, c->prec));
+  // re-pack, rebuild flagged wires, both passes with the per-atom terms
+  TB_TRY(launch_captured(c, c->obs_graph, [c](cudaStream_t s) {
+    TB_TRY(launch_pack(c, s, 1));
+    TB_TRY(launch_nl(c, s, 0, 0, nullptr));
+    return launch_pair<true>(c, s, c->prec);
+  }));
   const double rhs = 0.5 * c->P.r0;
   const double v_atom = 4.0 / 3.0 * 3.141592653589793238462643383279 * rhs * rhs * rhs;
   k_observe<<<std::min(c->W, 65535), 256, 0, c->stream>>>(
@@ -1302,12 +1334,16 @@ tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
 tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
   NvtxRange range_("tbsma_force_check");
   if (!c || !out) return TBSMA_EINVAL;
-  TB_TRY(refresh(c, 0));
-  TB_TRY(launch_pair<false>(c, c->stream, TBSMA_MIXED));
-  TB_TRY(launch_pair<true>(c, c->stream, TBSMA_FP64, true));
-  k_force_check<<<std::min(c->W, 65535), 256, 0, c->stream>>>(c->W, c->wd, c->N, c->f32, c->f64,
-                                                              c->s_atom, c->fcheck_d);
-  TB_CUDA(c, cudaGetLastError());
+  TB_TRY(launch_captured(c, c->fc_graph, [c](cudaStream_t s) {
+    TB_TRY(launch_pack(c, s, 1));
+    TB_TRY(launch_nl(c, s, 0, 0, nullptr));
+    TB_TRY(launch_pair<false>(c, s, TBSMA_MIXED));
+    TB_TRY(launch_pair<true>(c, s, TBSMA_FP64, true));
+    k_force_check<<<std::min(c->W, 65535), 256, 0, s>>>(c->W, c->wd, c->N, c->f32, c->f64,
+                                                        c->s_atom, c->fcheck_d);
+    TB_CUDA(c, cudaGetLastError());
+    return TBSMA_OK;
+  }));
   TB_CUDA(c, cudaMemcpyAsync(out, c->fcheck_d, sizeof(tbsma_fcheck) * c->W, cudaMemcpyDeviceToHost,
                              c->stream));
   TB_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -211,6 +211,46 @@ def test_disordered_atom_order_takes_the_cell_build(tb, orc):
     assert norm <= 1e-5
 
 
+def test_wire_beyond_the_slab_coordinate_range_takes_the_cell_build(tb, orc):
+    """A D2 x 300 nm wire (55k atoms) moved 600 A along its axis after init
+    reaches 2100 A from its fixed-point origin, beyond the 2048 A within
+    which the slab scan's FP32 coordinates stay inside the list radius's
+    guard, so its lists come from the cell grid (whose +L/2 margins hold the
+    moved wire); the short wire beside it takes the slab scan.  Both wires'
+    lists bracket the oracle's pairs and their forces match the oracle's."""
+    wires = [Wire(x=jitter(g.x, 0.05, 31 + k), kind=g.kind, diameter_nm=2.0, length_nm=g.length_nm,
+                  L0=g.L0, temperature=10.0, strain_rate=0.0, gamma=1e-3, seed=k)
+             for k, g in enumerate((fcc_wire(2.0, 300.0), fcc_wire(2.0, 6.0)))]
+    b = pack(wires)
+    eng = tb.Engine(b, precision="mixed")
+    s0 = b.wire_slice(0)
+    origin = 0.5 * (b.x[s0, 0].min() + b.x[s0, 0].max())  # the centre of the initial box
+    b.x[s0, 0] += 600.0
+    assert np.max(np.abs(b.x[s0, 0] - origin)) > 2048.0
+    eng.upload(np.ascontiguousarray(b.x.T).reshape(-1), None)
+    eng.build_neighbors(True)
+    n, nb = eng.neighbors()
+    n, nb = n.cpu().numpy(), nb.cpu().numpy()
+    F32, _ = eng.forces(f32=True, f64=False)
+    F32 = F32.double().cpu().numpy()
+    assert np.all(eng.wire_status() == 0)
+    eng.close()
+    r_list = orc.AU.r_cut + orc.R_SKIN + 1e-3
+    for w in range(2):
+        s = b.wire_slice(w)
+        o = int(b.offset[w])
+        s_in, n_in = orc.pairs(b.x[s], r_list - 1e-4, "cells")
+        for k in range(int(b.n[w])):
+            assert set(n_in[s_in[k]:s_in[k + 1]].tolist()) <= set((nb[o + k, :n[o + k]] - o).tolist())
+        ref = orc.tbsma(b.x[s], brute_max=0)
+        amb = ambiguous_atoms(orc, b.x[s], orc.AU.r_cut, 5e-6)
+        ok = np.ones(int(b.n[w]), bool)
+        ok[amb] = False
+        d, fm, norm = force_errors(F32[s], ref.F)
+        assert np.max(d[ok] / ref.S[ok]) <= 1e-5
+        assert norm <= 1e-5
+
+
 # --------------------------------------------------------- initial state
 def test_init_velocities_match_oracle(tb, orc):
     b = workload("tiny_batch")
