@@ -326,9 +326,10 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
  *                           returns EINVAL if the context cannot run it).
  * The persistent step kernel runs a call's steps (up to 1000 per launch) in
  * one cooperative launch, one block per 256-atom tile, its blocks meeting at
- * bounded grid-wide barriers between the phases of a step: the same
- * kernels' code per atom and per tile, so bitwise the same trajectories as
- * the graph replays, without a launch per phase.  It serves small contexts:
+ * bounded grid-wide barriers between the phases of a step (two per step
+ * without a rebuild: the force pass also integrates each atom's next step):
+ * the same kernels' code per atom and per tile, so bitwise the same
+ * trajectories as the graph replays, without a launch per phase.  It serves small contexts:
  * MIXED, the default protocol (Langevin, continuous pull), 256-atom tiles
  * (tbsma_set_launch), and every tile of the batch resident on the GPU at
  * once.  blocks (host, nullable) receives the blocks it would use in this

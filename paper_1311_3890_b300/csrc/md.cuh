@@ -727,30 +727,63 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Block per wire: mixed vs FP64 force errors.
+// Mixed vs FP64 force errors in two kernels, so that one large wire spreads
+// over the GPU: k_force_check_tiles takes one block per 256-slot tile (a
+// tile never mixes wires) and writes the tile's partials — the largest
+// |dF_i| / S_i, |dF_i| / |F_i| and |dF_i|, and the sums of |dF_i|^2 and
+// |F_i|^2 — to part[5 * tile]; k_force_check folds a wire's tiles, a block
+// per wire.  Sums run in fixed trees in both, so the results are the same on
+// every run and for a wire alone or in any batch.
 __global__ void __launch_bounds__(256)
-    k_force_check(int W, const WireDev* __restrict__ wd, int64_t N, const float* __restrict__ f32,
-                  const double* __restrict__ f64, const double* __restrict__ s_atom,
+    k_force_check_tiles(int64_t NS, int64_t N, const int32_t* __restrict__ perm,
+                        const float* __restrict__ f32, const double* __restrict__ f64,
+                        const double* __restrict__ s_atom, double* __restrict__ part) {
+  __shared__ double sh[256];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = t < NS ? perm[t] : -1;
+  double es = 0.0, er = 0.0, ea = 0.0, dd = 0.0, ff = 0.0;
+  if (i >= 0) {
+    for (int d = 0; d < 3; ++d) {
+      const double r = f64[d * N + i];
+      const double e = (double)f32[d * N + i] - r;
+      dd += e * e;
+      ff += r * r;
+    }
+    const double de = sqrt(dd), fm = sqrt(ff);
+    if (s_atom[i] > 0.0) es = de / s_atom[i];
+    if (fm > 0.0) er = de / fm;
+    ea = de;
+  }
+  es = block_max(es, sh);
+  er = block_max(er, sh);
+  ea = block_max(ea, sh);
+  dd = block_sum(dd, sh);
+  ff = block_sum(ff, sh);
+  if (threadIdx.x == 0) {
+    double* p = part + 5 * blockIdx.x;
+    p[0] = es;
+    p[1] = er;
+    p[2] = ea;
+    p[3] = dd;
+    p[4] = ff;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_force_check(int W, const WireDev* __restrict__ wd, const double* __restrict__ part,
                   tbsma_fcheck* __restrict__ out) {
   __shared__ double sh[256];
   for (int w = blockIdx.x; w < W; w += gridDim.x) {
     const WireDev& wr = wd[w];
+    const int64_t t0 = wr.slot_base / 256, nt = (wr.n + 255) / 256;
     double es = 0.0, er = 0.0, ea = 0.0, d2 = 0.0, f2 = 0.0;
-    for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
-      const int64_t i = wr.offset + a;
-      double dd = 0.0, ff = 0.0;
-      for (int d = 0; d < 3; ++d) {
-        const double r = f64[d * N + i];
-        const double e = (double)f32[d * N + i] - r;
-        dd += e * e;
-        ff += r * r;
-      }
-      const double de = sqrt(dd), fm = sqrt(ff);
-      if (s_atom[i] > 0.0) es = fmax(es, de / s_atom[i]);
-      if (fm > 0.0) er = fmax(er, de / fm);
-      ea = fmax(ea, de);
-      d2 += dd;
-      f2 += ff;
+    for (int64_t k = threadIdx.x; k < nt; k += blockDim.x) {
+      const double* p = part + 5 * (t0 + k);
+      es = fmax(es, p[0]);
+      er = fmax(er, p[1]);
+      ea = fmax(ea, p[2]);
+      d2 += p[3];
+      f2 += p[4];
     }
     es = block_max(es, sh);
     er = block_max(er, sh);

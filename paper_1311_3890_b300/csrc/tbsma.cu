@@ -140,6 +140,7 @@ struct tbsma_ctx {
   int64_t* step_counter = nullptr;
   tbsma_obs* obs_d = nullptr;
   tbsma_fcheck* fcheck_d = nullptr;
+  double* fc_part = nullptr;  // [NS / 256][5] per-tile partials of the force check
 
   std::vector<WireDev> wires_h;
   Graph graph;
@@ -1164,6 +1165,7 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->step_counter, 1);
   ALLOC(c->obs_d, W);
   ALLOC(c->fcheck_d, W);
+  ALLOC(c->fc_part, (size_t)(NS / 256) * 5);
 #undef ALLOC
 
   cudaStream_t st = c->stream;
@@ -1339,8 +1341,9 @@ tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {
     TB_TRY(launch_nl(c, s, 0, 0, nullptr));
     TB_TRY(launch_pair<false>(c, s, TBSMA_MIXED));
     TB_TRY(launch_pair<true>(c, s, TBSMA_FP64, true));
-    k_force_check<<<std::min(c->W, 65535), 256, 0, s>>>(c->W, c->wd, c->N, c->f32, c->f64,
-                                                        c->s_atom, c->fcheck_d);
+    k_force_check_tiles<<<(unsigned)(c->NS / 256), 256, 0, s>>>(c->NS, c->N, c->perm, c->f32,
+                                                                c->f64, c->s_atom, c->fc_part);
+    k_force_check<<<std::min(c->W, 65535), 256, 0, s>>>(c->W, c->wd, c->fc_part, c->fcheck_d);
     TB_CUDA(c, cudaGetLastError());
     return TBSMA_OK;
   }));
