@@ -44,6 +44,7 @@ WORKLOAD = "sweep2048"
 EQUIL_STEPS = 2000  # untimed equilibration before the warm-up steps (steady rebuild cadence)
 LAUNCH = (256, 1280)  # pair passes: atoms per tile (threads per block), shared-memory window (atoms)
 GRAPH_CHUNK = 50  # steps per captured graph (library constant)
+PERSIST_STEPS = 1000  # most steps per launch of the persistent step kernel (library constant)
 # List skin (A).  Results do not depend on it (every pass tests r_cut); at
 # 10 K a 0.40 A skin keeps the list radius (6.20 A) inside the gap between the
 # fourth (5.77 A) and fifth (6.45 A) fcc shells, so the lists are no longer
@@ -383,10 +384,15 @@ def _chunks(K: int):
     return out
 
 
-def launches_in(K: int, chains: int) -> int:
+def launches_in(K: int, chains: int, persistent: bool = False) -> int:
     """Kernels launched by K timed steps: the fixed ones per step and per
     report, one closing kernel per graph replay or direct sequence, and
-    `chains` launches of the rebuild chain (counted on the device)."""
+    `chains` launches of the rebuild chain (counted on the device).  In the
+    persistent step kernel a call of up to 1000 steps is one launch, and
+    only the reports launch the rebuild chain."""
+    if persistent:
+        return sum(-(-k // PERSIST_STEPS) + KERNELS_PER_OBS + KERNELS_PER_CHAIN
+                   for k in _chunks(K))
     n = KERNELS_PER_CHAIN * chains
     for k in _chunks(K):
         full, rem = divmod(k, GRAPH_CHUNK) if k >= GRAPH_CHUNK else (0, k)
@@ -691,7 +697,7 @@ def run_ours(args):
         "data": "synthetic", "config": cfg,
         "roofline": roof,
         "clocks": ck,
-        "gpu_launches": launches_in(args.steps, chains),
+        "gpu_launches": launches_in(args.steps, chains, persistent=persist_blocks > 0),
         "force_check": {"max_err_scaled": float(fc["max_err_scaled"].max()),
                         "norm_err": float(fc["norm_err"].max()),
                         "max_err_raw": float(fc["max_err_raw"].max())},

@@ -26,6 +26,15 @@ def test_launch_count_of_the_default_run():
     assert bench.launches_in(30, 30) == 4 * 30 + 1 + 5 + 7 * 30
 
 
+def test_launch_count_in_the_persistent_step_kernel():
+    """50000 steps of a small context: 50 calls of 1000 steps, each one
+    launch of the persistent kernel, and 50 reports of 5 kernels plus a
+    rebuild chain of 7 (the per-step plans inside the kernel launch
+    nothing)."""
+    assert bench.launches_in(50000, 50000 + 50, persistent=True) == 50 * (1 + 5 + 7) == 650
+    assert bench.launches_in(30, 31, persistent=True) == 1 + 5 + 7
+
+
 def test_roofline_bound_and_fraction():
     """A census of 44.87 in-cutoff and 0.82 skin entries per atom: the force
     pass is FP32-bound on the method's count (19 FP32 + 3 MUFU per in-cutoff
