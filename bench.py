@@ -84,7 +84,7 @@ def parse():
     p.add_argument("--run-log", default=None,
                    help="time the run through runlog.run_logged into this JSON-lines file: "
                         "observables every 1000 steps and the mixed-vs-FP64 force check at each")
-    p.add_argument("--lanes", type=int, default=1, choices=[1, 4],
+    p.add_argument("--lanes", type=int, default=1, choices=[1, 2, 4],
                    help="threads per atom in the pair passes (bitwise the same results)")
     p.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                    help="graph replays or the persistent step kernel (auto: persistent where "

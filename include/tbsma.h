@@ -336,11 +336,10 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
  * context (0: it cannot run it).  Errors: EINVAL (unknown mode). */
 /* Threads per atom in the MIXED pair passes, graph replays and the
  * persistent step kernel alike: 1 (default; one thread walks the atom's
- * list) or 4 (four threads per atom, each evaluating one entry of every
- * group of four, the terms added in list order through shuffles: bitwise
- * the same forces and energies).  Measured on a B300, 4 is slower both on
- * large batches and on a lone 17k-atom wire; it is kept because it is
- * exact.  Invalidates captured graphs.  Errors: EINVAL (other values). */
+ * list), 2 or 4 (each thread evaluating every second or fourth entry of
+ * every group of four, the terms added in list order through shuffles:
+ * bitwise the same forces and energies; a tile then holds 128 or 64
+ * atoms).  Invalidates captured graphs.  Errors: EINVAL (other values). */
 tbsma_status tbsma_set_pair_lanes(tbsma_ctx* ctx, int32_t lanes);
 
 #define TBSMA_STEPS_AUTO 0

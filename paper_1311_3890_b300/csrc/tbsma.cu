@@ -376,18 +376,21 @@ void pair_f32_pot(tbsma_ctx* c, cudaStream_t s, int which) {
 }
 
 // Threads per atom of the MIXED pair passes.
-int graph_lanes(const tbsma_ctx* c) { return c->lanes == 4 ? 4 : 1; }
+int graph_lanes(const tbsma_ctx* c) { return c->lanes; }
+
+template <bool OBS, bool EAM>
+void pair_f32_lanes(tbsma_ctx* c, cudaStream_t s, int which) {
+  switch (graph_lanes(c)) {
+    case 4: pair_f32_pot<OBS, EAM, 4>(c, s, which); break;
+    case 2: pair_f32_pot<OBS, EAM, 2>(c, s, which); break;
+    default: pair_f32_pot<OBS, EAM, 1>(c, s, which);
+  }
+}
 
 template <bool OBS>
 void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
-  const bool four = graph_lanes(c) == 4;
-  if (c->eam_on) {
-    if (four) pair_f32_pot<OBS, true, 4>(c, s, which);
-    else pair_f32_pot<OBS, true, 1>(c, s, which);
-  } else {
-    if (four) pair_f32_pot<OBS, false, 4>(c, s, which);
-    else pair_f32_pot<OBS, false, 1>(c, s, which);
-  }
+  if (c->eam_on) pair_f32_lanes<OBS, true>(c, s, which);
+  else pair_f32_lanes<OBS, false>(c, s, which);
 }
 
 template <bool OBS, bool DECIDE32, bool EAM>
@@ -669,7 +672,7 @@ tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
 // Dynamic shared memory of the persistent step kernel: the largest of the
 // pair passes' window with the tile cache and the two builds' buffers.
 size_t persist_smem(const tbsma_ctx* c) {
-  const int slots = 256 / (c->lanes == 4 ? 4 : 1);
+  const int slots = 256 / c->lanes;
   const size_t window = (size_t)c->wcap * sizeof(int4) + tile_cache_bytes(c->cap, slots);
   const size_t cell = (size_t)256 * c->cap * sizeof(int16_t);
   const size_t slab = (size_t)256 * ((c->cap + kSlabSlack) * sizeof(int16_t) + c->cap);
@@ -681,12 +684,17 @@ size_t persist_smem(const tbsma_ctx* c) {
 // batch resident at once (one block per tile, at most the co-resident
 // blocks of a cooperative launch).
 // Threads per atom of the persistent kernel's pair passes.
-int persist_lanes(const tbsma_ctx* c) { return c->lanes == 4 ? 4 : 1; }
+int persist_lanes(const tbsma_ctx* c) { return c->lanes; }
 
 const void* persist_fn(const tbsma_ctx* c) {
-  if (persist_lanes(c) == 4)
-    return c->eam_on ? (const void*)k_steps_persistent<true, 4> : (const void*)k_steps_persistent<false, 4>;
-  return c->eam_on ? (const void*)k_steps_persistent<true, 1> : (const void*)k_steps_persistent<false, 1>;
+  switch (persist_lanes(c)) {
+    case 4:
+      return c->eam_on ? (const void*)k_steps_persistent<true, 4> : (const void*)k_steps_persistent<false, 4>;
+    case 2:
+      return c->eam_on ? (const void*)k_steps_persistent<true, 2> : (const void*)k_steps_persistent<false, 2>;
+    default:
+      return c->eam_on ? (const void*)k_steps_persistent<true, 1> : (const void*)k_steps_persistent<false, 1>;
+  }
 }
 
 int persist_blocks(tbsma_ctx* c) {
@@ -1042,7 +1050,15 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       !smem_attr((const void*)k_density_f32<false, true, 4>) ||
       !smem_attr((const void*)k_density_f32<true, true, 4>) ||
       !smem_attr((const void*)k_force_f32<false, true, 4>) ||
-      !smem_attr((const void*)k_force_f32<true, true, 4>))
+      !smem_attr((const void*)k_force_f32<true, true, 4>) ||
+      !smem_attr((const void*)k_density_f32<false, false, 2>) ||
+      !smem_attr((const void*)k_density_f32<true, false, 2>) ||
+      !smem_attr((const void*)k_force_f32<false, false, 2>) ||
+      !smem_attr((const void*)k_force_f32<true, false, 2>) ||
+      !smem_attr((const void*)k_density_f32<false, true, 2>) ||
+      !smem_attr((const void*)k_density_f32<true, true, 2>) ||
+      !smem_attr((const void*)k_force_f32<false, true, 2>) ||
+      !smem_attr((const void*)k_force_f32<true, true, 2>))
     return bail(TBSMA_ECUDA);
   const int sbuf_max = 256 * kMaxCap * (int)sizeof(int16_t);  // k_nl_build's entry buffers
   const int slab_max = 256 * ((kMaxCap + kSlabSlack) * (int)sizeof(int16_t) + kMaxCap);  // k_nl_build_slab's
@@ -1061,7 +1077,9 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   if (cudaFuncSetAttribute(k_steps_persistent<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_steps_persistent<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
+      cudaFuncSetAttribute(k_steps_persistent<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
@@ -1561,7 +1579,7 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* c, int32_t steps) {
 
 tbsma_status tbsma_set_pair_lanes(tbsma_ctx* c, int32_t lanes) {
   if (!c) return TBSMA_EINVAL;
-  if (lanes != 1 && lanes != 4) return fail(c, TBSMA_EINVAL, "lanes must be 1 or 4");
+  if (lanes != 1 && lanes != 2 && lanes != 4) return fail(c, TBSMA_EINVAL, "lanes must be 1, 2 or 4");
   c->lanes = lanes;
   drop_graph(c);
   return TBSMA_OK;

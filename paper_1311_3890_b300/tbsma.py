@@ -452,7 +452,7 @@ class Engine:
 
     def set_pair_lanes(self, lanes: int = 1):
         """Threads per atom in the MIXED pair passes (tbsma_set_pair_lanes):
-        1 (default) or 4 (bitwise the same results)."""
+        1 (default), 2 or 4 (bitwise the same results)."""
         self._check(lib().tbsma_set_pair_lanes(self.ctx, int(lanes)), "tbsma_set_pair_lanes")
 
     def save(self, path: str):

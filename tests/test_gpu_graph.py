@@ -81,7 +81,7 @@ def test_profiled_steps_equal_graph_steps(tb, prec):
     assert all(v > 0.0 for v in ph.values())
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_persistent_step_kernel_equals_graph_replays(tb, lanes):
     """The persistent step kernel (one cooperative launch per call, grid
     barriers between the phases) runs the graph path's code per atom and
@@ -163,17 +163,18 @@ def test_persistent_mode_is_refused_where_it_cannot_run(tb):
     eng.close()
 
 
-def test_four_lanes_per_atom_give_bitwise_the_same_results(tb):
-    """The pair passes with four threads per atom (each evaluating one entry
-    of every group of four, the terms added in list order through shuffles)
-    give bitwise the forces, energies and virials of one thread per atom, on
-    a jittered tiny batch in both launch shapes, and the same trajectory."""
+def test_two_and_four_lanes_per_atom_give_bitwise_the_same_results(tb):
+    """The pair passes with two or four threads per atom (each evaluating
+    every second or fourth entry of every group of four, the terms added in
+    list order through shuffles) give bitwise the forces, energies and
+    virials of one thread per atom on a jittered tiny batch, and the same
+    trajectory."""
     from inputs import jitter
 
     b = workload("tiny_batch")
     b.x = jitter(b.x, 0.06, 41)
     out = []
-    for lanes in (1, 4):
+    for lanes in (1, 2, 4):
         eng = tb.Engine(b, precision="mixed")
         eng.set_step_mode("graph")
         eng.set_pair_lanes(lanes)
@@ -183,5 +184,6 @@ def test_four_lanes_per_atom_give_bitwise_the_same_results(tb):
         eng.step(120, 2.0)
         out.append((F32.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy(), eng.positions()))
         eng.close()
-    for a, c in zip(out[0], out[1]):
-        np.testing.assert_array_equal(a, c)
+    for other in out[1:]:
+        for a, c in zip(out[0], other):
+            np.testing.assert_array_equal(a, c)
