@@ -760,8 +760,12 @@ def run_ours(args):
             picks = stratified_sample(specs, batch.n,
                                       max(1, (3 * threads + n_strata - 1) // n_strata))
             v, cores, desc, _, _ = oracle_sample(batch, budget_s=15.0, eam=eam, wires=picks)
+            # one core: the sample's median-sized wire alone (one wire is one task)
+            mid = sorted(picks, key=lambda w: batch.n[w])[len(picks) // 2]
+            v1, _, desc1, _, _ = oracle_sample(batch, budget_s=2.0, eam=eam, wires=[mid])
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": desc + ", stratified over diameter and temperature"}
+                                    "sample": desc + ", stratified over diameter and temperature",
+                                    "single_core": {"value": v1, "unit": UNIT, "sample": desc1}}
     eng.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
