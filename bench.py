@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--run-log", default=None,
                    help="time the run through runlog.run_logged into this JSON-lines file: "
                         "observables every 1000 steps and the mixed-vs-FP64 force check at each")
+    p.add_argument("--r-skin", type=float, default=R_SKIN,
+                   help="neighbour-list skin, A (forces do not depend on it)")
     p.add_argument("--lanes", type=int, default=1, choices=[1, 2, 4],
                    help="threads per atom in the pair passes (bitwise the same results)")
     p.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
@@ -589,7 +591,7 @@ def run_ours(args):
     specs = replicate_specs(WORKLOADS[args.workload](), rank, world)
     batch = build(specs)
     N, W = batch.n_atoms, batch.n_wires
-    params = tb.au_params(r_skin=R_SKIN)
+    params = tb.au_params(r_skin=args.r_skin)
     eng = tb.Engine(batch, precision=args.precision, params=params)
     eam = args.potential == "eam"
     if eam:
@@ -675,7 +677,8 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         res[which] = a.elapsed_time(b) / reps
-    captured = tuple(launch) == LAUNCH and args.lanes == 1 and args.workload in ("sweep2048", "sweep144")
+    captured = (tuple(launch) == LAUNCH and args.lanes == 1 and args.r_skin == R_SKIN
+                and args.workload in ("sweep2048", "sweep144"))
     roof = (pass_rooflines(eng, res[2], res[1], ck, eam=eam, captured=captured)
             if args.precision == "mixed" else None)
     cfg = {"workload": args.workload, "atoms_per_gpu": N, "dt_fs": 2.0}
@@ -685,7 +688,7 @@ def run_ours(args):
                               if persist_blocks else "graph replays of 50 steps"),
                 "potential": "tabulated EAM (TB-SMA sampled)" if eam else "TB-SMA (Eq. 1-3)",
                 "equilibration_steps": args.equil, "observables_every": OBS_EVERY,
-                "r_skin_A": R_SKIN, "tile_atoms": launch[0], "window_atoms": launch[1],
+                "r_skin_A": args.r_skin, "tile_atoms": launch[0], "window_atoms": launch[1],
                 "pair_lanes": args.lanes,
                 "launch": "autotuned" if args.autotune else "fixed",
                 "l2": "inputs larger than L2 (no flush)", "parallelism": f"wires x{world}"})
