@@ -62,7 +62,7 @@ UNIT = "atom-steps/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5000)
+    p.add_argument("--steps", type=int, default=10000)
     p.add_argument("--warmup", type=int, default=100, help="untimed steps after the equilibration")
     p.add_argument("--equil", type=int, default=EQUIL_STEPS,
                    help="untimed equilibration steps from the lattice start (part of the input "
