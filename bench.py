@@ -440,9 +440,9 @@ FORCE_IMPL_MODEL = {"fp32_in": 21, "fp32_skin": 7, "mufu_in": 3, "bytes_out": 12
 EAM_MODEL = {"fp32_in": 25, "fp32_skin": 7, "mufu_in": 1, "bytes_out": 12}
 # DRAM bytes (read + write) per atom of one force-pass launch from an ncu
 # capture of the current kernel on a smaller case of the same workload
-# (sweep144: 528.27 MB read + 42.81 MB written for 3,971,388 atoms), scaled
+# (sweep144: 528.30 MB read + 41.71 MB written for 3,971,388 atoms), scaled
 # by the atom count (the traffic is per atom); None once the kernel changes.
-FORCE_TRAFFIC_B_PER_ATOM = 143.8
+FORCE_TRAFFIC_B_PER_ATOM = 143.5
 
 
 def au_eam_tables(d_r=0.002, d_rho=0.005, rho_max=120.0, r_cut=5.8):

@@ -330,10 +330,12 @@ tbsma_status tbsma_set_wait_limit(tbsma_ctx* ctx, int32_t steps);
  * without a rebuild: the force pass also integrates each atom's next step):
  * the same kernels' code per atom and per tile, so bitwise the same
  * trajectories as the graph replays, without a launch per phase.  It serves small contexts:
- * MIXED, the default protocol (Langevin, continuous pull), 256-atom tiles
+ * the default protocol (Langevin, continuous pull), 256-atom tiles
  * (tbsma_set_launch), and every tile of the batch resident on the GPU at
- * once.  blocks (host, nullable) receives the blocks it would use in this
- * context (0: it cannot run it).  Errors: EINVAL (unknown mode). */
+ * once; MIXED and FP64 contexts alike (FP64: 128-thread blocks, the FP64
+ * passes 16 lanes per slot over the grid, three barriers per step).
+ * blocks (host, nullable) receives the blocks it would use in this context
+ * (0: it cannot run it).  Errors: EINVAL (unknown mode). */
 /* Threads per atom in the MIXED pair passes, graph replays and the
  * persistent step kernel alike: 1 (default; one thread walks the atom's
  * list), 2 or 4 (each thread evaluating every second or fourth entry of

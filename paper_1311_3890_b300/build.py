@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc", "tbsma.cu")
-DEPS = [os.path.join(HERE, "csrc", f) for f in ("device.cuh", "nlist.cuh", "pair.cuh", "md.cuh", "topo.cuh")]
+DEPS = [os.path.join(HERE, "csrc", f) for f in ("device.cuh", "nlist.cuh", "pair.cuh", "md.cuh", "persist.cuh", "topo.cuh")]
 HEADER = os.path.join(ROOT, "include", "tbsma.h")
 LIB = os.path.join(HERE, "libtbsma.so")
 

@@ -131,6 +131,7 @@ struct PairConsts {
   float gA, gB;
   // FP64 path
   double rc2, r0, A, xi2, p, q, fp, fg;  // fp = 2 p / r0, fg = 2 q / r0
+  double inv_r0;                          // 1 / r0: s = r inv_r0 - 1
 };
 
 // Tabulated EAM tables on the device (tbsma_set_eam).  Each function is a

@@ -113,7 +113,7 @@ __device__ __forceinline__ void pack_and_check(int64_t i, uint32_t m, const Wire
                                                double py, double pz, int4* xq, double4_32a* xd,
                                                const int4* xq_b, const double4_32a* xd_b,
                                                double half_skin2, int check, int32_t* flag,
-                                               uint32_t* wire_status) {
+                                               uint32_t* wire_status, int32_t* any = nullptr) {
   const uint32_t wi = meta_wire(m);
   bool moved = false;
   if (PREC == TBSMA_MIXED) {
@@ -137,7 +137,10 @@ __device__ __forceinline__ void pack_and_check(int64_t i, uint32_t m, const Wire
       moved = dx * dx + dy * dy + dz * dz > half_skin2;
     }
   }
-  if (moved) flag[wi] = 1;
+  if (moved) {
+    flag[wi] = 1;
+    if (any) *any = 1;
+  }
 }
 
 // Pack the caller's positions for the pair kernels (both layouts), and, if
@@ -177,22 +180,18 @@ __global__ void k_pack(int64_t N, const double* __restrict__ x, const uint32_t* 
 // ramped target temperature (see ProtoDev).  PROTO = false compiles the
 // default protocol (Langevin, continuous pull, no ramp) alone.
 template <int PREC, int KICK, bool PROTO>
-__global__ void __launch_bounds__(256)
-    k_integrate(int64_t N, double* __restrict__ x, double* __restrict__ v,
-                const float* __restrict__ f32, const double* __restrict__ f64,
-                const uint32_t* __restrict__ meta, const WireDev* __restrict__ wd,
-                const WireDyn* __restrict__ wdyn, double dt, double inv_m,
-                const int64_t* __restrict__ step_counter, int4* xq, double4_32a* xd,
-                const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
-                int32_t* flag, uint32_t* wire_status, double* d_grip, ProtoDev proto,
-                const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__device__ __forceinline__ void integrate_atom(
+    int64_t i, long long step, int64_t N, double* __restrict__ x, double* __restrict__ v,
+    const float* __restrict__ f32, const double* __restrict__ f64,
+    const uint32_t* __restrict__ meta, const WireDev* __restrict__ wd,
+    const WireDyn* __restrict__ wdyn, double dt, double inv_m, int4* xq, double4_32a* xd,
+    const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
+    int32_t* flag, uint32_t* wire_status, double* d_grip, const ProtoDev& proto,
+    const NhState* __restrict__ nh, const BaroState* __restrict__ baro, int32_t* any) {
   const uint32_t m = meta[i];
   const uint32_t wi = meta_wire(m), kind = meta_kind(m);
   const WireDev& w = wd[wi];
   const WireDyn dy = wdyn[wi];
-  const long long step = step_counter[0];
   const double delta = PROTO ? grip_delta(proto, dy.delta, step) : dy.delta;
   double px = x[i], py = x[N + i], pz = x[2 * N + i];
   double bc = 0.0, bmu = 1.0;
@@ -278,8 +277,26 @@ __global__ void __launch_bounds__(256)
   v[N + i] = vy;
   v[2 * N + i] = vz;
   if (!isfinite(px + py + pz + vx + vy + vz)) atomicOr(&wire_status[wi], kWireNonFinite);
-  pack_and_check<PREC>(i, m, w, px, py, pz, xq, xd, xq_b, xd_b, half_skin2, 1, flag, wire_status);
+  pack_and_check<PREC>(i, m, w, px, py, pz, xq, xd, xq_b, xd_b, half_skin2, 1, flag, wire_status,
+                       any);
   if (i == w.offset) d_grip[wi] += delta;
+}
+
+template <int PREC, int KICK, bool PROTO>
+__global__ void __launch_bounds__(256)
+    k_integrate(int64_t N, double* __restrict__ x, double* __restrict__ v,
+                const float* __restrict__ f32, const double* __restrict__ f64,
+                const uint32_t* __restrict__ meta, const WireDev* __restrict__ wd,
+                const WireDyn* __restrict__ wdyn, double dt, double inv_m,
+                const int64_t* __restrict__ step_counter, int4* xq, double4_32a* xd,
+                const int4* __restrict__ xq_b, const double4_32a* __restrict__ xd_b, double half_skin2,
+                int32_t* flag, uint32_t* wire_status, double* d_grip, ProtoDev proto,
+                const NhState* __restrict__ nh, const BaroState* __restrict__ baro) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  integrate_atom<PREC, KICK, PROTO>(i, step_counter[0], N, x, v, f32, f64, meta, wd, wdyn, dt, inv_m,
+                                    xq, xd, xq_b, xd_b, half_skin2, flag, wire_status, d_grip, proto,
+                                    nh, baro, nullptr);
 }
 
 // Non-finite test on the exponent bits (integer ops, no FP64 pipe).

@@ -8,7 +8,8 @@
 // into the same sequences as the graph replays, hence bitwise the same
 // trajectory) in one cooperative launch whose blocks meet at grid-wide
 // barriers between the phases.  It covers MIXED contexts under the default
-// protocol (Langevin, continuous pull), TB-SMA or tabulated EAM.  Two
+// protocol (Langevin, continuous pull), TB-SMA or tabulated EAM (FP64
+// contexts have their own, k_steps_persistent_fp64, at the end).  Two
 // barriers per step without a rebuild: after the density pass, and after
 // the force pass, in which each atom's thread, its force at hand, also
 // integrates the atom's next step (into the other of two position buffers,
@@ -280,6 +281,125 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
                                           nullptr, nullptr, nullptr, a.eam, epi);
     }
     if (!grid_sync(a.bar, bt, &s_any, &flagged)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.step_counter[0] = a.step0 + a.n_steps;
+}
+
+}  // namespace tbsma
+
+namespace tbsma {
+
+// The persistent step kernel of FP64 contexts: the same step as the graph
+// path's (integrate, plan and cell-grid rebuild of the flagged wires,
+// density pass, force pass, the closing half kick at a sequence's end) with
+// the same per-atom and per-slot code, in one cooperative launch per call
+// of up to a thousand steps, in blocks of kPair64Block threads.  The FP64
+// passes run kLanes64 lanes per slot, strided over the grid's lane groups;
+// three barriers per step without a rebuild.
+struct PersistArgs64 {
+  int64_t N, NS;
+  int W;
+  double* x;
+  double* v;
+  double* f64;
+  const uint32_t* meta;
+  const WireDev* wd;
+  const WireDyn* wdyn;
+  double dt, inv_m, hk_close;
+  int4* xq;
+  double4_32a* xd;
+  const int4* xq_b;
+  double4_32a* xd_b;
+  double half_skin2;
+  int32_t* flag;
+  uint32_t* wire_status;
+  double* d_grip;
+  int64_t* step_counter;
+  NlWork nw;
+  int32_t* cell_count;
+  int32_t* cell_atoms;
+  int32_t* cell_of;
+  const int32_t* slot_of;
+  float rlist2;
+  int16_t* nbr;
+  int32_t* n_nbr;
+  int cap;
+  int2* jrange;
+  const int32_t* perm;
+  PairConsts pc;
+  double* inv64;
+  EamDev eam;
+  int64_t step0;
+  int n_steps;
+  int seq;
+  GridBarrier bar;
+};
+
+template <bool EAM>
+__global__ void __launch_bounds__(kPair64Block) k_steps_persistent_fp64(PersistArgs64 a) {
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ngroups = nthreads / kLanes64, ggroup = gtid / kLanes64;
+  const int q = threadIdx.x % kLanes64;
+  // the integrate loops deal chunks of 8 consecutive atoms round-robin over
+  // the blocks: an atom's step with its FP64 normals costs some 250 FP64
+  // operations, which atom-by-thread order would leave to the first few
+  // blocks of a small context (1035 atoms: 9 of 148)
+  const int64_t i0 = ((int64_t)(threadIdx.x >> 3) * gridDim.x + blockIdx.x) * 8 + (threadIdx.x & 7);
+  const ProtoDev proto{};
+  unsigned bt = 0;  // barrier target
+  __shared__ int32_t s_any;  // some atom of this block flagged a rebuild since the last barrier
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  unsigned flagged = 0, flagged_before = 0;
+  for (int k = 0; k < a.n_steps; ++k) {
+    const long long step = a.step0 + k;
+    // B A O A, pack, displacement check; a sequence's first step opens with a
+    // half kick, later ones merge the previous closing and this opening kick
+    for (int64_t i = i0; i < a.N; i += nthreads) {
+      if (k % a.seq == 0)
+        integrate_atom<TBSMA_FP64, 1, false>(i, step, a.N, a.x, a.v, nullptr, a.f64, a.meta, a.wd,
+                                             a.wdyn, a.dt, a.inv_m, a.xq, a.xd, a.xq_b, a.xd_b,
+                                             a.half_skin2, a.flag, a.wire_status, a.d_grip, proto,
+                                             nullptr, nullptr, &s_any);
+      else
+        integrate_atom<TBSMA_FP64, 2, false>(i, step, a.N, a.x, a.v, nullptr, a.f64, a.meta, a.wd,
+                                             a.wdyn, a.dt, a.inv_m, a.xq, a.xd, a.xq_b, a.xd_b,
+                                             a.half_skin2, a.flag, a.wire_status, a.d_grip, proto,
+                                             nullptr, nullptr, &s_any);
+    }
+    if (!grid_sync(a.bar, bt, &s_any, &flagged)) return;
+    const bool rebuild = flagged != flagged_before;
+    flagged_before = flagged;
+    if (rebuild) {
+      if (blockIdx.x == 0) nl_plan_body(a.W, a.nw, a.wd, 0, 1, nullptr, step);
+      if (!grid_sync(a.bar, bt)) return;
+      nl_clear_body(a.nw, a.wd, a.cell_count);
+      if (!grid_sync(a.bar, bt)) return;
+      nl_bin_body(a.nw, a.wd, a.x, a.N, a.cell_count, a.cell_atoms, a.cell_of, a.wire_status);
+      if (!grid_sync(a.bar, bt)) return;
+      nl_sort_body(a.nw, a.wd, a.cell_count, a.cell_atoms);
+      if (!grid_sync(a.bar, bt)) return;
+      nl_build_body<double4_32a>(a.nw, a.wd, a.cell_count, a.cell_atoms, a.cell_of, a.slot_of,
+                                 a.rlist2, a.nbr, a.n_nbr, a.cap, a.jrange, a.xd, a.xd_b,
+                                 a.wire_status);
+      if (!grid_sync(a.bar, bt)) return;
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.nw.chains[0] += 1;  // the plan of a step without a rebuild, as in the graph path
+    }
+    for (int64_t t = ggroup; t < a.NS; t += ngroups)
+      density_f64_slot<false, false, EAM>(t, q, a.xd, a.xq, a.nbr, a.n_nbr, a.perm, a.cap, a.pc,
+                                          a.inv64, nullptr, a.eam);
+    if (!grid_sync(a.bar, bt)) return;
+    for (int64_t t = ggroup; t < a.NS; t += ngroups)
+      force_f64_slot<false, false, EAM>(t, q, a.N, a.xd, a.xq, a.nbr, a.n_nbr, a.perm, a.cap, a.pc,
+                                        a.inv64, a.f64, nullptr, nullptr, nullptr, nullptr, a.eam);
+    if (!grid_sync(a.bar, bt)) return;
+    // a sequence's last step closes with a half kick (each thread kicks the
+    // atoms it integrates next, so no barrier is needed before that)
+    if ((k + 1) % a.seq == 0 || k + 1 == a.n_steps)
+      for (int64_t i = i0; i < a.N; i += nthreads)
+        half_kick_atom<TBSMA_FP64>(i, a.N, a.v, nullptr, a.f64, a.meta, a.hk_close);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.step_counter[0] = a.step0 + a.n_steps;
 }

@@ -264,6 +264,7 @@ void fill_pair_consts(tbsma_ctx* c) {
   k.q = P.q;
   k.fp = 2.0 * P.p / P.r0;
   k.fg = 2.0 * P.q / P.r0;
+  k.inv_r0 = 1.0 / P.r0;
   // list radius with a 1e-3 A guard so rounding in the build or in the
   // displacement check can never drop a pair that reaches r_cut
   const double rl = P.r_cut + P.r_skin + 1e-3;
@@ -395,13 +396,13 @@ void pair_f32(tbsma_ctx* c, cudaStream_t s, int which = 3) {
 
 template <bool OBS, bool DECIDE32, bool EAM>
 void pair_f64_pot(tbsma_ctx* c, cudaStream_t s, int which) {
-  const unsigned g = grid_for(c->NS * kLanes64, c->block);  // a warp per atom
+  const unsigned g = grid_for(c->NS * kLanes64, kPair64Block);  // kLanes64 lanes per atom
   if (which & 1)
-    k_density_f64<OBS, DECIDE32, EAM><<<g, c->block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
+    k_density_f64<OBS, DECIDE32, EAM><<<g, kPair64Block, 0, s>>>(c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
                                                               c->perm, c->cap, c->pc, c->inv64,
                                                               c->e_band, c->eam);
   if (which & 2)
-    k_force_f64<OBS, DECIDE32, EAM><<<g, c->block, 0, s>>>(c->N, c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
+    k_force_f64<OBS, DECIDE32, EAM><<<g, kPair64Block, 0, s>>>(c->N, c->NS, c->xd, c->xq, c->nbr, c->n_nbr,
                                                             c->perm, c->cap, c->pc, c->inv64, c->f64,
                                                             c->e_band, c->e_atom, c->w_atom, c->s_atom,
                                                             c->eam);
@@ -466,8 +467,8 @@ void integrate_as(tbsma_ctx* c, cudaStream_t s, double dt) {
         c->N, c->x, c->v, c->f32, c->meta, c->wd, c->wdyn, (float)kick, (float)(0.5 * dt),
         c->step_counter, c->xq, c->xq_b, (float)c->half_skin2, c->flag, c->wire_status,
         c->d_grip, proto_dev(c), c->nh, c->baro);
-  else
-    k_integrate<TBSMA_FP64, KICK, PROTO><<<g, 256, 0, s>>>(
+  else  // warp-sized blocks: FP64-bound, so a small context's atoms reach more SMs
+    k_integrate<TBSMA_FP64, KICK, PROTO><<<grid_for(c->N, 32), 32, 0, s>>>(
         c->N, c->x, c->v, c->f32, c->f64, c->meta, c->wd, c->wdyn, dt, c->inv_m, c->step_counter,
         c->xq, c->xd, c->xq_b, c->xd_b, c->half_skin2, c->flag, c->wire_status, c->d_grip,
         proto_dev(c), c->nh, c->baro);
@@ -671,7 +672,12 @@ tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
 // ------------------------------------------------ persistent step kernel
 // Dynamic shared memory of the persistent step kernel: the largest of the
 // pair passes' window with the tile cache and the two builds' buffers.
+// Threads per block of the persistent step kernel: 256-atom tiles (MIXED),
+// the FP64 passes' blocks (FP64).
+int persist_block(const tbsma_ctx* c) { return c->prec == TBSMA_MIXED ? 256 : kPair64Block; }
+
 size_t persist_smem(const tbsma_ctx* c) {
+  if (c->prec != TBSMA_MIXED) return (size_t)kPair64Block * c->cap * sizeof(int16_t);  // the cell build's
   const int slots = 256 / c->lanes;
   const size_t window = (size_t)c->wcap * sizeof(int4) + tile_cache_bytes(c->cap, slots);
   const size_t cell = (size_t)256 * c->cap * sizeof(int16_t);
@@ -679,14 +685,12 @@ size_t persist_smem(const tbsma_ctx* c) {
   return std::max(window, std::max(cell, slab));
 }
 
-// Blocks of the persistent step kernel for this context, 0 if it cannot run
-// it: MIXED, the default protocol, 256-atom tiles, and every tile of the
-// batch resident at once (one block per tile, at most the co-resident
-// blocks of a cooperative launch).
 // Threads per atom of the persistent kernel's pair passes.
 int persist_lanes(const tbsma_ctx* c) { return c->lanes; }
 
 const void* persist_fn(const tbsma_ctx* c) {
+  if (c->prec != TBSMA_MIXED)
+    return c->eam_on ? (const void*)k_steps_persistent_fp64<true> : (const void*)k_steps_persistent_fp64<false>;
   switch (persist_lanes(c)) {
     case 4:
       return c->eam_on ? (const void*)k_steps_persistent<true, 4> : (const void*)k_steps_persistent<false, 4>;
@@ -697,15 +701,29 @@ const void* persist_fn(const tbsma_ctx* c) {
   }
 }
 
+// Blocks of the persistent step kernel for this context, 0 if it cannot run
+// it: the default protocol, 256-atom tiles, and (MIXED) every tile of the
+// batch resident at once (one block per tile, at most the co-resident
+// blocks of a cooperative launch).
 int persist_blocks(tbsma_ctx* c) {
-  if (c->prec != TBSMA_MIXED || protocol_mode(c) || c->block != 256) return 0;
+  if (protocol_mode(c) || c->block != 256) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_fn(c), 256, persist_smem(c)) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_fn(c), persist_block(c),
+                                                    persist_smem(c)) !=
       cudaSuccess)
     return 0;
   const int64_t tiles = c->NS / 256;
   const int64_t most = (int64_t)per_sm * c->sm_count;
   if (tiles < 1 || tiles > most) return 0;
+  // FP64: kLanes64 lanes per slot over the grid, as many blocks as the
+  // slots fill or as fit, beyond one per SM rounded down to whole rounds of
+  // the SMs (a second block on only some SMs would double their FP64 work
+  // and hold up every barrier)
+  if (c->prec != TBSMA_MIXED) {
+    int64_t b = std::min<int64_t>(c->NS * kLanes64 / kPair64Block, most);
+    if (b > c->sm_count) b = b / c->sm_count * c->sm_count;
+    return (int)b;
+  }
   // one block per tile of the pair passes (256 / lanes atoms), as many as fit
   return (int)std::min<int64_t>(tiles * persist_lanes(c), most);
 }
@@ -713,7 +731,57 @@ int persist_blocks(tbsma_ctx* c) {
 // n steps in one cooperative launch of the persistent step kernel (the
 // caller has checked persist_blocks > 0 and set dt).  Same steps, kicks and
 // step counts as enqueue_steps.
+tbsma_status launch_persistent_fp64(tbsma_ctx* c, int blocks, int n, int seq, double dt) {
+  PersistArgs64 a;
+  a.N = c->N;
+  a.NS = c->NS;
+  a.W = c->W;
+  a.x = c->x;
+  a.v = c->v;
+  a.f64 = c->f64;
+  a.meta = c->meta;
+  a.wd = c->wd;
+  a.wdyn = c->wdyn;
+  a.dt = dt;
+  a.inv_m = c->inv_m;
+  a.hk_close = 0.5 * dt * c->inv_m;
+  a.xq = c->xq;
+  a.xd = c->xd;
+  a.xq_b = c->xq_b;
+  a.xd_b = c->xd_b;
+  a.half_skin2 = c->half_skin2;
+  a.flag = c->flag;
+  a.wire_status = c->wire_status;
+  a.d_grip = c->d_grip;
+  a.step_counter = c->step_counter;
+  a.nw = c->nw();
+  a.cell_count = c->cell_count;
+  a.cell_atoms = c->cell_atoms;
+  a.cell_of = c->cell_of;
+  a.slot_of = c->slot_of;
+  a.rlist2 = c->rlist2;
+  a.nbr = c->nbr;
+  a.n_nbr = c->n_nbr;
+  a.cap = c->cap;
+  a.jrange = c->jrange;
+  a.perm = c->perm;
+  a.pc = c->pc;
+  a.inv64 = c->inv64;
+  a.eam = c->eam;
+  a.step0 = c->steps_done;
+  a.n_steps = n;
+  a.seq = seq;
+  a.bar = GridBarrier{reinterpret_cast<unsigned long long*>(c->bar), c->bar + 2,
+                      (unsigned)std::max(0, c->wait_limit - 1) * 4u};
+  TB_CUDA(c, cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), c->stream));
+  void* args[] = {&a};
+  TB_CUDA(c, cudaLaunchCooperativeKernel(persist_fn(c), dim3((unsigned)blocks), dim3(kPair64Block), args,
+                                         persist_smem(c), c->stream));
+  return TBSMA_OK;
+}
+
 tbsma_status launch_persistent(tbsma_ctx* c, int blocks, int n, int seq, double dt) {
+  if (c->prec != TBSMA_MIXED) return launch_persistent_fp64(c, blocks, n, seq, dt);
   if (!c->xq2) TB_TRY(alloc(c, &c->xq2, (size_t)c->N));  // the kernel's second position buffer
   PersistArgs a;
   a.N = c->N;
@@ -1079,7 +1147,9 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
       cudaFuncSetAttribute(k_steps_persistent<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
       cudaFuncSetAttribute(k_steps_persistent<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
-      cudaFuncSetAttribute(k_steps_persistent<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess)
+      cudaFuncSetAttribute(k_steps_persistent<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, persist_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent_fp64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess ||
+      cudaFuncSetAttribute(k_steps_persistent_fp64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbuf_max) != cudaSuccess)
     return bail(TBSMA_ECUDA);
   const int W = n_wires;
   tbsma_status s = TBSMA_OK;
@@ -1843,6 +1913,7 @@ extern "C" tbsma_status tbsma_forces_noalloc(const tbsma_params* params, int32_t
   pc.q = P.q;
   pc.fp = 2.0 * P.p / P.r0;
   pc.fg = 2.0 * P.q / P.r0;
+  pc.inv_r0 = 1.0 / P.r0;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int block = 128;
   const unsigned grid = (unsigned)((n_atoms + block - 1) / block);

@@ -175,20 +175,50 @@ def test_persistent_barrier_gives_up_and_context_recovers(tb, tmp_path):
 
 
 def test_persistent_mode_is_refused_where_it_cannot_run(tb):
-    """FP64 contexts and the paper's protocol mode run graph replays; asking
-    them for the persistent step kernel is an EINVAL at the step call."""
+    """The paper's protocol mode and launch shapes other than 256-atom tiles
+    run graph replays; asking them for the persistent step kernel is an
+    EINVAL at the step call."""
     b = workload("tiny_batch")
-    eng = tb.Engine(b, precision="fp64")
-    assert eng.set_step_mode("persistent") == 0
-    with pytest.raises(tb.TbsmaError) as e:
-        eng.step(5, 2.0)
-    assert e.value.status == 1
-    eng.close()
+    for prec in ("mixed", "fp64"):
+        eng = tb.Engine(b, precision=prec)
+        eng.set_protocol()
+        assert eng.set_step_mode("persistent") == 0
+        with pytest.raises(tb.TbsmaError) as e:
+            eng.step(5, 2.0)
+        assert e.value.status == 1
+        eng.close()
     eng = tb.Engine(b, precision="mixed")
-    eng.set_protocol()
+    eng.set_launch(64, 1280)
     assert eng.set_step_mode("auto") == 0
     eng.step(5, 2.0)  # graph replays
     eng.close()
+
+
+def test_fp64_persistent_step_kernel_equals_graph_replays(tb):
+    """FP64 contexts run the persistent step kernel too (a warp per slot in
+    the FP64 passes, the cell build on rebuilds): 300 steps of the tiny batch
+    (10 K and 298 K, pulled, with rebuilds) in calls of 50 and 25 steps give
+    bitwise the positions, velocities and rebuild counts of graph replays."""
+    b = workload("tiny_batch")
+    out = []
+    for mode in ("graph", "persistent"):
+        eng = tb.Engine(b, precision="fp64")
+        blocks = eng.set_step_mode(mode)
+        assert (blocks > 0) == (mode == "persistent")
+        eng.init_velocities()
+        for n in [50, 25] * 4:
+            eng.step(n, 2.0)
+        ob = eng.observables()
+        out.append((eng.positions(), eng.velocities(), ob, eng.rebuild_stats()))
+        eng.close()
+    (xa, va, oa, ra), (xb, vb, ob, rb) = out
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(oa["n_rebuilds"], ob["n_rebuilds"])
+    assert oa["n_rebuilds"].sum() > 3
+    assert ra == rb
+    for k in ("e_pot", "e_kin", "sigma_xx", "strain"):
+        np.testing.assert_array_equal(oa[k], ob[k])
 
 
 def test_two_and_four_lanes_per_atom_give_bitwise_the_same_results(tb):
