@@ -195,7 +195,7 @@ def test_persistent_mode_is_refused_where_it_cannot_run(tb):
 
 
 def test_fp64_persistent_step_kernel_equals_graph_replays(tb):
-    """FP64 contexts run the persistent step kernel too (a warp per slot in
+    """FP64 contexts run the persistent step kernel too (16 lanes per slot in
     the FP64 passes, the cell build on rebuilds): 300 steps of the tiny batch
     (10 K and 298 K, pulled, with rebuilds) in calls of 50 and 25 steps give
     bitwise the positions, velocities and rebuild counts of graph replays."""
@@ -219,6 +219,35 @@ def test_fp64_persistent_step_kernel_equals_graph_replays(tb):
     assert ra == rb
     for k in ("e_pot", "e_kin", "sigma_xx", "strain"):
         np.testing.assert_array_equal(oa[k], ob[k])
+
+
+def test_fp64_persistent_step_kernel_on_more_atoms_than_threads(tb):
+    """Six D3 x L40 wires (~105k atoms, 10 and 298 K, pulled) in FP64: more
+    atoms than the persistent grid has threads, so the integrate loops'
+    8-atom chunks take a second round and every block owns several slots of
+    the FP64 passes; 100 steps with rebuilds give bitwise the graph
+    replays' positions, velocities and rebuild counts."""
+    from inputs.configs import WireSpec, build
+
+    b = build([WireSpec(3.0, 40.0, 10.0 if s % 2 == 0 else 298.0, 1.0e9, s) for s in range(6)])
+    out = []
+    for mode in ("graph", "persistent"):
+        eng = tb.Engine(b, precision="fp64")
+        blocks = eng.set_step_mode(mode)
+        if mode == "persistent":
+            assert 0 < blocks * 128 < b.n_atoms
+        eng.init_velocities()
+        for n in (50, 25, 25):
+            eng.step(n, 2.0)
+        ob = eng.observables()
+        out.append((eng.positions(), eng.velocities(), ob, eng.rebuild_stats()))
+        eng.close()
+    (xa, va, oa, ra), (xb, vb, ob, rb) = out
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(oa["n_rebuilds"], ob["n_rebuilds"])
+    assert oa["n_rebuilds"].sum() > 0
+    assert ra == rb
 
 
 def test_two_and_four_lanes_per_atom_give_bitwise_the_same_results(tb):
