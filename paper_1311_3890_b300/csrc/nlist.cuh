@@ -41,6 +41,14 @@ struct NlWork {
   int64_t* last_build;  // [W] step of the wire's last list build
   uint8_t* banked;      // [W] the wire's rows in bank-group order (k_nl_build) at this build
   int64_t* rebuilt;     // [2] wires and atoms whose lists were built, accumulated
+  // the flagged wires that take the cell build (MIXED: those the envelopes
+  // do not give to the slab build; written by the last block of the envelope
+  // merge), with the prefixes of their cells and atoms
+  int32_t* cl_wire;        // [W]
+  int64_t* cl_cell;        // [W+1]
+  int64_t* cl_atom;        // [W+1]
+  int32_t* n_cell;         // [1]
+  uint32_t* merge_done;    // [1] envelope-merge blocks done (zeroed by the plan)
 };
 
 // Shortest life (steps) of a wire's previous list for which the cell build
@@ -56,6 +64,21 @@ constexpr int kSlotTile = 256;
 // k_nl_env_merge, small enough; NaN positions give a NaN disorder: cells).
 __device__ __forceinline__ bool use_slab(const NlWork& nw, int w) {
   return nw.slab_ok && __uint_as_float(nw.wdis[w]) <= nw.max_disorder;
+}
+
+// The flagged wires the cell build (clear, bin, sort, build) works on: all
+// of them in a context without the slab build, else the list the envelope
+// merge compacted (so the cell build's kernels walk no slab wire's cells or
+// atoms; most steps they have none to walk).
+struct CellList {
+  int n;
+  const int32_t* wire;
+  const int64_t* cell;
+  const int64_t* atom;
+};
+__device__ __forceinline__ CellList cell_list(const NlWork& nw) {
+  if (!nw.slab_ok) return CellList{nw.n_flagged[0], nw.wl_wire, nw.wl_cell, nw.wl_atom};
+  return CellList{nw.n_cell[0], nw.cl_wire, nw.cl_cell, nw.cl_atom};
 }
 
 // Binary search: largest k < nf with pre[k] <= idx.
@@ -153,6 +176,8 @@ __device__ __forceinline__ void nl_plan_body(int W, NlWork nw, const WireDev* __
   if (t == 0) {
     const int nf = (int)tot[3];
     nw.n_flagged[0] = nf;
+    nw.n_cell[0] = 0;      // the envelope merge lists the cell-build wires, if any
+    nw.merge_done[0] = 0;
     nw.wl_cell[nf] = tot[0];
     nw.wl_atom[nf] = tot[1];
     nw.wl_tile[nf] = tot[2];
@@ -171,15 +196,14 @@ __global__ void __launch_bounds__(1024)
 
 __device__ __forceinline__ void nl_clear_body(NlWork nw, const WireDev* __restrict__ wd,
                                               int32_t* cell_count) {
-  const int nf = nw.n_flagged[0];
-  if (nf == 0) return;
-  const int64_t total = nw.wl_cell[nf];
+  const CellList cl = cell_list(nw);
+  if (cl.n == 0) return;
+  const int64_t total = cl.cell[cl.n];
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int k = wl_find(nw.wl_cell, nf, idx);
-    if (use_slab(nw, nw.wl_wire[k])) continue;  // the slab build takes this wire
-    const WireDev& w = wd[nw.wl_wire[k]];
-    cell_count[w.cell_base + (idx - nw.wl_cell[k])] = 0;
+    const int k = wl_find(cl.cell, cl.n, idx);
+    const WireDev& w = wd[cl.wire[k]];
+    cell_count[w.cell_base + (idx - cl.cell[k])] = 0;
   }
 }
 __global__ void k_nl_clear(NlWork nw, const WireDev* __restrict__ wd, int32_t* cell_count) {
@@ -200,16 +224,15 @@ __device__ __forceinline__ void nl_bin_body(NlWork nw, const WireDev* __restrict
                                             const double* __restrict__ x, int64_t N,
                                             int32_t* cell_count, int32_t* cell_atoms,
                                             int32_t* cell_of, uint32_t* wire_status) {
-  const int nf = nw.n_flagged[0];
-  if (nf == 0) return;
-  const int64_t total = nw.wl_atom[nf];
+  const CellList cl = cell_list(nw);
+  if (cl.n == 0) return;
+  const int64_t total = cl.atom[cl.n];
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int k = wl_find(nw.wl_atom, nf, idx);
-    const int wi = nw.wl_wire[k];
-    if (use_slab(nw, wi)) continue;  // the slab build takes this wire
+    const int k = wl_find(cl.atom, cl.n, idx);
+    const int wi = cl.wire[k];
     const WireDev& w = wd[wi];
-    const int64_t i = w.offset + (idx - nw.wl_atom[k]);
+    const int64_t i = w.offset + (idx - cl.atom[k]);
     bool out = false;
     const int cx = cell_coord(x[i] - w.origin[0], w.glo[0], w.einv[0], w.nc[0], out);
     const int cy = cell_coord(x[N + i] - w.origin[1], w.glo[1], w.einv[1], w.nc[1], out);
@@ -231,16 +254,15 @@ __global__ void k_nl_bin(NlWork nw, const WireDev* __restrict__ wd, const double
 // Warp per flagged cell: sort its members ascending (rank by counting).
 __device__ __forceinline__ void nl_sort_body(NlWork nw, const WireDev* __restrict__ wd,
                                              const int32_t* cell_count, int32_t* cell_atoms) {
-  const int nf = nw.n_flagged[0];
-  if (nf == 0) return;
-  const int64_t total = nw.wl_cell[nf];
+  const CellList cl = cell_list(nw);
+  if (cl.n == 0) return;
+  const int64_t total = cl.cell[cl.n];
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
        idx += warps) {
-    const int k = wl_find(nw.wl_cell, nf, idx);
-    if (use_slab(nw, nw.wl_wire[k])) continue;  // warp-uniform (one cell per warp)
-    const int64_t c = wd[nw.wl_wire[k]].cell_base + (idx - nw.wl_cell[k]);
+    const int k = wl_find(cl.cell, cl.n, idx);
+    const int64_t c = wd[cl.wire[k]].cell_base + (idx - cl.cell[k]);
     const int cnt = min(cell_count[c], kCellCap);
     const int32_t m = lane < cnt ? cell_atoms[c * kCellCap + lane] : INT32_MAX;
     int rank = 0;
@@ -318,20 +340,19 @@ __device__ __forceinline__ void nl_build_body(
     int16_t* __restrict__ nbr, int32_t* __restrict__ n_nbr, int cap, int2* __restrict__ jrange,
     const PosT* __restrict__ pos, PosT* __restrict__ pos_build, uint32_t* wire_status) {
   extern __shared__ int16_t sbuf[];  // [cap][blockDim.x]: entry e of thread x at e * blockDim.x + x
-  const int nf = nw.n_flagged[0];
-  if (nf == 0) return;
-  const int64_t total = nw.wl_atom[nf] * kBuildQuad;
+  const CellList cl = cell_list(nw);
+  if (cl.n == 0) return;
+  const int64_t total = cl.atom[cl.n] * kBuildQuad;
   const int q = threadIdx.x & (kBuildQuad - 1);
   const unsigned quad_mask = 0xfu << (threadIdx.x & 31 & ~(kBuildQuad - 1));
   // the stride is a multiple of 4, so a quad is always entirely in or out
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = idx / kBuildQuad;
-    const int k = wl_find(nw.wl_atom, nf, a);
-    const int wi = nw.wl_wire[k];
-    if (use_slab(nw, wi)) continue;  // quad-uniform: the slab build takes this wire
+    const int k = wl_find(cl.atom, cl.n, a);
+    const int wi = cl.wire[k];
     const WireDev& w = wd[wi];
-    const int64_t i = w.offset + (a - nw.wl_atom[k]);
+    const int64_t i = w.offset + (a - cl.atom[k]);
     const int32_t ii = (int32_t)i;
     const int co = cell_of[i];
     const int cx = co >> 20, cy = (co >> 10) & 1023, cz = co & 1023;
@@ -543,8 +564,50 @@ __global__ void __launch_bounds__(kSlotTile)
   nl_env_tiles_body(nw, wd, x);
 }
 
+// One block: the flagged wires that take the cell build (disorder above the
+// slab build's limit, read past L1: the other blocks' atomicMax results),
+// compacted in flagged order with the prefixes of their cells and atoms.
+__device__ __forceinline__ void nl_cell_list_block(NlWork nw, const WireDev* __restrict__ wd) {
+  __shared__ int64_t tot[4];
+  const int nf = nw.n_flagged[0];
+  const int t = threadIdx.x;
+  const int chunk = (nf + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int k0 = min(nf, t * chunk), k1 = min(nf, k0 + chunk);
+  auto cells = [&](int wi) { return (int64_t)wd[wi].nc[0] * wd[wi].nc[1] * wd[wi].nc[2]; };
+  auto cell_wire = [&](int wi) { return !(__uint_as_float(__ldcg(nw.wdis + wi)) <= nw.max_disorder); };
+  int64_t v[4] = {0, 0, 0, 0};  // cells, atoms, -, wires
+  for (int k = k0; k < k1; ++k) {
+    const int wi = nw.wl_wire[k];
+    if (cell_wire(wi)) {
+      v[0] += cells(wi);
+      v[1] += wd[wi].n;
+      v[3] += 1;
+    }
+  }
+  block_scan4(v, tot);
+  int64_t c_pre = v[0], a_pre = v[1], kk = v[3];
+  for (int k = k0; k < k1; ++k) {
+    const int wi = nw.wl_wire[k];
+    if (cell_wire(wi)) {
+      nw.cl_wire[kk] = wi;
+      nw.cl_cell[kk] = c_pre;
+      nw.cl_atom[kk] = a_pre;
+      c_pre += cells(wi);
+      a_pre += wd[wi].n;
+      ++kk;
+    }
+  }
+  if (t == 0) {
+    const int n = (int)tot[3];
+    nw.cl_cell[n] = tot[0];
+    nw.cl_atom[n] = tot[1];
+    nw.n_cell[0] = n;
+  }
+}
+
 __device__ __forceinline__ void nl_env_merge_body(NlWork nw, const WireDev* __restrict__ wd) {
   __shared__ float s_red[2][kSlotTile / 32];
+  __shared__ int s_last;
   const int nf = nw.n_flagged[0];
   if (nf == 0 || !nw.slab_ok) return;
   const int64_t tiles = nw.wl_tile[nf];
@@ -594,6 +657,16 @@ __device__ __forceinline__ void nl_env_merge_body(NlWork nw, const WireDev* __re
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dis = fmaxf(dis, __shfl_xor_sync(0xffffffffu, dis, o));
     if (lane == 0 && dis > 0.f) atomicMax(nw.wdis + wi, __float_as_uint(dis));
+  }
+  // the last block to finish lists the wires that take the cell build (every
+  // block's disorder maxima fenced before its arrival is counted)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(nw.merge_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    nl_cell_list_block(nw, wd);
   }
 }
 __global__ void __launch_bounds__(kSlotTile) k_nl_env_merge(NlWork nw, const WireDev* __restrict__ wd) {

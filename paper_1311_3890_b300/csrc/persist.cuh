@@ -228,12 +228,17 @@ __global__ void __launch_bounds__(256) k_steps_persistent(PersistArgs a) {
       if (!grid_sync(a.bar, bt)) return;
       nl_env_merge_body(a.nw, a.wd);
       if (!grid_sync(a.bar, bt)) return;
-      nl_clear_body(a.nw, a.wd, a.cell_count);
-      if (!grid_sync(a.bar, bt)) return;
-      nl_bin_body(a.nw, a.wd, a.x, a.N, a.cell_count, a.cell_atoms, a.cell_of, a.wire_status);
-      if (!grid_sync(a.bar, bt)) return;
-      nl_sort_body(a.nw, a.wd, a.cell_count, a.cell_atoms);
-      if (!grid_sync(a.bar, bt)) return;
+      // the cell build's phases only when a wire takes it (the count read from
+      // L2, so that every block takes the same branch and meets the same
+      // barriers)
+      if (__ldcg(a.nw.n_cell) > 0) {
+        nl_clear_body(a.nw, a.wd, a.cell_count);
+        if (!grid_sync(a.bar, bt)) return;
+        nl_bin_body(a.nw, a.wd, a.x, a.N, a.cell_count, a.cell_atoms, a.cell_of, a.wire_status);
+        if (!grid_sync(a.bar, bt)) return;
+        nl_sort_body(a.nw, a.wd, a.cell_count, a.cell_atoms);
+        if (!grid_sync(a.bar, bt)) return;
+      }
       nl_build_body<int4>(a.nw, a.wd, a.cell_count, a.cell_atoms, a.cell_of, a.slot_of, a.rlist2u,
                           a.nbr, a.n_nbr, a.cap, a.jrange, xq, a.xq_b, a.wire_status);
       nl_build_slab_body(a.nw, a.wd, a.slot_of, a.rlist2, a.slab_range, a.nbr, a.n_nbr, a.cap,

@@ -109,6 +109,11 @@ struct tbsma_ctx {
   int64_t* wl_cell = nullptr;
   int64_t* wl_atom = nullptr;
   int64_t* wl_tile = nullptr;
+  int32_t* cl_wire = nullptr;   // flagged wires that take the cell build (see NlWork)
+  int64_t* cl_cell = nullptr;
+  int64_t* cl_atom = nullptr;
+  int32_t* n_cell = nullptr;
+  uint32_t* merge_done = nullptr;
   int4* xq2 = nullptr;         // second position buffer of the persistent step kernel
   float2* xenv = nullptr;      // per atom: prefix max / suffix min of x (slab-build envelopes)
   float2* tenv = nullptr;      // per tile: max / min of x (slab-build envelopes)
@@ -178,6 +183,11 @@ struct tbsma_ctx {
     w.last_build = last_build;
     w.banked = banked;
     w.rebuilt = rebuilt;
+    w.cl_wire = cl_wire;
+    w.cl_cell = cl_cell;
+    w.cl_atom = cl_atom;
+    w.n_cell = n_cell;
+    w.merge_done = merge_done;
     return w;
   }
 };
@@ -1235,6 +1245,11 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ALLOC(c->wl_cell, W + 1);
   ALLOC(c->wl_atom, W + 1);
   ALLOC(c->wl_tile, W + 1);
+  ALLOC(c->cl_wire, W);
+  ALLOC(c->cl_cell, W + 1);
+  ALLOC(c->cl_atom, W + 1);
+  ALLOC(c->n_cell, 1);
+  ALLOC(c->merge_done, 1);
   ALLOC(c->xenv, N);
   ALLOC(c->tenv, (size_t)(NS / kSlotTile));
   ALLOC(c->wdis, W);
@@ -1262,6 +1277,8 @@ tbsma_status tbsma_init(const tbsma_params* params, tbsma_precision precision, i
   ok = ok && cudaMemsetAsync(c->flag, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->n_rebuilds, 0, sizeof(int32_t) * W, st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->chains, 0, sizeof(int64_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->n_cell, 0, sizeof(int32_t), st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->merge_done, 0, sizeof(uint32_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->rebuilt, 0, 2 * sizeof(int64_t), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->last_build, 0, sizeof(int64_t) * W, st) == cudaSuccess;

@@ -211,19 +211,25 @@ def test_disordered_atom_order_takes_the_cell_build(tb, orc):
     assert norm <= 1e-5
 
 
-def test_wire_beyond_the_slab_coordinate_range_takes_the_cell_build(tb, orc):
+@pytest.mark.parametrize("long_first", [True, False])
+def test_wire_beyond_the_slab_coordinate_range_takes_the_cell_build(tb, orc, long_first):
     """A D2 x 300 nm wire (55k atoms) moved 600 A along its axis after init
     reaches 2100 A from its fixed-point origin, beyond the 2048 A within
     which the slab scan's FP32 coordinates stay inside the list radius's
     guard, so its lists come from the cell grid (whose +L/2 margins hold the
     moved wire); the short wire beside it takes the slab scan.  Both wires'
-    lists bracket the oracle's pairs and their forces match the oracle's."""
+    lists bracket the oracle's pairs and their forces match the oracle's,
+    with the cell-built wire first or second in the batch (the cell build
+    walks its own compacted list of wires)."""
+    geoms = (fcc_wire(2.0, 300.0), fcc_wire(2.0, 6.0))
+    if not long_first:
+        geoms = geoms[::-1]
     wires = [Wire(x=jitter(g.x, 0.05, 31 + k), kind=g.kind, diameter_nm=2.0, length_nm=g.length_nm,
                   L0=g.L0, temperature=10.0, strain_rate=0.0, gamma=1e-3, seed=k)
-             for k, g in enumerate((fcc_wire(2.0, 300.0), fcc_wire(2.0, 6.0)))]
+             for k, g in enumerate(geoms)]
     b = pack(wires)
     eng = tb.Engine(b, precision="mixed")
-    s0 = b.wire_slice(0)
+    s0 = b.wire_slice(0 if long_first else 1)
     origin = 0.5 * (b.x[s0, 0].min() + b.x[s0, 0].max())  # the centre of the initial box
     b.x[s0, 0] += 600.0
     assert np.max(np.abs(b.x[s0, 0] - origin)) > 2048.0
