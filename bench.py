@@ -55,6 +55,9 @@ KERNELS_PER_STEP = 4  # integrate, plan, density, force (+ the rebuild chain whe
 KERNELS_PER_CHAIN = 7  # two envelope passes, cell clear, bin, sort, cell build, slab build (per plan)
 OBS_EVERY = 1000  # per-wire observables reported every OBS_EVERY steps inside the timed region
 KERNELS_PER_OBS = 5  # pack, plan, density + force (with energies), reduce (+ a rebuild chain)
+# a report folded into the call's last step (tbsma_step_observe in graph
+# replays): that step's passes form the energies, so the report is the reduce
+KERNELS_PER_FOLDED_OBS = 1
 METRIC = "aggregate TB-SMA atom-steps/s (batched FP32/FP64-mixed vs plain FP64) at ≤1e-5 force err"
 UNIT = "atom-steps/s"
 
@@ -387,11 +390,12 @@ def _chunks(K: int):
 
 
 def launches_in(K: int, chains: int, persistent: bool = False) -> int:
-    """Kernels launched by K timed steps: the fixed ones per step and per
-    report, one closing kernel per graph replay or direct sequence, and
+    """Kernels launched by K timed steps in calls of tbsma_step_observe: the
+    fixed ones per step, one closing kernel per graph replay or direct
+    sequence, the report's reduce (folded into the call's last step), and
     `chains` launches of the rebuild chain (counted on the device).  In the
-    persistent step kernel a call of up to 1000 steps is one launch, and
-    only the reports launch the rebuild chain."""
+    persistent step kernel a call of up to 1000 steps is one launch, and the
+    report runs its own passes: only the reports launch the rebuild chain."""
     if persistent:
         return sum(-(-k // PERSIST_STEPS) + KERNELS_PER_OBS + KERNELS_PER_CHAIN
                    for k in _chunks(K))
@@ -401,7 +405,7 @@ def launches_in(K: int, chains: int, persistent: bool = False) -> int:
         n += full * (KERNELS_PER_STEP * GRAPH_CHUNK + 1)
         if rem:
             n += KERNELS_PER_STEP * rem + 1
-        n += KERNELS_PER_OBS
+        n += KERNELS_PER_FOLDED_OBS
     return n
 
 
@@ -638,8 +642,7 @@ def run_ours(args):
         ob = run_logged(eng, args.steps, log, 2.0, report_every=OBS_EVERY, check_every=1)
     else:
         for k in _chunks(args.steps):  # the job: steps with per-wire observables every OBS_EVERY
-            eng.step(k, 2.0)
-            ob = eng.observables()
+            ob = eng.step_observe(k, 2.0)
     ev1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -745,8 +748,7 @@ def run_ours(args):
         t = time.perf_counter()
         for _ in range(n_seg):
             eng.upload(xh, vh)
-            eng.step(seg, 2.0)
-            eng.observables()
+            eng.step_observe(seg, 2.0)
             eng.download(xh, vh)
         el = time.perf_counter() - t
         obs_bytes = W * 64

@@ -427,6 +427,18 @@ tbsma_status tbsma_restore_state(tbsma_ctx* ctx, const double* x_host, const dou
  * still filled). */
 tbsma_status tbsma_reduce_observables(tbsma_ctx* ctx, tbsma_obs* out);
 
+/* n_steps steps as tbsma_step_nvt_pull, then the observables of the final
+ * state as tbsma_reduce_observables (Eq. 3-5): bitwise the same trajectory
+ * and the same out[n_wires] (host) as the two calls.  In graph replays
+ * under the default protocol the last step's pair passes also form the
+ * per-atom energy and virial terms (their forces are the same), so the
+ * report does not run the passes again (a whole last graph chunk replays a
+ * second captured graph, kept until the graphs are dropped); the
+ * persistent step kernel and the protocol mode make the two calls.
+ * Synchronises.  Errors: as tbsma_step_nvt_pull, and EINVAL for a null out;
+ * EWIRE as tbsma_reduce_observables (out is still filled). */
+tbsma_status tbsma_step_observe(tbsma_ctx* ctx, int64_t n_steps, double dt_fs, tbsma_obs* out);
+
 /* Compare MIXED and FP64 forces at the current positions on the same list,
  * per wire, into out[n_wires] (host).  Whether a pair is inside r_cut is
  * decided once, by the MIXED path's FP32 rule, for both arms (a pair within

@@ -150,6 +150,11 @@ struct tbsma_ctx {
   std::vector<WireDev> wires_h;
   Graph graph;
   cudaGraphExec_t obs_graph = nullptr;  // a report's re-pack, rebuild and passes (launch_captured)
+  // tbsma_step_observe's last kick sequence: the step graph with the
+  // per-atom energy terms in its last step's passes
+  cudaGraphExec_t seq_obs_graph = nullptr;
+  int seq_obs_steps = 0;
+  double seq_obs_dt = -1.0;
   cudaGraphExec_t fc_graph = nullptr;   // the force check's
   double graph_dt = -1.0;
 
@@ -567,7 +572,10 @@ struct PhaseMarks {
 // merged full kick, and a closing half kick after the last force pass.
 // With `pm`, the list rebuild chain and the two pair passes are enqueued
 // one by one with an event after each phase (same kernels, same order).
-tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt, PhaseMarks* pm = nullptr) {
+// obs_last: the last step's pair passes also form the per-atom energy and
+// virial terms (the same forces), for a report at the sequence's end.
+tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt, PhaseMarks* pm = nullptr,
+                           bool obs_last = false) {
   if (barostat(c)) return enqueue_steps_baro(c, s, n, dt);
   const double hk = 0.5 * dt * c->inv_m;
   for (int k = 0; k < n; ++k) {
@@ -578,7 +586,8 @@ tbsma_status enqueue_steps(tbsma_ctx* c, cudaStream_t s, int n, double dt, Phase
     else integrate<2>(c, s, dt);
     if (!pm) {
       TB_TRY(launch_nl(c, s, 0, 1, c->step_counter));
-      TB_TRY(launch_pair<false>(c, s, c->prec));
+      if (obs_last && k == n - 1) TB_TRY(launch_pair<true>(c, s, c->prec));
+      else TB_TRY(launch_pair<false>(c, s, c->prec));
       continue;
     }
     pm->mark(s, TBSMA_PHASE_INTEGRATE);
@@ -605,11 +614,13 @@ void drop_graph(tbsma_ctx* c) {
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   c->graph = Graph{};
   c->graph_dt = -1.0;
-  for (cudaGraphExec_t* g : {&c->obs_graph, &c->fc_graph})
+  for (cudaGraphExec_t* g : {&c->obs_graph, &c->fc_graph, &c->seq_obs_graph})
     if (*g) {
       cudaGraphExecDestroy(*g);
       *g = nullptr;
     }
+  c->seq_obs_steps = 0;
+  c->seq_obs_dt = -1.0;
 }
 
 // Launch the kernels `enqueue` puts on a stream as one graph, captured on
@@ -659,21 +670,27 @@ tbsma_status set_dt(tbsma_ctx* c, double dt) {
   return TBSMA_OK;
 }
 
-tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
-  NvtxRange range_("capture step graph");
-  drop_graph(c);
+// Captures `steps` steps as one kick sequence (enqueue_steps) into *out.
+tbsma_status capture_steps(tbsma_ctx* c, int steps, double dt, bool obs_last, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   TB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  tbsma_status st = enqueue_steps(c, c->cap_stream, steps, dt);
+  tbsma_status st = enqueue_steps(c, c->cap_stream, steps, dt, nullptr, obs_last);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (st != TBSMA_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&c->graph.exec, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return TBSMA_OK;
+}
+
+tbsma_status capture(tbsma_ctx* c, int steps, double dt) {
+  NvtxRange range_("capture step graph");
+  drop_graph(c);
+  TB_TRY(capture_steps(c, steps, dt, false, &c->graph.exec));
   c->graph.steps = steps;
   c->graph_dt = dt;
   return TBSMA_OK;
@@ -1416,15 +1433,11 @@ tbsma_status tbsma_step_nvt_pull(tbsma_ctx* c, int64_t n_steps, double dt_fs) {
   return status_verdict(c);
 }
 
-tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
-  NvtxRange range_("tbsma_reduce_observables");
-  if (!c || !out) return TBSMA_EINVAL;
-  // re-pack, rebuild flagged wires, both passes with the per-atom terms
-  TB_TRY(launch_captured(c, c->obs_graph, [c](cudaStream_t s) {
-    TB_TRY(launch_pack(c, s, 1));
-    TB_TRY(launch_nl(c, s, 0, 0, nullptr));
-    return launch_pair<true>(c, s, c->prec);
-  }));
+namespace {
+
+// The per-wire reduction of a report from the per-atom terms the last pair
+// passes formed at the current positions, copied to the host.
+tbsma_status observe_out(tbsma_ctx* c, tbsma_obs* out) {
   const double rhs = 0.5 * c->P.r0;
   const double v_atom = 4.0 / 3.0 * 3.141592653589793238462643383279 * rhs * rhs * rhs;
   k_observe<<<std::min(c->W, 65535), 256, 0, c->stream>>>(
@@ -1436,6 +1449,60 @@ tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
   // the grid-clamp mark is not a fault, and status_verdict grows the grid now
   for (int w = 0; w < c->W; ++w) out[w].status &= ~(int32_t)kWireGridClamp;
   return status_verdict(c);
+}
+
+}  // namespace
+
+tbsma_status tbsma_reduce_observables(tbsma_ctx* c, tbsma_obs* out) {
+  NvtxRange range_("tbsma_reduce_observables");
+  if (!c || !out) return TBSMA_EINVAL;
+  // re-pack, rebuild flagged wires, both passes with the per-atom terms
+  TB_TRY(launch_captured(c, c->obs_graph, [c](cudaStream_t s) {
+    TB_TRY(launch_pack(c, s, 1));
+    TB_TRY(launch_nl(c, s, 0, 0, nullptr));
+    return launch_pair<true>(c, s, c->prec);
+  }));
+  return observe_out(c, out);
+}
+
+tbsma_status tbsma_step_observe(tbsma_ctx* c, int64_t n_steps, double dt_fs, tbsma_obs* out) {
+  NvtxRange range_("tbsma_step_observe");
+  if (!c || !out) return TBSMA_EINVAL;
+  if (n_steps < 0 || !(dt_fs > 0.0)) return fail(c, TBSMA_EINVAL, "n_steps < 0 or dt <= 0");
+  // Graph replays under the default protocol fold the report into the
+  // call's last step; the persistent step kernel, the protocol mode and an
+  // empty call step, then report.
+  const bool fold = n_steps > 0 && !protocol_mode(c) &&
+                    (c->step_mode == TBSMA_STEPS_GRAPH ||
+                     (c->step_mode == TBSMA_STEPS_AUTO && persist_blocks(c) == 0));
+  if (!fold) {
+    const tbsma_status st = tbsma_step_nvt_pull(c, n_steps, dt_fs);
+    if (st != TBSMA_OK && st != TBSMA_EWIRE) return st;
+    return tbsma_reduce_observables(c, out);
+  }
+  // the call's kick sequences as tbsma_step_nvt_pull splits them: whole
+  // graph chunks, then the remainder (or the last whole chunk)
+  const int64_t chunk = std::min<int64_t>(n_steps, kGraphChunk);
+  const int64_t last = n_steps % chunk == 0 ? chunk : n_steps % chunk;
+  if (n_steps > last) {
+    const tbsma_status st = tbsma_step_nvt_pull(c, n_steps - last, dt_fs);
+    if (st != TBSMA_OK && st != TBSMA_EWIRE) return st;  // a bad wire stops no other
+  }
+  TB_TRY(set_dt(c, dt_fs));
+  if (last == chunk) {  // a whole chunk: its own graph, replayed
+    if (!c->seq_obs_graph || c->seq_obs_steps != chunk || c->seq_obs_dt != dt_fs) {
+      if (c->seq_obs_graph) cudaGraphExecDestroy(c->seq_obs_graph);
+      c->seq_obs_graph = nullptr;
+      TB_TRY(capture_steps(c, (int)chunk, dt_fs, true, &c->seq_obs_graph));
+      c->seq_obs_steps = (int)chunk;
+      c->seq_obs_dt = dt_fs;
+    }
+    TB_CUDA(c, cudaGraphLaunch(c->seq_obs_graph, c->stream));
+  } else {
+    TB_TRY(enqueue_steps(c, c->stream, (int)last, dt_fs, nullptr, true));
+  }
+  c->steps_done += last;
+  return observe_out(c, out);
 }
 
 tbsma_status tbsma_force_check(tbsma_ctx* c, tbsma_fcheck* out) {

@@ -76,10 +76,11 @@ def run_logged(eng, n_steps: int, log: RunLog, dt: float = 2.0, report_every: in
     done, ob = 0, None
     while done < n_steps or ob is None:
         k = min(report_every, n_steps - done)
-        if k > 0:
-            eng.step(k, dt)
+        if k > 0:  # the steps and their report in one call
+            ob = eng.step_observe(k, dt)
             done += k
-        ob = eng.observables()
+        else:
+            ob = eng.observables()
         log.report(ob)
         step = int(ob["step"][0])
         if check_every and step % check_every == 0:

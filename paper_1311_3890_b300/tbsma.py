@@ -138,6 +138,7 @@ SIGNATURES = [
     ("tbsma_atom_energies", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_step_nvt_pull", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
     ("tbsma_reduce_observables", ctypes.c_int, [_P, _P]),
+    ("tbsma_step_observe", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P]),
     ("tbsma_force_check", ctypes.c_int, [_P, _P]),
     ("tbsma_upload_state", ctypes.c_int, [_P, _P, _P]),
     ("tbsma_download_state", ctypes.c_int, [_P, _P, _P]),
@@ -298,6 +299,17 @@ class Engine:
         st = lib().tbsma_reduce_observables(self.ctx, out)
         if check:
             self._check(st, "tbsma_reduce_observables")
+        return np.ctypeslib.as_array(out).copy()
+
+    def step_observe(self, n_steps: int, dt: float = 2.0, check: bool = True) -> np.ndarray:
+        """step(n_steps, dt), then observables(), in one call
+        (tbsma_step_observe): the same trajectory and bitwise the same
+        report, the report's pair passes folded into the last step in graph
+        replays."""
+        out = (ObsC * self.W)()
+        st = lib().tbsma_step_observe(self.ctx, int(n_steps), float(dt), out)
+        if check:
+            self._check(st, "tbsma_step_observe")
         return np.ctypeslib.as_array(out).copy()
 
     def force_check(self) -> np.ndarray:

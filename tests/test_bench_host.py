@@ -16,14 +16,14 @@ def test_chunks_report_every_1000_steps():
 
 def test_launch_count_of_the_default_run():
     """10000 steps: 200 graph replays of 50 steps (4 kernels per step plus the
-    closing half kick each), 10 reports of 5 kernels, and the rebuild chains
-    the library counted (one per step and per report's refresh: 7 kernels
-    each, the two envelope passes, the four of the cell build and the slab
-    build)."""
-    chains = 10000 + 10
-    assert bench.launches_in(10000, chains) == 200 * (4 * 50 + 1) + 10 * 5 + 7 * chains == 110320
+    closing half kick each), 10 reports folded into the calls' last steps
+    (the reduce kernel each), and the rebuild chains the library counted
+    (one per step: 7 kernels each, the two envelope passes, the four of the
+    cell build and the slab build)."""
+    chains = 10000
+    assert bench.launches_in(10000, chains) == 200 * (4 * 50 + 1) + 10 * 1 + 7 * chains == 110210
     # a call shorter than the graph is captured whole: one closing kernel
-    assert bench.launches_in(30, 30) == 4 * 30 + 1 + 5 + 7 * 30
+    assert bench.launches_in(30, 30) == 4 * 30 + 1 + 1 + 7 * 30
 
 
 def test_launch_count_in_the_persistent_step_kernel():

@@ -23,6 +23,10 @@ class FakeEngine:
         ob["n_rebuilds"] = self.t // 100
         return ob
 
+    def step_observe(self, n, dt):
+        self.step(n, dt)
+        return self.observables()
+
     def force_check(self):
         self.checks.append(self.t)
         fc = np.ctypeslib.as_array((FCheckC * self.W)()).copy()
