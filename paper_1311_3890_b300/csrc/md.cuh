@@ -711,23 +711,27 @@ __global__ void __launch_bounds__(256)
   __shared__ double sh[256];
   for (int w = blockIdx.x; w < W; w += gridDim.x) {
     const WireDev& wr = wd[w];
-    double e = 0.0, vir = 0.0, v2 = 0.0, vx2 = 0.0, nm = 0.0;
+    // five FP64 operations per atom (B300's FP64 pipe is the bound): the
+    // x and the y + z parts of v^2 apart, the mobile count in an integer
+    double e = 0.0, vir = 0.0, vx2 = 0.0, vyz = 0.0;
+    int nmob = 0;
     for (int a = threadIdx.x; a < wr.n; a += blockDim.x) {
       const int64_t i = wr.offset + a;
       e += e_atom[i];
       vir += w_atom[i];
       if (meta_kind(meta[i]) == 0) {
         const double ux = v[i], uy = v[N + i], uz = v[2 * N + i];
-        v2 += ux * ux + uy * uy + uz * uz;
-        vx2 += ux * ux;
-        nm += 1.0;
+        vx2 = fma(ux, ux, vx2);
+        vyz = fma(uy, uy, fma(uz, uz, vyz));
+        ++nmob;
       }
     }
     e = block_sum(e, sh);
     vir = block_sum(vir, sh);
-    v2 = block_sum(v2, sh);
     vx2 = block_sum(vx2, sh);
-    nm = block_sum(nm, sh);
+    vyz = block_sum(vyz, sh);
+    const double nm = block_sum((double)nmob, sh);
+    const double v2 = vx2 + vyz;
     if (threadIdx.x == 0) {
       tbsma_obs o;
       o.step = steps;
